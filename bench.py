@@ -1,0 +1,294 @@
+#!/usr/bin/env python3
+"""Benchmark: forward + log-likelihood evaluations per second on the
+forward-throughput workload (2^20 synthetic layered models per GPU, 1..10
+layers, 30 gates, 60 frequencies, 200 Hankel points), FP32 path.
+
+One step = one aem_loglik_f32 launch over the whole batch (Cole-Cole, TE
+recursion, Hankel sum, step-off gate transform and Gaussian log-likelihood)
+with inputs resident in HBM; the 210 MB of model inputs exceed the 129 MB L2,
+so each step re-reads them from HBM.  `e2e` times the same call with the
+inputs copied from pinned host memory and the log-likelihoods copied back
+inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the comparison arm for this
+build) on a bounded sample of the same workload on the host cores.
+
+Multi-GPU: every rank evaluates its own 2^20 models (weak scaling, no
+collective on the data path); value = all ranks' models / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "forward-g30-f60-k200"
+P_PER_GPU = 1 << 20
+FLOPS_PER_LAYER_STEP = 60  # FP32 flops (FMA = 2) per layer-step of the recursion, counted from forward.cu
+MUFU_PER_LAYER_STEP = 6    # sqrt(|w|), rsqrt, rcp, ex2, sin, cos
+METRIC = "forward+loglik evals/s"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--models", type=int, default=P_PER_GPU)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def layer_steps(nlayers, F, K):
+    return float(np.sum(nlayers.astype(np.int64))) * F * K
+
+
+def cpu_baseline(target_seconds=15.0):
+    """The FP64 oracle (adaptive-quadrature Hankel integrals), as it stands, on
+    a bounded sample of the workload on this host's cores."""
+    import oracle as O
+    from paper_2109_00661_gb300 import inputs as I
+    so = I.oracle_system(WORKLOAD)
+    so["T"] = O.tmatrix(so["freqs"], so["times"])
+    y_obs = I.noisy(O.forward(I.truth_3layer(), so)[0], seed=0)
+    cores = os.cpu_count() or 1
+    n = 64
+    done, elapsed = 0, 0.0
+    while elapsed < target_seconds:
+        models = I.random_models(n, seed=1000 + done)
+        t0 = time.perf_counter()
+        y = O.forward(models, so, nthreads=cores)
+        O.loglik(y, y_obs, I.EPS_AN, I.EPS_MN)
+        elapsed += time.perf_counter() - t0
+        done += n
+        n = min(n * 2, 4096)
+    return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} models of the {WORKLOAD} workload (adaptive-quadrature FP64 oracle, "
+                      f"{cores} threads), {elapsed:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2109_00661_gb300 import inputs as I
+    so = I.oracle_system(WORKLOAD)
+    so["T"] = O.tmatrix(so["freqs"], so["times"])
+    y_obs = I.noisy(O.forward(I.truth_3layer(), so)[0], seed=0)
+    cores = os.cpu_count() or 1
+    per_step = 256
+    for w in range(args.warmup):
+        O.forward(I.random_models(per_step, seed=w), so, nthreads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        y = O.forward(I.random_models(per_step, seed=100 + s), so, nthreads=cores)
+        O.loglik(y, y_obs, I.EPS_AN, I.EPS_MN)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {per_step}-model sample per step of the 2^20-model batch",
+                       "models_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} models per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2109_00661_gb300 as L
+    from paper_2109_00661_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sysg = L.System(**I.system_kwargs(WORKLOAD))
+    F, K, G = sysg.F, sysg.K, sysg.G
+    P = args.models
+    models_np = I.random_models(P, seed=rank)
+    models = I.to_torch(models_np, torch.float32)
+    y_obs = torch.as_tensor(I.noisy(np.full(G, 1e-11), seed=0), dtype=torch.float64, device="cuda")
+    eps_an = torch.full((G,), I.EPS_AN, dtype=torch.float64, device="cuda")
+    ll = torch.empty(P, dtype=torch.float64, device="cuda")
+    steps_work = layer_steps(models_np["nlayers"], F, K)
+    peaks = L.probe_peaks()
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return L.loglik_f32(sysg, models, y_obs, eps_an, I.EPS_MN, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * P / (ms_max * 1e-3)
+
+    # end to end through the public API: pinned host inputs -> device -> loglik -> host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.as_tensor(np.ascontiguousarray(v, dtype=np.int8 if k == "nlayers" else np.float32)).pin_memory()
+                for k, v in models_np.items()}
+        ll_host = torch.empty(P, dtype=torch.float64).pin_memory()
+        dev = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = ll_host.numel() * ll_host.element_size()
+
+        def e2e_step():
+            for k in host:
+                dev[k].copy_(host[k], non_blocking=True)
+            out = L.loglik_f32(sysg, dev, y_obs, eps_an, I.EPS_MN, stream=stream)
+            ll_host.copy_(out, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = f0.elapsed_time(f1) / args.steps
+        te = torch.tensor([ems], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * P / (float(te.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0:
+        flops = steps_work * FLOPS_PER_LAYER_STEP
+        achieved = flops / (ms * 1e-3) / 1e12
+        peak = 2.0 * peaks["fp32_fma_per_s"] / 1e12
+        mufu_frac = steps_work * MUFU_PER_LAYER_STEP / (ms * 1e-3) / peaks["mufu_per_s"]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {P} random layered models per GPU, 1..10 layers, "
+                                   f"{G} gates, {F} freqs, {K} Hankel points, a=13 m, h=30 m",
+                       "models_per_gpu": P, "gates": G, "freqs": F, "hankel": K,
+                       "l2": "inputs larger than L2 (210 MB of model parameters per step)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
+                         "mufu_frac": mufu_frac, "layer_steps_per_s": steps_work / (ms * 1e-3)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "peaks_measured": peaks,
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -399,6 +399,22 @@ static double mag(const Moments4 &a) {
     return s;
 }
 
+// sin(w t) with the phase reduced modulo 2 pi before rounding: w t can reach
+// 1e6 rad, where rounding w t to double alone would cost ~1e-10 rad.  The
+// product is split exactly (w t = p + e with an FMA) and p is reduced by the
+// nearest multiple of 2 pi using a two-term split of 2 pi.
+static double sin_of_product(double w, double t) {
+    double p = w * t;
+    if (std::fabs(p) < 100.0) return std::sin(p);
+    double e = std::fma(w, t, -p);
+    const double c1 = 6.283185307179586232;    // fl(2 pi)
+    const double c2 = 2.4492935982947064e-16;  // 2 pi - fl(2 pi)
+    double n = std::floor(p / c1 + 0.5);
+    double red = std::fma(-n, c1, p);
+    red = std::fma(-n, c2, red);
+    return std::sin(red + e);
+}
+
 extern "C" void orc_tmatrix(int F, const double *freqs, int G, const double *times, double *T) {
     std::vector<double> w(F), x(F);
     for (int f = 0; f < F; ++f) {
@@ -413,7 +429,7 @@ extern "C" void orc_tmatrix(int F, const double *freqs, int G, const double *tim
         for (int j = 0; j + 1 < F; ++j) {
             auto fm = [&](double om) -> Moments4 {
                 Moments4 r;
-                double d = std::log(om) - x[j], s = std::sin(om * t);
+                double d = std::log(om) - x[j], s = sin_of_product(om, t);
                 r.m[0] = s;
                 r.m[1] = s * d;
                 r.m[2] = s * d * d;
@@ -450,7 +466,7 @@ extern "C" void orc_tmatrix(int F, const double *freqs, int G, const double *tim
         // panels between zeros of sin(w t), partial sums extrapolated by Wynn epsilon
         {
             double wF = w[F - 1];
-            auto fh = [&](double om) -> double { return std::sqrt(wF / om) * std::sin(om * t); };
+            auto fh = [&](double om) -> double { return std::sqrt(wF / om) * sin_of_product(om, t); };
             double first_zero = std::ceil(wF * t / PI) * PI / t;
             if (first_zero <= wF) first_zero += PI / t;
             double total = integrate<double>(fh, wF, first_zero, 1e-10, 1e-300, 8);

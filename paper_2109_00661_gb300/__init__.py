@@ -1,0 +1,157 @@
+"""GB300-native hot path of RJSMC for airborne-EM IP detectability
+(Davies et al., arXiv 2109.00661).
+
+Thin Python binding over the C ABI in ``include/aem_rjsmc.h``: argument
+marshalling only.  Every step of the forward model, likelihood and SMC stage
+runs in the CUDA kernels of ``libaemrjsmc.so``; PyTorch provides device memory
+and streams.  Calls fail loudly if the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import AEMError, check
+
+__all__ = ["System", "forward_f32", "forward_f64", "loglik_f32", "loglik_f64", "probe_peaks", "AEMError",
+           "CC_PAPER", "CC_PELTON"]
+
+CC_PAPER = 0
+CC_PELTON = 1
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise AEMError("paper_2109_00661_gb300 needs a CUDA device; there is no CPU path")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class System:
+    """aem_system: loop geometry plus the precomputed Hankel rule and transform matrix."""
+
+    def __init__(self, loop_radius=13.0, height=30.0, current=1.0, n_freq=60, f_min_hz=1.0, f_max_hz=1e7,
+                 gate_times=None, n_hankel=200, cc_form=CC_PAPER):
+        _torch()
+        lib = _lib.load()
+        if gate_times is None:
+            gate_times = np.logspace(-5, -2, 30)
+        self._times = np.ascontiguousarray(gate_times, dtype=np.float64)
+        desc = _lib.SystemDesc(float(loop_radius), float(height), float(current), int(n_freq), float(f_min_hz),
+                               float(f_max_hz), len(self._times),
+                               self._times.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n_hankel),
+                               int(cc_form))
+        h = ctypes.c_void_p()
+        check(lib.aem_system_create(ctypes.byref(desc), ctypes.byref(h)), "aem_system_create")
+        self._h = h
+        self.F, self.G, self.K = int(n_freq), len(self._times), int(n_hankel)
+        self.loop_radius, self.height, self.current, self.cc_form = loop_radius, height, current, cc_form
+        self.times = self._times.copy()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self):
+        """Host copies of (freqs_hz [F], lambda [K], hankel_w [K], T [G, F])."""
+        f = np.zeros(self.F)
+        lam = np.zeros(self.K)
+        hw = np.zeros(self.K)
+        T = np.zeros((self.G, self.F))
+        check(_lib.load().aem_system_tables(self._h, f.ctypes.data, lam.ctypes.data, hw.ctypes.data, T.ctypes.data),
+              "aem_system_tables")
+        return f, lam, hw, T
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().aem_system_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _models_struct(models, dtype):
+    torch = _torch()
+    nl = models["nlayers"]
+    arrs = [models[k] for k in ("logsig", "logh", "m", "logtau", "c")]
+    for a in arrs:
+        if a.dtype != dtype or not a.is_cuda or not a.is_contiguous() or a.dim() != 2:
+            raise AEMError(f"model arrays must be contiguous 2-D CUDA tensors of {dtype}")
+    if nl.dtype != torch.int8 or not nl.is_cuda:
+        raise AEMError("nlayers must be a CUDA int8 tensor")
+    P, lmax = arrs[0].shape
+    return _lib.Models(P, lmax, nl.data_ptr(), *[a.data_ptr() for a in arrs])
+
+
+def _forward(fn, models, dtype, want_gates, want_imh, system, stream):
+    torch = _torch()
+    ms = _models_struct(models, dtype)
+    P = ms.n_models
+    dev = models["logsig"].device
+    gates = torch.empty((P, system.G), dtype=dtype, device=dev) if want_gates else None
+    imh = torch.empty((P, system.F), dtype=dtype, device=dev) if want_imh else None
+    check(fn(system.handle, ctypes.byref(ms), _dptr(gates), _dptr(imh), _stream_ptr(stream)), fn.__name__)
+    return gates, imh
+
+
+def forward_f32(system, models, want_imh=False, stream=None):
+    """aem_forward_f32: gates [P, G] (float32), and Im Hz_s [P, F] when want_imh."""
+    g, i = _forward(_lib.load().aem_forward_f32, models, _torch().float32, True, want_imh, system, stream)
+    return (g, i) if want_imh else g
+
+
+def forward_f64(system, models, want_imh=False, stream=None):
+    """aem_forward_f64: the plain double-precision form of the same kernel."""
+    g, i = _forward(_lib.load().aem_forward_f64, models, _torch().float64, True, want_imh, system, stream)
+    return (g, i) if want_imh else g
+
+
+def _loglik(fn, models, dtype, y_obs, eps_an, eps_mn, system, want_gates, stream):
+    torch = _torch()
+    ms = _models_struct(models, dtype)
+    P = ms.n_models
+    dev = models["logsig"].device
+    y_obs = torch.as_tensor(y_obs, dtype=torch.float64, device=dev).contiguous()
+    eps_an = torch.as_tensor(eps_an, dtype=torch.float64, device=dev).expand(system.G).contiguous()
+    ll = torch.empty(P, dtype=torch.float64, device=dev)
+    gates = torch.empty((P, system.G), dtype=dtype, device=dev) if want_gates else None
+    check(fn(system.handle, ctypes.byref(ms), _dptr(y_obs), _dptr(eps_an), float(eps_mn), _dptr(ll), _dptr(gates),
+             _stream_ptr(stream)), fn.__name__)
+    return (ll, gates) if want_gates else ll
+
+
+def loglik_f32(system, models, y_obs, eps_an, eps_mn, want_gates=False, stream=None):
+    """aem_loglik_f32: Gaussian log-likelihood [P] (float64 sums of FP32 predictions)."""
+    return _loglik(_lib.load().aem_loglik_f32, models, _torch().float32, y_obs, eps_an, eps_mn, system,
+                   want_gates, stream)
+
+
+def loglik_f64(system, models, y_obs, eps_an, eps_mn, want_gates=False, stream=None):
+    """aem_loglik_f64: the same likelihood on the double-precision forward model."""
+    return _loglik(_lib.load().aem_loglik_f64, models, _torch().float64, y_obs, eps_an, eps_mn, system,
+                   want_gates, stream)
+
+
+def probe_peaks():
+    """aem_probe_peaks: measured FP32 FMA/s, MUFU op/s, FP64 FMA/s and SM clock (Hz)."""
+    _torch()
+    out = [ctypes.c_double() for _ in range(4)]
+    check(_lib.load().aem_probe_peaks(*[ctypes.byref(o) for o in out]), "aem_probe_peaks")
+    return dict(fp32_fma_per_s=out[0].value, mufu_per_s=out[1].value, fp64_fma_per_s=out[2].value,
+                sm_clock_hz=out[3].value)

@@ -1,0 +1,47 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aem_rjsmc.h"
+
+namespace aem {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4e-7 * kPi;
+
+// Records the message returned by aem_last_error() and passes the code through.
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t err, const char *what);
+
+#define AEM_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::aem::cuda_fail(_e, #expr); \
+    } while (0)
+
+// Host-side tables (double) and their device copies (float and double).
+struct SystemTables {
+    double a = 0, h = 0, current = 1;
+    int F = 0, G = 0, K = 0, cc_form = 0;
+    std::vector<double> freqs, omega, times, lam, hw, T;  // T is G x F
+};
+
+}  // namespace aem
+
+struct aem_system {
+    aem::SystemTables host;
+    int device = 0;
+    // device tables: omega[F], lam[K], hw[K], T[G*F] in both precisions
+    float *d_omega_f = nullptr, *d_lam_f = nullptr, *d_hw_f = nullptr, *d_T_f = nullptr;
+    double *d_omega_d = nullptr, *d_lam_d = nullptr, *d_hw_d = nullptr, *d_T_d = nullptr;
+    int num_sms = 0;
+};
+
+namespace aem {
+// Builds the Hankel rule and the transform matrix on the host (system.cpp).
+int build_tables(const aem_system_desc *desc, SystemTables *out);
+}  // namespace aem
