@@ -1,0 +1,548 @@
+"""Serial FP64 reference of the RJSMC stage (Davies et al., arXiv 2109.00661,
+Algorithm 1 with the adaptive choices of Section 3.2 and Appendices B-E).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain Python / numpy,
+one particle at a time, in the order the paper states the steps:
+
+  reweight   w = W L^(gamma_t - gamma_{t-1}) within each model, gamma_t by
+             bisection so that TESS = sum_k ESS_k ~ alpha N (Section 3.2.1,
+             App. C), Z_k <- Z_k sum_i w (App. D);
+  resample   within-model systematic resampling, N_{t,k} held fixed (Alg. 1);
+  mutate     R_t sweeps of an RJMCMC kernel: conductive / chargeable birth
+             and death with properties drawn from the prior (App. E: the
+             acceptance then reduces to the tempered likelihood ratio),
+             interface-depth moves and component-wise Gaussian random walks;
+  odds       pi(k|y) = N_k / N (Section 3.2.1) and the BFIPD statistic of
+             Section 2.3.3.
+
+Random numbers come from Philox4x32-10 (Salmon et al., SC 2011) written out
+here from its published definition, keyed per sounding and counted per
+(particle, draw, stage, sweep), so the GPU sampler can reproduce the same
+uniforms.  Readings of the paper used here are listed in the design doc.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------- Philox4x32-10
+_M0 = 0xD2511F53
+_M1 = 0xCD9E8D57
+_W0 = 0x9E3779B9
+_W1 = 0xBB67AE85
+_MASK = 0xFFFFFFFF
+
+
+def philox4x32(counter, key):
+    """Philox4x32 with 10 rounds.  counter: (n, 4) uint32-valued, key: (k0, k1).
+    Returns (n, 4) uint32 as uint64 array."""
+    c = np.array(counter, dtype=np.uint64).reshape(-1, 4).copy()
+    k0 = np.uint64(key[0] & _MASK)
+    k1 = np.uint64(key[1] & _MASK)
+    for r in range(10):
+        p0 = c[:, 0] * np.uint64(_M0)
+        p1 = c[:, 2] * np.uint64(_M1)
+        hi0, lo0 = p0 >> np.uint64(32), p0 & np.uint64(_MASK)
+        hi1, lo1 = p1 >> np.uint64(32), p1 & np.uint64(_MASK)
+        n0 = hi1 ^ c[:, 1] ^ k0
+        n2 = hi0 ^ c[:, 3] ^ k1
+        c = np.stack([n0, lo1, n2, lo0], axis=1)
+        k0 = (k0 + np.uint64(_W0)) & np.uint64(_MASK)
+        k1 = (k1 + np.uint64(_W1)) & np.uint64(_MASK)
+    return c
+
+
+def u01_from(x):
+    """Uniform on (0, 1) from one 32-bit word: (x >> 8 + 1/2) * 2^-24."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 0.5) * (2.0 ** -24)
+
+
+def u01_53(x0, x1):
+    """Uniform on (0, 1) with 53 bits from two words."""
+    hi = (np.asarray(x0, dtype=np.uint64) >> np.uint64(6)).astype(np.float64)
+    lo = (np.asarray(x1, dtype=np.uint64) >> np.uint64(5)).astype(np.float64)
+    return (hi * 2.0 ** 27 + lo + 0.5) * (2.0 ** -53)
+
+
+def gauss_pair(x0, x1):
+    """Box-Muller from two 32-bit words (first output only)."""
+    u1 = u01_from(x0)
+    u2 = u01_from(x1)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+# Stream identities.  Counter words: (particle, purpose, stage, sweep);
+# key: (seed low 32 bits, seed high 32 bits xor sounding).
+PURPOSE_PRIOR0 = 0
+PURPOSE_PRIOR_MAX = 63  # prior draws use purposes 0..63
+PURPOSE_MOVE = 64
+PURPOSE_VALUE = 65
+PURPOSE_ACCEPT = 66
+PURPOSE_RESAMPLE = 67
+
+
+def stream_key(seed, sounding):
+    return (seed & _MASK, ((seed >> 32) ^ sounding) & _MASK)
+
+
+def draws(seed, sounding, particle, purpose, stage, sweep):
+    """Four 32-bit words for each particle index in `particle`."""
+    particle = np.atleast_1d(np.asarray(particle, dtype=np.uint64))
+    ctr = np.zeros((len(particle), 4), dtype=np.uint64)
+    ctr[:, 0] = particle
+    ctr[:, 1] = purpose
+    ctr[:, 2] = stage
+    ctr[:, 3] = sweep
+    return philox4x32(ctr, stream_key(seed, sounding))
+
+
+# ------------------------------------------------------------------ settings
+@dataclass
+class SMCSettings:
+    n_particles: int = 256
+    kappa_max: int = 3
+    lambda_max: int = 4
+    zmax: float = 500.0
+    alpha: float = 0.5          # TESS threshold proportion
+    c_mut: float = 0.01         # 1 - c' (App. B)
+    r_max: int = 10
+    n_sweeps: int = 10          # > 0: fixed R_t; <= 0: adaptive R_t (App. B)
+    step_phi: float = 0.2
+    step_m: float = 0.05
+    step_tau: float = 0.05
+    step_c: float = 0.05
+    step_z: float = 10.0
+    phi_lo: float = -4.0
+    phi_hi: float = 2.0
+    tau_log_prior: bool = False  # False: tau ~ U(0, 1) s (Section 2.3.1); True: log10 tau ~ U(lo, hi)
+    logtau_lo: float = -6.0
+    logtau_hi: float = -1.0
+    seed: int = 0
+    sounding: int = 0
+    bisect_iters: int = 60
+
+    @property
+    def n_models(self):
+        return (self.kappa_max + 1) * (self.lambda_max + 1)
+
+
+# Move types, chosen uniformly (a move that is impossible in the current
+# model is proposed and counted as a rejection).
+MOVES = ("sigma_birth", "sigma_death", "m_birth", "m_death", "depth", "perturb")
+
+
+@dataclass
+class Particle:
+    kappa: int
+    lam: int
+    phib: float
+    zc: list
+    phic: list
+    zm: list
+    mv: list
+    tau: float
+    c: float
+
+    def model(self, s: SMCSettings):
+        return self.kappa * (s.lambda_max + 1) + self.lam
+
+    def copy(self):
+        return Particle(self.kappa, self.lam, self.phib, list(self.zc), list(self.phic), list(self.zm),
+                        list(self.mv), self.tau, self.c)
+
+
+# -------------------------------------------------------------------- prior
+# Prior draw layout: draw index d uses word d % 4 of the Philox block with
+# purpose d // 4 (purposes 0..17).
+PRIOR_SLOTS = 16  # reserved interface slots per profile
+D_KAPPA, D_LAM, D_PHIB, D_TAU, D_C = 0, 1, 2, 3, 4
+D_ZC = 5
+D_PHIC = D_ZC + PRIOR_SLOTS
+D_ZM = D_PHIC + PRIOR_SLOTS
+D_MV = D_ZM + PRIOR_SLOTS
+N_PRIOR_DRAWS = D_MV + PRIOR_SLOTS
+
+
+def prior_uniforms(s: SMCSettings, i: int):
+    words = np.concatenate([draws(s.seed, s.sounding, i, p, 0, 0)[0] for p in range((N_PRIOR_DRAWS + 3) // 4)])
+    return u01_from(words)
+
+
+def sample_prior(s: SMCSettings, i: int) -> Particle:
+    """kappa ~ U{0..kappa_max}, lambda ~ U{0..lambda_max}; depths are sorted
+    uniforms on (0, zmax) (density k!/zmax^k); log10 sigma ~ U(-4, 2); m ~ U(0,1);
+    tau, c global (Section 2.3.1)."""
+    u = prior_uniforms(s, i)
+    kappa = min(int(u[D_KAPPA] * (s.kappa_max + 1)), s.kappa_max)
+    lam = min(int(u[D_LAM] * (s.lambda_max + 1)), s.lambda_max)
+    phib = s.phi_lo + (s.phi_hi - s.phi_lo) * u[D_PHIB]
+    if s.tau_log_prior:
+        tau = 10.0 ** (s.logtau_lo + (s.logtau_hi - s.logtau_lo) * u[D_TAU])
+    else:
+        tau = u[D_TAU]
+    c = u[D_C]
+    zc = [s.zmax * u[D_ZC + j] for j in range(kappa)]
+    phic = [s.phi_lo + (s.phi_hi - s.phi_lo) * u[D_PHIC + j] for j in range(kappa)]
+    zm = [s.zmax * u[D_ZM + j] for j in range(lam)]
+    mv = [u[D_MV + j] for j in range(lam)]
+    oc = np.argsort(zc, kind="stable")
+    om = np.argsort(zm, kind="stable")
+    return Particle(kappa, lam, phib, [zc[j] for j in oc], [phic[j] for j in oc], [zm[j] for j in om],
+                    [mv[j] for j in om], tau, c)
+
+
+def in_prior(p: Particle, s: SMCSettings) -> bool:
+    if not (s.phi_lo < p.phib < s.phi_hi):
+        return False
+    if any(not (s.phi_lo < v < s.phi_hi) for v in p.phic):
+        return False
+    if any(not (0.0 < v < 1.0) for v in p.mv):
+        return False
+    if any(not (0.0 < z < s.zmax) for z in p.zc + p.zm):
+        return False
+    if s.tau_log_prior:
+        if not (s.logtau_lo < math.log10(p.tau) < s.logtau_hi):
+            return False
+    elif not (0.0 < p.tau < 1.0):
+        return False
+    return 0.0 < p.c < 1.0
+
+
+# ---------------------------------------------------------------- merge (a1)
+def merge_particle(p: Particle, lmax: int):
+    """Direct sum of the decoupled profiles (Section 2.1, Fig. 2): returns
+    (L, logsig[lmax], logh[lmax], m[lmax], logtau[lmax], c[lmax])."""
+    z = sorted(p.zc + p.zm)
+    L = len(z) + 1
+    logsig = np.zeros(lmax)
+    logh = np.zeros(lmax)
+    m = np.zeros(lmax)
+    for n in range(L):
+        top = 0.0 if n == 0 else z[n - 1]
+        ic = sum(1 for v in p.zc if v <= top) if n > 0 else 0
+        jm = sum(1 for v in p.zm if v <= top) if n > 0 else 0
+        logsig[n] = p.phib if ic == 0 else p.phic[ic - 1]
+        m[n] = 0.0 if jm == 0 else p.mv[jm - 1]
+        if n < L - 1:
+            logh[n] = math.log10(z[n] - top)
+    return L, logsig, logh, m, np.full(lmax, math.log10(p.tau)), np.full(lmax, p.c)
+
+
+def merged_batch(parts, lmax):
+    P = len(parts)
+    out = dict(nlayers=np.zeros(P, dtype=np.int8), logsig=np.zeros((P, lmax)), logh=np.zeros((P, lmax)),
+               m=np.zeros((P, lmax)), logtau=np.zeros((P, lmax)), c=np.zeros((P, lmax)))
+    for i, p in enumerate(parts):
+        L, ls, lh, mm, lt, cc = merge_particle(p, lmax)
+        out["nlayers"][i] = L
+        out["logsig"][i] = ls
+        out["logh"][i] = lh
+        out["m"][i] = mm
+        out["logtau"][i] = lt
+        out["c"][i] = cc
+    return out
+
+
+# -------------------------------------------------------------- reweight (a7)
+def _lse(v):
+    v = np.asarray(v, dtype=np.float64)
+    if v.size == 0:
+        return -np.inf
+    m = np.max(v)
+    if not np.isfinite(m):
+        return m
+    return m + math.log(float(np.sum(np.exp(v - m))))
+
+
+def tess(ll, model, n_models, dgamma):
+    """TESS = sum_k ESS_k with ESS_k = (sum_i w_i)^2 / sum_i w_i^2 over model k's
+    particles, w_i = L_i^dgamma with uniform W within each model (App. C)."""
+    total = 0.0
+    for k in range(n_models):
+        a = dgamma * ll[model == k]
+        if a.size == 0:
+            continue
+        total += math.exp(2.0 * _lse(a) - _lse(2.0 * a))
+    return total
+
+
+def choose_dgamma(ll, model, n_models, gamma_prev, alpha, iters=60):
+    """Bisection on dgamma in (0, 1 - gamma_prev] so that TESS ~ alpha N
+    (Alg. 1, Section 3.2.1).  Takes the whole remaining step when it keeps
+    TESS >= alpha N; otherwise the largest bisection point found with
+    TESS >= alpha N (the smallest failing point if none was found)."""
+    N = len(ll)
+    target = alpha * N
+    hi = 1.0 - gamma_prev
+    if tess(ll, model, n_models, hi) >= target:
+        return hi, True
+    lo = 0.0
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if tess(ll, model, n_models, mid) >= target:
+            lo = mid
+        else:
+            hi = mid
+    return (lo if lo > 0.0 else hi), False
+
+
+def reweight(ll, model, n_models, gamma_prev, alpha, iters=60):
+    """One re-weighting step.  Returns (dgamma, reached_one, logz_increment[k],
+    W[i] normalised within each model)."""
+    dg, done = choose_dgamma(ll, model, n_models, gamma_prev, alpha, iters)
+    inc = np.zeros(n_models)
+    W = np.zeros(len(ll))
+    for k in range(n_models):
+        idx = np.nonzero(model == k)[0]
+        if idx.size == 0:
+            continue
+        a = dg * ll[idx]
+        l = _lse(a)
+        inc[k] = l - math.log(idx.size)  # log of sum_i W_{t-1} w, W_{t-1} = 1/N_k (App. D)
+        W[idx] = np.exp(a - l)
+    return dg, done, inc, W
+
+
+# -------------------------------------------------------------- resample (a8)
+CDF_BITS = 40
+
+
+def resample_systematic(W, model, n_models, u40):
+    """Within-model systematic resampling with an integer CDF.
+
+    For model k with particles i_0 < i_1 < ... (index order), q_j =
+    round(W_{i_j} 2^40), C_j = q_0 + ... + q_j with the last C forced to 2^40;
+    the j-th output slot (the j-th particle of model k in index order) takes the
+    smallest j' with C_{j'} > floor((j 2^40 + u40_k) / N_k).  Returns the
+    ancestor index of every particle."""
+    one = 1 << CDF_BITS
+    anc = np.arange(len(W))
+    for k in range(n_models):
+        idx = np.nonzero(model == k)[0]
+        n = idx.size
+        if n == 0:
+            continue
+        q = [int(round(float(W[i]) * one)) for i in idx]
+        C = []
+        acc = 0
+        for v in q:
+            acc += v
+            C.append(acc)
+        C[-1] = one
+        for j in range(n):
+            thr = (j * one + int(u40[k])) // n
+            sel = next(jj for jj in range(n) if C[jj] > thr)
+            anc[idx[j]] = idx[sel]
+    return anc
+
+
+def resample_uniforms(s: SMCSettings, stage: int):
+    """u40_k for each model: the low 40 bits of (x0 << 8 | x1 >> 24)."""
+    d = draws(s.seed, s.sounding, np.arange(s.n_models), PURPOSE_RESAMPLE, stage, 0)
+    return ((d[:, 0] << np.uint64(8)) | (d[:, 1] >> np.uint64(24))) & np.uint64((1 << CDF_BITS) - 1)
+
+
+# --------------------------------------------------------------- mutate (a9)
+def sweeps_needed(p_acc_min, c_mut, r_max):
+    """R = ceil(log c / log(1 - p_acc^min)) (App. B), clamped to [1, r_max]."""
+    if p_acc_min <= 0.0:
+        return r_max
+    if p_acc_min >= 1.0:
+        return 1
+    r = math.ceil(math.log(c_mut) / math.log(1.0 - p_acc_min))
+    return max(1, min(r_max, r))
+
+
+def propose(p: Particle, s: SMCSettings, i: int, stage: int, sweep: int):
+    """One proposal for particle i.  Returns (move_index, proposal or None if the
+    move is impossible or leaves the prior support)."""
+    d0 = draws(s.seed, s.sounding, i, PURPOSE_MOVE, stage, sweep)[0]
+    d1 = draws(s.seed, s.sounding, i, PURPOSE_VALUE, stage, sweep)[0]
+    u = u01_from(np.concatenate([d0, d1]))
+    move = min(int(u[0] * 6), 5)
+    q = p.copy()
+    if move == 0:  # conductive birth: depth U(0, zmax), log10 sigma from the prior
+        if p.kappa >= s.kappa_max:
+            return move, None
+        z = s.zmax * u[1]
+        v = s.phi_lo + (s.phi_hi - s.phi_lo) * u[2]
+        j = sum(1 for zz in p.zc if zz < z)
+        q.zc.insert(j, z)
+        q.phic.insert(j, v)
+        q.kappa += 1
+    elif move == 1:  # conductive death: a uniformly chosen interface
+        if p.kappa == 0:
+            return move, None
+        j = min(int(u[1] * p.kappa), p.kappa - 1)
+        del q.zc[j]
+        del q.phic[j]
+        q.kappa -= 1
+    elif move == 2:  # chargeable birth: depth U(0, zmax), m from the prior
+        if p.lam >= s.lambda_max:
+            return move, None
+        z = s.zmax * u[1]
+        v = u[2]
+        j = sum(1 for zz in p.zm if zz < z)
+        q.zm.insert(j, z)
+        q.mv.insert(j, v)
+        q.lam += 1
+    elif move == 3:  # chargeable death
+        if p.lam == 0:
+            return move, None
+        j = min(int(u[1] * p.lam), p.lam - 1)
+        del q.zm[j]
+        del q.mv[j]
+        q.lam -= 1
+    elif move == 4:  # depth move of one interface; keeps the order within its profile
+        n_int = p.kappa + p.lam
+        if n_int == 0:
+            return move, None
+        j = min(int(u[1] * n_int), n_int - 1)
+        step = s.step_z * float(gauss_pair(d1[1], d1[2]))
+        if j < p.kappa:
+            arr, jj = q.zc, j
+        else:
+            arr, jj = q.zm, j - p.kappa
+        z = arr[jj] + step
+        lo = arr[jj - 1] if jj > 0 else 0.0
+        hi = arr[jj + 1] if jj + 1 < len(arr) else s.zmax
+        if not (lo < z < hi):
+            return move, None
+        arr[jj] = z
+    else:  # component-wise Gaussian random walk
+        n_comp = 1 + p.kappa + p.lam + 2
+        j = min(int(u[1] * n_comp), n_comp - 1)
+        g = float(gauss_pair(d1[1], d1[2]))
+        if j == 0:
+            q.phib = p.phib + s.step_phi * g
+        elif j <= p.kappa:
+            q.phic[j - 1] = p.phic[j - 1] + s.step_phi * g
+        elif j <= p.kappa + p.lam:
+            q.mv[j - 1 - p.kappa] = p.mv[j - 1 - p.kappa] + s.step_m * g
+        elif j == p.kappa + p.lam + 1:
+            if s.tau_log_prior:
+                q.tau = 10.0 ** (math.log10(p.tau) + s.step_tau * g)
+            else:
+                q.tau = p.tau + s.step_tau * g
+        else:
+            q.c = p.c + s.step_c * g
+        if not in_prior(q, s):
+            return move, None
+    return move, q
+
+
+def accept_uniform(s: SMCSettings, i: int, stage: int, sweep: int):
+    d = draws(s.seed, s.sounding, i, PURPOSE_ACCEPT, stage, sweep)[0]
+    return float(u01_53(d[0], d[1]))
+
+
+# ------------------------------------------------------------------- driver
+@dataclass
+class SMCResult:
+    gammas: list = field(default_factory=list)
+    log_z: np.ndarray = None
+    counts: np.ndarray = None
+    particles: list = None
+    ll: np.ndarray = None
+    accept: np.ndarray = None
+    proposed: np.ndarray = None
+    sweeps: list = field(default_factory=list)
+
+
+class ForwardLik:
+    """Log-likelihood of merged particles through the oracle forward model."""
+
+    def __init__(self, system, y_obs, eps_an, eps_mn, lmax, mode=None):
+        import oracle as O
+        self.O = O
+        self.system = dict(system)
+        if self.system.get("T") is None:
+            self.system["T"] = O.tmatrix(self.system["freqs"], self.system["times"])
+        self.y_obs = np.asarray(y_obs, dtype=np.float64)
+        self.eps_an = eps_an
+        self.eps_mn = eps_mn
+        self.lmax = lmax
+        self.mode = O.HANKEL_RULE if mode is None else mode
+
+    def __call__(self, parts):
+        if not parts:
+            return np.zeros(0)
+        mb = merged_batch(parts, self.lmax)
+        y = self.O.forward(mb, self.system, mode=self.mode)
+        return self.O.loglik(y, self.y_obs, self.eps_an, self.eps_mn)
+
+
+def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=propose):
+    """Algorithm 1: initialise from the prior, then reweight / resample /
+    mutate until gamma = 1.  `loglik` maps a list of particles to their
+    log-likelihoods."""
+    N = s.n_particles
+    parts = [prior(s, i) for i in range(N)]
+    ll = np.asarray(loglik(parts), dtype=np.float64)
+    gamma = 0.0
+    log_z = np.zeros(s.n_models)
+    res = SMCResult()
+    acc = np.zeros(6)
+    prop = np.zeros(6)
+    p_min = 0.0
+    for stage in range(1, max_stages + 1):
+        model = np.array([p.model(s) for p in parts])
+        dg, done, inc, W = reweight(ll, model, s.n_models, gamma, s.alpha, s.bisect_iters)
+        gamma = 1.0 if done else gamma + dg
+        log_z += inc
+        res.gammas.append(gamma)
+        anc = resample_systematic(W, model, s.n_models, resample_uniforms(s, stage))
+        parts = [parts[a].copy() for a in anc]
+        ll = ll[anc].copy()
+        R = s.n_sweeps if s.n_sweeps > 0 else (s.r_max if stage == 1 else sweeps_needed(p_min, s.c_mut, s.r_max))
+        res.sweeps.append(R)
+        acc_stage = np.zeros(6)
+        prop_stage = np.zeros(6)
+        for sweep in range(R):
+            props = [proposer(parts[i], s, i, stage, sweep) for i in range(N)]
+            live = [i for i in range(N) if props[i][1] is not None]
+            ll_new = np.full(N, -np.inf)
+            if live:
+                ll_new[live] = loglik([props[i][1] for i in live])
+            for i in range(N):
+                mv, q = props[i]
+                prop_stage[mv] += 1
+                if q is None:
+                    continue
+                u = accept_uniform(s, i, stage, sweep)
+                if math.log(u) < gamma * (ll_new[i] - ll[i]):
+                    parts[i] = q
+                    ll[i] = ll_new[i]
+                    acc_stage[mv] += 1
+        acc += acc_stage
+        prop += prop_stage
+        rates = np.where(prop_stage > 0, acc_stage / np.maximum(prop_stage, 1), 1.0)
+        p_min = float(np.min(rates))
+        if gamma >= 1.0:
+            break
+    model = np.array([p.model(s) for p in parts])
+    res.log_z = log_z
+    res.counts = np.bincount(model, minlength=s.n_models)
+    res.particles = parts
+    res.ll = ll
+    res.accept = acc
+    res.proposed = prop
+    return res
+
+
+def model_odds(counts, kappa_max, lambda_max):
+    """pi(k|y) = N_k / N and log BFIPD (Section 2.3.3) with uniform p(k):
+    B = (|M_kappa| sum_{IP} pi/p) / (|M_lambda| sum_{non-IP} pi/p) = N_IP / (lambda_max N_nonIP)."""
+    counts = np.asarray(counts, dtype=np.float64)
+    N = counts.sum()
+    post = counts / N
+    grid = counts.reshape(kappa_max + 1, lambda_max + 1)
+    n_non = grid[:, 0].sum()
+    n_ip = grid[:, 1:].sum()
+    if n_non == 0:
+        return post, math.inf
+    if n_ip == 0:
+        return post, -math.inf
+    return post, math.log(n_ip / (lambda_max * n_non))

@@ -1,0 +1,205 @@
+"""Pins for the serial RJSMC oracle (no GPU): the paper's identities
+(App. B-D), brute-force and defining properties of systematic resampling, and
+end-to-end statistics on toy problems whose evidence and model probabilities
+are known in closed form."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.stats import norm, chi2
+
+from oracle import rjsmc as R
+
+
+# ----------------------------------------------------------------- reweight
+def random_population(rng, N=400, K=6):
+    model = rng.integers(0, K, N)
+    ll = rng.normal(-50.0, 15.0, N) - 5.0 * model
+    return ll, model
+
+
+def test_tess_equals_sum_of_model_ess():
+    """App. C: TESS = sum_k ESS_k with ESS_k = 1 / sum_i W_i^2 (W normalised in model k)."""
+    rng = np.random.default_rng(1)
+    ll, model = random_population(rng)
+    for dg in (1e-4, 1e-2, 0.1, 0.7):
+        dgam, _, _, W = R.reweight(ll, model, 6, 1.0 - dg, 0.0)  # alpha = 0: the whole step dg is taken
+        assert dgam == pytest.approx(dg)
+        ess = sum(1.0 / np.sum(W[model == k] ** 2) for k in range(6) if np.any(model == k))
+        assert abs(R.tess(ll, model, 6, dg) - ess) <= 1e-9 * ess
+
+
+def test_bisection_lands_on_alpha_n():
+    rng = np.random.default_rng(2)
+    ll, model = random_population(rng)
+    N = len(ll)
+    dg, done = R.choose_dgamma(ll, model, 6, 0.0, 0.5)
+    assert not done
+    t_at = R.tess(ll, model, 6, dg)
+    assert t_at >= 0.5 * N
+    # the next representable bisection point above fails the threshold
+    assert R.tess(ll, model, 6, dg + 2.0 ** -58) < 0.5 * N + 1e-6 * N
+    # TESS falls monotonically with the tempering increment
+    grid = np.linspace(0, 1, 41)
+    vals = [R.tess(ll, model, 6, g) for g in grid]
+    assert all(a >= b - 1e-9 for a, b in zip(vals, vals[1:]))
+    # when the rest of the path keeps TESS above the threshold it is taken whole
+    dg2, done2 = R.choose_dgamma(ll * 1e-9, model, 6, 0.3, 0.5)
+    assert done2 and dg2 == pytest.approx(0.7)
+
+
+def test_weights_normalised_within_models():
+    rng = np.random.default_rng(3)
+    ll, model = random_population(rng)
+    _, _, _, W = R.reweight(ll, model, 6, 0.0, 0.5)
+    for k in range(6):
+        assert abs(W[model == k].sum() - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------- resampling
+def test_systematic_counts_are_floor_or_ceil():
+    """Systematic resampling gives every particle floor(N_k W_i) or ceil(N_k W_i)
+    copies of itself, within its own model (W taken at the 2^-40 grid)."""
+    rng = np.random.default_rng(4)
+    for trial in range(20):
+        N, K = 200, 5
+        model = rng.integers(0, K, N)
+        W = np.zeros(N)
+        for k in range(K):
+            idx = np.nonzero(model == k)[0]
+            if idx.size:
+                w = rng.exponential(1.0, idx.size) ** 3
+                W[idx] = w / w.sum()
+        u40 = rng.integers(0, 1 << 40, K, dtype=np.uint64)
+        anc = R.resample_systematic(W, model, K, u40)
+        assert np.all(model[anc] == model)
+        counts = np.bincount(anc, minlength=N)
+        for k in range(K):
+            idx = np.nonzero(model == k)[0]
+            if not idx.size:
+                continue
+            q = np.array([round(W[i] * 2.0 ** 40) for i in idx], dtype=np.float64)
+            q[-1] = 2.0 ** 40 - q[:-1].sum()
+            expect = q / 2.0 ** 40 * idx.size
+            c = counts[idx]
+            assert np.all(c >= np.floor(expect - 1e-9)) and np.all(c <= np.ceil(expect + 1e-9))
+            assert c.sum() == idx.size
+
+
+def test_systematic_matches_float_definition():
+    """Brute force against the textbook float form on cases without ties."""
+    rng = np.random.default_rng(5)
+    for trial in range(50):
+        n = int(rng.integers(1, 12))
+        W = rng.dirichlet(np.ones(n))
+        u40 = int(rng.integers(0, 1 << 40))
+        anc = R.resample_systematic(W, np.zeros(n, dtype=int), 1, np.array([u40], dtype=np.uint64))
+        U = u40 / 2.0 ** 40
+        cdf = np.cumsum(W)
+        ref = [int(np.searchsorted(cdf, (j + U) / n, side="right")) for j in range(n)]
+        ref = [min(r, n - 1) for r in ref]
+        assert list(anc) == ref
+
+
+# -------------------------------------------------------------- sweep count
+@pytest.mark.parametrize("p", [0.01, 0.05, 0.2, 0.44, 0.9])
+def test_sweeps_formula_is_the_smallest_r(p):
+    """App. B: R = ceil(log c / log(1 - p)) is the smallest R with (1-p)^R <= c."""
+    c = 0.01
+    r = R.sweeps_needed(p, c, 10 ** 6)
+    assert (1 - p) ** r <= c * (1 + 1e-12)
+    assert r == 1 or (1 - p) ** (r - 1) > c
+
+
+# ------------------------------------------------------------------- Philox
+def test_philox_uniform_statistics():
+    d = R.draws(7, 0, np.arange(1 << 14), R.PURPOSE_MOVE, 1, 0).ravel()
+    u = R.u01_from(d)
+    assert 0.0 < u.min() and u.max() < 1.0
+    hist = np.bincount((u * 64).astype(int), minlength=64)
+    stat = np.sum((hist - u.size / 64) ** 2 / (u.size / 64))
+    assert stat < chi2.ppf(0.9999, 63)
+    bits = np.unpackbits(d.astype(np.uint32).view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+    # distinct counters give distinct blocks; the key changes the stream
+    e = R.draws(8, 0, np.arange(16), R.PURPOSE_MOVE, 1, 0)
+    assert not np.array_equal(e, R.draws(7, 0, np.arange(16), R.PURPOSE_MOVE, 1, 0))
+
+
+# ---------------------------------------------------------------- merge (a1)
+def test_merge_matches_c_oracle():
+    import oracle as O
+    s = R.SMCSettings(kappa_max=5, lambda_max=5)
+    for i in range(30):
+        p = R.sample_prior(s, i)
+        L, ls, lh, m, lt, c = R.merge_particle(p, 12)
+        th, ls2, m2 = O.merge(p.zc, [p.phib] + p.phic, p.zm, p.mv)
+        assert L == len(th)
+        assert np.allclose(ls[:L], ls2) and np.allclose(m[:L], m2)
+        assert np.allclose(10 ** lh[:L - 1], th[:-1])
+
+
+# ------------------------------------------------------------------- toys
+SIG = 0.1
+Y3 = np.array([0.5, 0.3, 0.6])
+
+
+def toy_evidence_loglik(parts):
+    """y1 ~ N(phi_b, s^2), y2 ~ N(tau, s^2), y3 ~ N(c, s^2)."""
+    th = np.array([[p.phib, p.tau, p.c] for p in parts])
+    return np.sum(norm.logpdf(Y3[None, :], th, SIG), axis=1)
+
+
+def toy_log_z():
+    lo = np.array([-4.0, 0.0, 0.0])
+    hi = np.array([2.0, 1.0, 1.0])
+    return float(np.sum(np.log((norm.cdf((hi - Y3) / SIG) - norm.cdf((lo - Y3) / SIG)) / (hi - lo))))
+
+
+@pytest.mark.slow
+def test_smc_evidence_on_toy_with_closed_form():
+    """Static SMC (one model) reproduces the analytic log evidence within
+    three Monte Carlo standard errors over 12 seeds."""
+    est = []
+    for seed in range(12):
+        s = R.SMCSettings(n_particles=300, kappa_max=0, lambda_max=0, n_sweeps=8, seed=seed)
+        res = R.run(s, toy_evidence_loglik)
+        assert res.gammas[-1] == 1.0
+        est.append(res.log_z[0])
+    est = np.array(est)
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - toy_log_z()) < 3 * se + 0.02
+
+
+def toy_rj_loglik(parts):
+    """Model k = number of conductive interfaces; y ~ N(sum of the k layer values, s^2)."""
+    return np.array([norm.logpdf(1.0, sum(p.phic), 0.5) for p in parts])
+
+
+def toy_rj_posterior():
+    a, b, s, y = -4.0, 2.0, 0.5, 1.0
+    z0 = norm.pdf(y, 0.0, s)
+    z1 = (norm.cdf((b - y) / s) - norm.cdf((a - y) / s)) / (b - a)
+
+    def tri(x):
+        w = (b - a) ** 2
+        return (x - 2 * a) / w if x <= a + b else (2 * b - x) / w
+
+    z2 = integrate.quad(lambda x: tri(x) * norm.pdf(y, x, s), 2 * a, 2 * b, points=[a + b], limit=200)[0]
+    z = np.array([z0, z1, z2])
+    return z / z.sum()
+
+
+@pytest.mark.slow
+def test_rj_toy_model_probabilities():
+    """Birth/death with prior-drawn properties (App. E) targets pi(k|y) in
+    closed form: the final model counts match within Monte Carlo error."""
+    post = toy_rj_posterior()
+    freq = []
+    for seed in range(4):
+        s = R.SMCSettings(n_particles=600, kappa_max=2, lambda_max=0, n_sweeps=10, seed=seed)
+        res = R.run(s, toy_rj_loglik)
+        freq.append(res.counts / res.counts.sum())
+    freq = np.mean(freq, axis=0)
+    assert np.all(np.abs(freq - post) < 0.05), (freq, post)
