@@ -138,6 +138,137 @@ int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const do
                    const double *eps_an, double eps_mn, double *ll, double *gates, void *stream);
 
 /* ------------------------------------------------------------------------
+ * RJSMC stage (Algorithm 1 with the adaptive choices of Section 3.2 and
+ * Appendices B-E).
+ *
+ * Particle state (decoupled model of Section 2.1, priors of Section 2.3.1):
+ * kappa conductive interfaces (depths zc, log10 sigma of the layer below each,
+ * phic) under a background log10 sigma phib; lambda chargeable interfaces
+ * (depths zm, chargeability of the layer below each, mv) under m = 0; global
+ * Cole-Cole tau [s] and c.  Model index k = kappa * (lambda_max + 1) + lambda.
+ * Priors: kappa ~ U{0..kappa_max}, lambda ~ U{0..lambda_max}, depths sorted
+ * uniforms on (0, zmax), log10 sigma ~ U(phi_lo, phi_hi), m ~ U(0,1),
+ * tau ~ U(0,1) (or log10 tau ~ U(logtau_lo, logtau_hi)), c ~ U(0,1).
+ * Random numbers: Philox4x32-10 with key (seed low 32 bits, seed high 32 bits
+ * xor sounding) and counter (particle, purpose, stage, sweep).
+ * ---------------------------------------------------------------------- */
+#define AEM_SMC_SLOTS 10           /* interface slots per profile: kappa_max, lambda_max <= 9 */
+#define AEM_SMC_MAX_MODELS 100     /* (kappa_max + 1) (lambda_max + 1) */
+#define AEM_SMC_MAX_PARTICLES 16384 /* particles per sounding */
+
+typedef struct {
+    int n_particles;   /* N per sounding, 2..AEM_SMC_MAX_PARTICLES */
+    int n_soundings;   /* S >= 1; soundings are independent samplers */
+    int kappa_max;     /* 0..9 */
+    int lambda_max;    /* 0..9, kappa_max + lambda_max + 1 <= AEM_MAX_LAYERS */
+    double zmax;       /* maximum interface depth [m] */
+    double alpha;      /* TESS threshold proportion, 0 < alpha < 1 */
+    double c_mut;      /* c of App. B: R_t = ceil(log c / log(1 - p_acc_min)) */
+    int r_max;         /* upper bound on R_t */
+    double step_phi, step_m, step_tau, step_c, step_z; /* random-walk scales */
+    double phi_lo, phi_hi;                 /* log10 sigma prior bounds */
+    int tau_log_prior;                     /* 0: tau ~ U(0,1) s; 1: log10 tau ~ U(lo, hi) */
+    double logtau_lo, logtau_hi;
+    unsigned long long seed;
+    int bisect_iters;                      /* bisection iterations for gamma_t (1..200) */
+} smc_desc;
+
+typedef struct smc_state smc_state;
+
+/* Host mirror of the particle arrays (P = S * N particles, sounding-major;
+ * zc/phic/zm/mv are [P][AEM_SMC_SLOTS], entries past kappa / lambda are 0).
+ * move / valid may be NULL; they are filled only for the proposal set. */
+typedef struct {
+    int *kappa, *lam;
+    float *phib, *tau, *c, *zc, *phic, *zm, *mv;
+    double *ll;
+    int8_t *move, *valid;
+} smc_particles_host;
+
+/* Fills *d with the defaults (N = 256, kappa_max = 3, lambda_max = 4,
+ * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2)). */
+int smc_desc_defaults(smc_desc *d);
+
+/* Synchronous.  y_obs [host, S x G] observed gates per sounding; eps_an [host, G];
+ * eps_mn multiplicative noise.  All later calls run on `stream`. */
+int smc_create(const aem_system *sys, const smc_desc *desc, const double *y_obs, const double *eps_an,
+               double eps_mn, void *stream, smc_state **out);
+int smc_destroy(smc_state *st);
+
+/* Draws every particle from the prior and evaluates its log-likelihood
+ * (Alg. 1 initialisation; gamma_0 = 0, Z_0 = 1). */
+int smc_init(smc_state *st);
+
+/* Re-weight (a7): gamma_t by bisection so that TESS = sum_k ESS_k ~ alpha N
+ * (the whole remaining step when that keeps TESS >= alpha N), log Z_k +=
+ * log(mean_i L_i^(gamma_t - gamma_{t-1})) over model k, normalised weights
+ * within each model.  FP64 throughout.  Advances the stage counter.  If
+ * gamma_out is not NULL the new gamma of every sounding is copied to it
+ * (synchronising the stream). */
+int smc_reweight(smc_state *st, double *gamma_out);
+
+/* Resample (a8): within-model systematic resampling (N_k kept fixed) on an
+ * integer CDF (q = round(W 2^40), last entry forced to 2^40), one uniform
+ * per model and stage. */
+int smc_resample(smc_state *st);
+
+/* Mutate (a9): n_sweeps sweeps (n_sweeps <= 0: R_t of App. B from the
+ * previous stage's lowest move-type acceptance rate, r_max on the first
+ * stage).  Each sweep proposes one move per particle, chosen uniformly among
+ * conductive birth, conductive death, chargeable birth, chargeable death,
+ * depth move and Gaussian random walk (impossible moves count as rejected),
+ * evaluates the proposals through the FP32 forward model and accepts with
+ * probability min(1, exp(gamma_t (l' - l))).  Synchronises at the end. */
+int smc_mutate(smc_state *st, int n_sweeps);
+
+/* Proposal step only (for inspection): proposals for (stage, sweep) from the
+ * current particles into the proposal set, without likelihood evaluation. */
+int smc_propose(smc_state *st, int stage, int sweep);
+
+/* Re-evaluates the log-likelihood of the current particles. */
+int smc_loglik_current(smc_state *st);
+
+/* Runs reweight / resample / mutate until gamma = 1 for every sounding or
+ * max_stages stages (Alg. 1).  stages_out may be NULL. */
+int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
+
+/* Synchronous (a10).  post_k [S x M]: N_k / N; log_bfipd [S]: log of the
+ * BFIPD statistic of Section 2.3.3 with uniform p(k), i.e.
+ * log(N_IP / (lambda_max N_nonIP)), +inf when no particle is non-chargeable;
+ * log_z_k [S x M]: accumulated log Z_k.  Any pointer may be NULL. */
+int smc_model_odds(const smc_state *st, double *post_k, double *log_bfipd, double *log_z_k);
+
+/* Synchronous.  gamma [S], stage, accepted / proposed [S x 6] counts of the
+ * last smc_mutate call by move type.  Any pointer may be NULL. */
+int smc_stats(const smc_state *st, double *gamma, int *stage, int *accepted, int *proposed);
+
+/* Synchronous copies of the particle arrays: which = 0 current, 1 proposals. */
+int smc_get_particles(const smc_state *st, int which, smc_particles_host *h);
+/* Synchronous.  Replaces the current particles (and, when not NULL / >= 0,
+ * gamma [S], log_z [S x M] and the stage counter). */
+int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *gamma, const double *log_z,
+                      int stage);
+
+/* Standalone single-sounding forms of a7 and a8 on caller buffers
+ * ([device] pointers; `work` is a [device] scratch buffer of at least
+ * aem_smc_workspace_bytes(n, n_models) bytes, 64-byte aligned, owned by the
+ * caller and overwritten). */
+size_t aem_smc_workspace_bytes(int n, int n_models);
+/* ll [n], model [n] (0..n_models-1): outputs dgamma [1], reached_one [1],
+ * logz_inc [n_models] (0 for empty models) and W [n] normalised within each
+ * model, for the step from gamma_prev. */
+int aem_reweight(const double *ll, const int *model, int n, int n_models, double gamma_prev, double alpha,
+                 int bisect_iters, double *dgamma, int *reached_one, double *logz_inc, double *W, void *work,
+                 size_t work_bytes, void *stream);
+/* W [n] normalised within each model, model [n], u40 [n_models] integers in
+ * [0, 2^40): ancestor [n] of every particle (bit-exact integer arithmetic). */
+int aem_resample_systematic(const double *W, const int *model, int n, int n_models, const unsigned long long *u40,
+                            int *ancestor, void *work, size_t work_bytes, void *stream);
+/* Philox4x32-10 of n counters [device, n x 4] under key (key0, key1). */
+int aem_philox4x32(const unsigned int *counters, unsigned int key0, unsigned int key1, unsigned int *out, int n,
+                   void *stream);
+
+/* ------------------------------------------------------------------------
  * Device throughput probes used for the roofline denominators: FP32 FMA and
  * MUFU (ex2/sin/cos/rsqrt/rcp) operation rates measured by dependency-free
  * loops on every SM.  Synchronous.  Results in operations per second.

@@ -226,7 +226,9 @@ def merge_particle(p: Particle, lmax: int):
         logsig[n] = p.phib if ic == 0 else p.phic[ic - 1]
         m[n] = 0.0 if jm == 0 else p.mv[jm - 1]
         if n < L - 1:
-            logh[n] = math.log10(z[n] - top)
+            # coincident conductive and chargeable interfaces leave a
+            # zero-thickness merged layer (thickness floored at 1e-30 m)
+            logh[n] = math.log10(max(z[n] - top, 1e-30))
     return L, logsig, logh, m, np.full(lmax, math.log10(p.tau)), np.full(lmax, p.c)
 
 

@@ -45,6 +45,36 @@ class Models(ctypes.Structure):
     ]
 
 
+class SMCDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_particles", c_int),
+        ("n_soundings", c_int),
+        ("kappa_max", c_int),
+        ("lambda_max", c_int),
+        ("zmax", c_double),
+        ("alpha", c_double),
+        ("c_mut", c_double),
+        ("r_max", c_int),
+        ("step_phi", c_double),
+        ("step_m", c_double),
+        ("step_tau", c_double),
+        ("step_c", c_double),
+        ("step_z", c_double),
+        ("phi_lo", c_double),
+        ("phi_hi", c_double),
+        ("tau_log_prior", c_int),
+        ("logtau_lo", c_double),
+        ("logtau_hi", c_double),
+        ("seed", ctypes.c_ulonglong),
+        ("bisect_iters", c_int),
+    ]
+
+
+class ParticlesHost(ctypes.Structure):
+    _fields_ = [(n, c_void_p) for n in ("kappa", "lam", "phib", "tau", "c", "zc", "phic", "zm", "mv", "ll", "move",
+                                          "valid")]
+
+
 # Every symbol include/aem_rjsmc.h declares, with its ctypes signature.
 SIGNATURES = {
     "aem_last_error": ([], ctypes.c_char_p),
@@ -58,6 +88,27 @@ SIGNATURES = {
     "aem_loglik_f64": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                         c_void_p], c_int),
     "aem_probe_peaks": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "smc_desc_defaults": ([ctypes.POINTER(SMCDesc)], c_int),
+    "smc_create": ([c_void_p, ctypes.POINTER(SMCDesc), c_void_p, c_void_p, c_double, c_void_p,
+                    ctypes.POINTER(c_void_p)], c_int),
+    "smc_destroy": ([c_void_p], c_int),
+    "smc_init": ([c_void_p], c_int),
+    "smc_reweight": ([c_void_p, c_void_p], c_int),
+    "smc_resample": ([c_void_p], c_int),
+    "smc_mutate": ([c_void_p, c_int], c_int),
+    "smc_propose": ([c_void_p, c_int, c_int], c_int),
+    "smc_loglik_current": ([c_void_p], c_int),
+    "smc_run": ([c_void_p, c_int, c_int, c_void_p], c_int),
+    "smc_model_odds": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "smc_stats": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "smc_get_particles": ([c_void_p, c_int, ctypes.POINTER(ParticlesHost)], c_int),
+    "smc_set_particles": ([c_void_p, ctypes.POINTER(ParticlesHost), c_void_p, c_void_p, c_int], c_int),
+    "aem_smc_workspace_bytes": ([c_int, c_int], ctypes.c_size_t),
+    "aem_reweight": ([c_void_p, c_void_p, c_int, c_int, c_double, c_double, c_int, c_void_p, c_void_p, c_void_p,
+                      c_void_p, c_void_p, ctypes.c_size_t, c_void_p], c_int),
+    "aem_resample_systematic": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                 c_void_p], c_int),
+    "aem_philox4x32": ([c_void_p, ctypes.c_uint, ctypes.c_uint, c_void_p, c_int, c_void_p], c_int),
 }
 
 

@@ -44,4 +44,9 @@ struct aem_system {
 namespace aem {
 // Builds the Hankel rule and the transform matrix on the host (system.cpp).
 int build_tables(const aem_system_desc *desc, SystemTables *out);
+// FP32 forward + log-likelihood where consecutive blocks of
+// models_per_sounding models use consecutive rows of y_obs (forward.cu).
+int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                         int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
+                         cudaStream_t stream);
 }  // namespace aem

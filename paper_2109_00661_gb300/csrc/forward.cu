@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                                                            const typename Ops::R *__restrict__ g_T,
                                                            typename Ops::R *__restrict__ gates_out,
                                                            typename Ops::R *__restrict__ imh_out,
-                                                           const double *__restrict__ y_obs,
+                                                           const double *__restrict__ y_obs, int obs_per,
                                                            const double *__restrict__ eps_an, double eps_mn,
                                                            double *__restrict__ ll_out) {
     using R = typename Ops::R;
@@ -286,7 +286,9 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                 double yh = (double)acc;
                 double ea = eps_an[tid];
                 double v = ea * ea + (eps_mn * yh) * (eps_mn * yh);
-                double rr = y_obs[tid] - yh;
+                // models [s*obs_per, (s+1)*obs_per) share sounding s's data
+                const double *yo = y_obs + (obs_per > 0 ? (size_t)(p / obs_per) * G : 0);
+                double rr = yo[tid] - yh;
                 term = rr * rr / v + log(2.0 * kPi * v);
             }
         }
@@ -316,7 +318,7 @@ size_t smem_bytes(int F, int G, int K) {
 
 template <class Ops, class Models>
 int launch_forward(const aem_system *sys, const Models *models, typename Ops::R *gates, typename Ops::R *imh,
-                   const double *y_obs, const double *eps_an, double eps_mn, double *ll, void *stream,
+                   const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream,
                    const typename Ops::R *omega, const typename Ops::R *lam, const typename Ops::R *hw,
                    const typename Ops::R *T, const char *name) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
@@ -339,7 +341,7 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
     long long grid = (long long)sys->num_sms * per_sm;
     if (grid > models->n_models) grid = models->n_models;
     kern<<<(unsigned)grid, kThreads, smem, (cudaStream_t)stream>>>(mv, h.F, h.G, h.K, h.cc_form, omega, lam, hw, T,
-                                                                   gates, imh, y_obs, eps_an, eps_mn, ll);
+                                                                   gates, imh, y_obs, obs_per, eps_an, eps_mn, ll);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -347,18 +349,28 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
 }  // namespace
 }  // namespace aem
 
+namespace aem {
+int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                         int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
+                         cudaStream_t stream) {
+    return launch_forward<FP32Ops>(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding,
+                                   eps_an, eps_mn, ll, (void *)stream, sys->d_omega_f, sys->d_lam_f, sys->d_hw_f,
+                                   sys->d_T_f, "loglik (SMC)");
+}
+}  // namespace aem
+
 using namespace aem;
 
 extern "C" int aem_forward_f32(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh,
                                void *stream) {
-    return launch_forward<FP32Ops>(sys, models, gates, imh, nullptr, nullptr, 0.0, nullptr, stream,
+    return launch_forward<FP32Ops>(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream,
                                    sys ? sys->d_omega_f : nullptr, sys ? sys->d_lam_f : nullptr,
                                    sys ? sys->d_hw_f : nullptr, sys ? sys->d_T_f : nullptr, "aem_forward_f32");
 }
 
 extern "C" int aem_forward_f64(const aem_system *sys, const aem_models_f64 *models, double *gates, double *imh,
                                void *stream) {
-    return launch_forward<FP64Ops>(sys, models, gates, imh, nullptr, nullptr, 0.0, nullptr, stream,
+    return launch_forward<FP64Ops>(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream,
                                    sys ? sys->d_omega_d : nullptr, sys ? sys->d_lam_d : nullptr,
                                    sys ? sys->d_hw_d : nullptr, sys ? sys->d_T_d : nullptr, "aem_forward_f64");
 }
@@ -366,7 +378,7 @@ extern "C" int aem_forward_f64(const aem_system *sys, const aem_models_f64 *mode
 extern "C" int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               const double *eps_an, double eps_mn, double *ll, float *gates, void *stream) {
     if (!ll && models && models->n_models > 0) return fail(AEM_ERR_INVALID_ARG, "aem_loglik_f32: ll is NULL");
-    return launch_forward<FP32Ops>(sys, models, gates, nullptr, y_obs, eps_an, eps_mn, ll, stream,
+    return launch_forward<FP32Ops>(sys, models, gates, nullptr, y_obs, 0, eps_an, eps_mn, ll, stream,
                                    sys ? sys->d_omega_f : nullptr, sys ? sys->d_lam_f : nullptr,
                                    sys ? sys->d_hw_f : nullptr, sys ? sys->d_T_f : nullptr, "aem_loglik_f32");
 }
@@ -374,7 +386,7 @@ extern "C" int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *model
 extern "C" int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
                               const double *eps_an, double eps_mn, double *ll, double *gates, void *stream) {
     if (!ll && models && models->n_models > 0) return fail(AEM_ERR_INVALID_ARG, "aem_loglik_f64: ll is NULL");
-    return launch_forward<FP64Ops>(sys, models, gates, nullptr, y_obs, eps_an, eps_mn, ll, stream,
+    return launch_forward<FP64Ops>(sys, models, gates, nullptr, y_obs, 0, eps_an, eps_mn, ll, stream,
                                    sys ? sys->d_omega_d : nullptr, sys ? sys->d_lam_d : nullptr,
                                    sys ? sys->d_hw_d : nullptr, sys ? sys->d_T_d : nullptr, "aem_loglik_f64");
 }

@@ -1,3 +1,1101 @@
-// RJSMC stage kernels (reweight with TESS bisection, within-model systematic
-// resampling, RJ mutation, model odds).  Filled in by the SMC build-out.
+// RJSMC stage on the GPU (Davies et al., arXiv 2109.00661, Algorithm 1):
+//   reweight  - per-model log-sum-exp sums in FP64, gamma_t by bisection on
+//               TESS = sum_k ESS_k (Section 3.2.1, App. C), Z_k update (App. D);
+//   resample  - within-model systematic resampling on an integer CDF;
+//   mutate    - RJMCMC sweeps: conductive / chargeable birth and death with
+//               prior-drawn properties (App. E), depth moves, component-wise
+//               Gaussian random walks, then the batched forward model and the
+//               tempered Metropolis-Hastings test;
+//   odds      - model counts, pi(k|y) = N_k / N and the BFIPD statistic.
+// Soundings are independent: per-sounding kernels run one CTA per sounding,
+// per-particle kernels one thread per particle.  Random numbers come from
+// Philox4x32-10 keyed by (seed, sounding) and counted by (particle, purpose,
+// stage, sweep), so every draw is reproducible and independent of scheduling.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
 #include "aem_internal.h"
+
+namespace aem {
+namespace {
+
+constexpr int KS = AEM_SMC_SLOTS;  // interface slots per profile
+constexpr int kMoves = 6;
+constexpr int kGroupThreads = 1024;
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kPurposeMove = 64, kPurposeValue = 65, kPurposeAccept = 66, kPurposeResample = 67;
+// Prior draw layout: draw d is word d % 4 of the block with purpose d / 4.
+constexpr int kPriorSlots = 16;
+constexpr int D_KAPPA = 0, D_LAM = 1, D_PHIB = 2, D_TAU = 3, D_C = 4, D_ZC = 5, D_PHIC = D_ZC + kPriorSlots,
+              D_ZM = D_PHIC + kPriorSlots, D_MV = D_ZM + kPriorSlots;
+constexpr int kCdfBits = 40;
+
+// ------------------------------------------------------------------ Philox
+struct Key {
+    uint32_t k0, k1;
+};
+
+__host__ __device__ inline Key stream_key(unsigned long long seed, int sounding) {
+    return {(uint32_t)(seed & 0xffffffffull), (uint32_t)((seed >> 32) ^ (unsigned long long)(uint32_t)sounding)};
+}
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC 2011).
+__host__ __device__ inline void philox(uint32_t c[4], Key key) {
+    uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ inline void block_draws(uint32_t out[4], Key key, uint32_t particle, uint32_t purpose, uint32_t stage,
+                                   uint32_t sweep) {
+    out[0] = particle;
+    out[1] = purpose;
+    out[2] = stage;
+    out[3] = sweep;
+    philox(out, key);
+}
+
+// Uniform on (0, 1): ((x >> 8) + 1/2) 2^-24, formed exactly in double.
+__device__ inline double u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * 5.9604644775390625e-08; }
+__device__ inline double u01_53(uint32_t x0, uint32_t x1) {
+    return ((double)(x0 >> 6) * 134217728.0 + (double)(x1 >> 5) + 0.5) * 1.1102230246251565e-16;
+}
+// Box-Muller, first output: sqrt(-2 ln u1) cos(2 pi u2), in double.
+__device__ inline double gauss(uint32_t x0, uint32_t x1) {
+    double u1 = u01(x0), u2 = u01(x1);
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// ---------------------------------------------------------- particle state
+struct PState {
+    int *kappa, *lam;
+    float *phib, *tau, *c, *zc, *phic, *zm, *mv;
+    double *ll;
+};
+
+struct Params {
+    int N, S, kappa_max, lambda_max, M, LMS, tau_log_prior;
+    double zmax, phi_lo, phi_hi, logtau_lo, logtau_hi, step_phi, step_m, step_tau, step_c, step_z;
+    unsigned long long seed;
+};
+
+__device__ inline void copy_particle(PState d, int i, PState s, int j) {
+    d.kappa[i] = s.kappa[j];
+    d.lam[i] = s.lam[j];
+    d.phib[i] = s.phib[j];
+    d.tau[i] = s.tau[j];
+    d.c[i] = s.c[j];
+#pragma unroll
+    for (int q = 0; q < KS; ++q) {
+        d.zc[i * KS + q] = s.zc[j * KS + q];
+        d.phic[i * KS + q] = s.phic[j * KS + q];
+        d.zm[i * KS + q] = s.zm[j * KS + q];
+        d.mv[i * KS + q] = s.mv[j * KS + q];
+    }
+    d.ll[i] = s.ll[j];
+}
+
+// Stable insertion sort of (z, v) pairs by z.
+__device__ inline void sort_pairs(double *z, double *v, int n) {
+    for (int a = 1; a < n; ++a) {
+        double kz = z[a], kv = v[a];
+        int b = a - 1;
+        while (b >= 0 && z[b] > kz) {
+            z[b + 1] = z[b];
+            v[b + 1] = v[b];
+            --b;
+        }
+        z[b + 1] = kz;
+        v[b + 1] = kv;
+    }
+}
+
+// --------------------------------------------------------------- prior draw
+__global__ void prior_kernel(PState st, Params pr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    int s = i / pr.N, j = i - s * pr.N;
+    Key key = stream_key(pr.seed, s);
+    auto draw = [&](int d) -> double {
+        uint32_t w[4];
+        block_draws(w, key, (uint32_t)j, (uint32_t)(d >> 2), 0u, 0u);
+        return u01(w[d & 3]);
+    };
+    int kappa = (int)(draw(D_KAPPA) * (pr.kappa_max + 1));
+    kappa = kappa > pr.kappa_max ? pr.kappa_max : kappa;
+    int lam = (int)(draw(D_LAM) * (pr.lambda_max + 1));
+    lam = lam > pr.lambda_max ? pr.lambda_max : lam;
+    double phib = __dadd_rn(pr.phi_lo, __dmul_rn(pr.phi_hi - pr.phi_lo, draw(D_PHIB)));
+    double tau;
+    if (pr.tau_log_prior)
+        tau = pow(10.0, __dadd_rn(pr.logtau_lo, __dmul_rn(pr.logtau_hi - pr.logtau_lo, draw(D_TAU))));
+    else
+        tau = draw(D_TAU);
+    double c = draw(D_C);
+    double zc[KS], phic[KS], zm[KS], mv[KS];
+    for (int q = 0; q < kappa; ++q) {
+        zc[q] = __dmul_rn(pr.zmax, draw(D_ZC + q));
+        phic[q] = __dadd_rn(pr.phi_lo, __dmul_rn(pr.phi_hi - pr.phi_lo, draw(D_PHIC + q)));
+    }
+    for (int q = 0; q < lam; ++q) {
+        zm[q] = __dmul_rn(pr.zmax, draw(D_ZM + q));
+        mv[q] = draw(D_MV + q);
+    }
+    sort_pairs(zc, phic, kappa);
+    sort_pairs(zm, mv, lam);
+    st.kappa[i] = kappa;
+    st.lam[i] = lam;
+    st.phib[i] = (float)phib;
+    st.tau[i] = (float)tau;
+    st.c[i] = (float)c;
+    for (int q = 0; q < KS; ++q) {
+        st.zc[i * KS + q] = q < kappa ? (float)zc[q] : 0.f;
+        st.phic[i * KS + q] = q < kappa ? (float)phic[q] : 0.f;
+        st.zm[i * KS + q] = q < lam ? (float)zm[q] : 0.f;
+        st.mv[i * KS + q] = q < lam ? (float)mv[q] : 0.f;
+    }
+    st.ll[i] = 0.0;
+}
+
+// ------------------------------------------------------------- merge (a1)
+// Direct sum of the two profiles (Section 2.1, Fig. 2): the merged
+// interfaces are the sorted union; each merged layer takes log10 sigma from
+// the conductive profile and m from the chargeable profile at its top.
+__global__ void merge_kernel(PState st, int P, int LMS, int8_t *nl, float *logsig, float *logh, float *m,
+                             float *logtau, float *cc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const int kappa = st.kappa[i], lam = st.lam[i];
+    float z[2 * KS];
+    int a = 0, b = 0, n = 0;
+    while (a < kappa || b < lam) {
+        float za = a < kappa ? st.zc[i * KS + a] : 3.0e38f;
+        float zb = b < lam ? st.zm[i * KS + b] : 3.0e38f;
+        if (za <= zb) {
+            z[n++] = za;
+            ++a;
+        } else {
+            z[n++] = zb;
+            ++b;
+        }
+    }
+    const int L = n + 1;
+    const float lt = (float)log10((double)st.tau[i]);
+    const float cv = st.c[i];
+    int ic = 0, jm = 0;
+    for (int q = 0; q < L; ++q) {
+        float top = q == 0 ? 0.f : z[q - 1];
+        if (q > 0) {
+            while (ic < kappa && st.zc[i * KS + ic] <= top) ++ic;
+            while (jm < lam && st.zm[i * KS + jm] <= top) ++jm;
+        }
+        size_t o = (size_t)i * LMS + q;
+        logsig[o] = ic == 0 ? st.phib[i] : st.phic[i * KS + ic - 1];
+        m[o] = jm == 0 ? 0.f : st.mv[i * KS + jm - 1];
+        double th = q < L - 1 ? (double)z[q] - (double)top : 1.0;
+        logh[o] = (float)log10(th > 1e-30 ? th : 1e-30);
+        logtau[o] = lt;
+        cc[o] = cv;
+    }
+    for (int q = L; q < LMS; ++q) {
+        size_t o = (size_t)i * LMS + q;
+        logsig[o] = 0.f;
+        m[o] = 0.f;
+        logh[o] = 0.f;
+        logtau[o] = lt;
+        cc[o] = cv;
+    }
+    nl[i] = (int8_t)L;
+}
+
+// ------------------------------------------------ grouping by model (stable)
+// One CTA per sounding: counts N_k, offsets and the particle indices of each
+// model in increasing index order (warp per model, ballot scans).
+__global__ void __launch_bounds__(kGroupThreads) group_kernel(const int *kappa, const int *lam, int N, int lp1,
+                                                              int M, int *perm, int *off, int *counts) {
+    extern __shared__ unsigned char mid[];
+    __shared__ int s_cnt[AEM_SMC_MAX_MODELS];
+    __shared__ int s_off[AEM_SMC_MAX_MODELS + 1];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int base = s * N;
+    for (int j = tid; j < N; j += blockDim.x) mid[j] = (unsigned char)(kappa[base + j] * lp1 + lam[base + j]);
+    __syncthreads();
+    for (int k = warp; k < M; k += nw) {
+        int cnt = 0;
+        for (int b0 = 0; b0 < N; b0 += 32) {
+            int j = b0 + lane;
+            cnt += __popc(__ballot_sync(kFullMask, j < N && mid[j] == k));
+        }
+        if (lane == 0) s_cnt[k] = cnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_off[0] = 0;
+        for (int k = 0; k < M; ++k) s_off[k + 1] = s_off[k] + s_cnt[k];
+    }
+    __syncthreads();
+    for (int k = warp; k < M; k += nw) {
+        int pos = s_off[k];
+        for (int b0 = 0; b0 < N; b0 += 32) {
+            int j = b0 + lane;
+            bool p = j < N && mid[j] == k;
+            unsigned bal = __ballot_sync(kFullMask, p);
+            if (p) perm[base + pos + __popc(bal & ((1u << lane) - 1u))] = base + j;
+            pos += __popc(bal);
+        }
+    }
+    for (int k = tid; k < M; k += blockDim.x) counts[s * M + k] = s_cnt[k];
+    for (int k = tid; k <= M; k += blockDim.x) off[s * (M + 1) + k] = s_off[k];
+}
+
+template <class T>
+__device__ inline T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+
+__device__ inline double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFullMask, v, o));
+    return v;
+}
+
+// -------------------------------------------------------------- reweight (a7)
+// One CTA per sounding.  With W uniform within each model after the last
+// resample, a_i = dgamma * ll_i, S1_k = sum e^{a_i - a_max}, S2_k = sum e^{2(a_i - a_max)},
+// ESS_k = S1^2 / S2 and TESS = sum_k ESS_k.  gamma_t by bisection on TESS = alpha N.
+__global__ void __launch_bounds__(kGroupThreads)
+    reweight_kernel(const double *ll, const int *perm, const int *off, const int *counts, int N, int M, double alpha,
+                    int iters, double *gamma, double *logz, double *Wg, double *dgamma_out, int *done_out) {
+    __shared__ double s_max[AEM_SMC_MAX_MODELS], s_s1[AEM_SMC_MAX_MODELS], s_ess[AEM_SMC_MAX_MODELS];
+    __shared__ double s_tess;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int *o = off + s * (M + 1);
+    const int *cnt = counts + s * M;
+    const double g0 = gamma[s];
+    if (g0 >= 1.0) {
+        if (tid == 0) {
+            dgamma_out[s] = 0.0;
+            done_out[s] = 1;
+        }
+        return;
+    }
+    for (int k = warp; k < M; k += nw) {
+        double mx = -INFINITY;
+        for (int r = lane; r < cnt[k]; r += 32) mx = fmax(mx, ll[perm[s * N + o[k] + r]]);
+        mx = warp_max(mx);
+        if (lane == 0) s_max[k] = mx;
+    }
+    __syncthreads();
+    auto evaluate = [&](double dg) {
+        for (int k = warp; k < M; k += nw) {
+            double s1 = 0.0, s2 = 0.0;
+            const double mk = s_max[k];
+            for (int r = lane; r < cnt[k]; r += 32) {
+                double v = ll[perm[s * N + o[k] + r]];
+                double e = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk));
+                s1 += e;
+                s2 += e * e;
+            }
+            s1 = warp_sum_t(s1);
+            s2 = warp_sum_t(s2);
+            if (lane == 0) {
+                s_s1[k] = s1;
+                s_ess[k] = (cnt[k] > 0 && s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double t = 0.0;
+            for (int k = lane; k < M; k += 32) t += s_ess[k];
+            t = warp_sum_t(t);
+            if (lane == 0) s_tess = t;
+        }
+        __syncthreads();
+        return s_tess;
+    };
+    const double target = alpha * (double)N;
+    double hi = 1.0 - g0, dg;
+    int done;
+    if (evaluate(hi) >= target) {
+        dg = hi;
+        done = 1;
+    } else {
+        double lo = 0.0;
+        for (int it = 0; it < iters; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (evaluate(mid) >= target)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        dg = lo > 0.0 ? lo : hi;
+        done = 0;
+        evaluate(dg);
+    }
+    for (int k = warp; k < M; k += nw) {
+        const int n = cnt[k];
+        if (n == 0) continue;
+        const double mk = s_max[k], s1 = s_s1[k];
+        for (int r = lane; r < n; r += 32) {
+            double v = ll[perm[s * N + o[k] + r]];
+            Wg[s * N + o[k] + r] = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk)) / s1;
+        }
+        if (lane == 0) logz[s * M + k] += dg * mk + log(s1) - log((double)n);
+    }
+    if (tid == 0) {
+        gamma[s] = done ? 1.0 : g0 + dg;
+        dgamma_out[s] = dg;
+        done_out[s] = done;
+    }
+}
+
+// ------------------------------------------------------------- resample (a8)
+// One CTA per sounding, warp per model.  q_r = round(W_r 2^40), C = prefix
+// sums with the last entry forced to 2^40; output slot j takes the smallest r
+// with C_r > floor((j 2^40 + u40_k) / N_k).
+__global__ void __launch_bounds__(kGroupThreads)
+    resample_kernel(const double *Wg, const int *perm, const int *off, const int *counts, int N, int M,
+                    const unsigned long long *u40_in, unsigned long long seed, int stage, unsigned long long *C,
+                    int *anc) {
+    const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int *o = off + s * (M + 1);
+    const int *cnt = counts + s * M;
+    const unsigned long long one = 1ull << kCdfBits;
+    for (int k = warp; k < M; k += nw) {
+        const int n = cnt[k];
+        if (n == 0) continue;
+        const int b = s * N + o[k];
+        unsigned long long u40;
+        if (u40_in) {
+            u40 = u40_in[s * M + k];
+        } else {
+            uint32_t w[4];
+            block_draws(w, stream_key(seed, s), (uint32_t)k, (uint32_t)kPurposeResample, (uint32_t)stage, 0u);
+            u40 = (((unsigned long long)w[0] << 8) | (unsigned long long)(w[1] >> 24)) & (one - 1ull);
+        }
+        unsigned long long carry = 0;
+        for (int r0 = 0; r0 < n; r0 += 32) {
+            int r = r0 + lane;
+            unsigned long long q = r < n ? (unsigned long long)__double2ll_rn(Wg[b + r] * (double)one) : 0ull;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned long long t = __shfl_up_sync(kFullMask, q, d);
+                if (lane >= d) q += t;
+            }
+            if (r < n) C[b + r] = carry + q;
+            carry += __shfl_sync(kFullMask, q, 31);
+        }
+        __syncwarp();
+        if (lane == 0) C[b + n - 1] = one;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            unsigned long long thr = ((unsigned long long)j * one + u40) / (unsigned long long)n;
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (C[b + mid] > thr)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            anc[perm[b + j]] = perm[b + lo];
+        }
+    }
+}
+
+__global__ void gather_kernel(PState dst, PState src, const int *anc, int P) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) copy_particle(dst, i, src, anc[i]);
+}
+
+// ---------------------------------------------------------- RJ proposal (a9)
+__device__ inline bool in_bounds_open(double v, double lo, double hi) { return lo < v && v < hi; }
+
+__global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage,
+                               int sweep) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    const int s = i / pr.N, j = i - s * pr.N;
+    const Key key = stream_key(pr.seed, s);
+    uint32_t d0[4], d1[4];
+    block_draws(d0, key, (uint32_t)j, (uint32_t)kPurposeMove, (uint32_t)stage, (uint32_t)sweep);
+    block_draws(d1, key, (uint32_t)j, (uint32_t)kPurposeValue, (uint32_t)stage, (uint32_t)sweep);
+    const double u0 = u01(d0[0]), u1 = u01(d0[1]), u2 = u01(d0[2]);
+    int move = (int)(u0 * 6.0);
+    move = move > 5 ? 5 : move;
+    copy_particle(prop, i, cur, i);
+    int kappa = cur.kappa[i], lam = cur.lam[i];
+    bool ok = true;
+    if (move == 0 || move == 2) {  // birth: depth U(0, zmax), property from the prior
+        const bool cond = move == 0;
+        const int n = cond ? kappa : lam;
+        if (n >= (cond ? pr.kappa_max : pr.lambda_max)) {
+            ok = false;
+        } else {
+            float *zz = cond ? prop.zc : prop.zm;
+            float *vv = cond ? prop.phic : prop.mv;
+            const double z = __dmul_rn(pr.zmax, u1);
+            const double v = cond ? __dadd_rn(pr.phi_lo, __dmul_rn(pr.phi_hi - pr.phi_lo, u2)) : u2;
+            int at = 0;
+            while (at < n && (double)zz[i * KS + at] < z) ++at;
+            for (int q = n; q > at; --q) {
+                zz[i * KS + q] = zz[i * KS + q - 1];
+                vv[i * KS + q] = vv[i * KS + q - 1];
+            }
+            zz[i * KS + at] = (float)z;
+            vv[i * KS + at] = (float)v;
+            if (cond)
+                prop.kappa[i] = kappa + 1;
+            else
+                prop.lam[i] = lam + 1;
+        }
+    } else if (move == 1 || move == 3) {  // death of a uniformly chosen interface
+        const bool cond = move == 1;
+        const int n = cond ? kappa : lam;
+        if (n == 0) {
+            ok = false;
+        } else {
+            int at = (int)(u1 * n);
+            at = at > n - 1 ? n - 1 : at;
+            float *zz = cond ? prop.zc : prop.zm;
+            float *vv = cond ? prop.phic : prop.mv;
+            for (int q = at; q < n - 1; ++q) {
+                zz[i * KS + q] = zz[i * KS + q + 1];
+                vv[i * KS + q] = vv[i * KS + q + 1];
+            }
+            zz[i * KS + n - 1] = 0.f;
+            vv[i * KS + n - 1] = 0.f;
+            if (cond)
+                prop.kappa[i] = kappa - 1;
+            else
+                prop.lam[i] = lam - 1;
+        }
+    } else if (move == 4) {  // depth move, order kept within the profile
+        const int nint = kappa + lam;
+        if (nint == 0) {
+            ok = false;
+        } else {
+            int at = (int)(u1 * nint);
+            at = at > nint - 1 ? nint - 1 : at;
+            const double step = pr.step_z * gauss(d1[1], d1[2]);
+            float *zz = at < kappa ? prop.zc : prop.zm;
+            const int n = at < kappa ? kappa : lam;
+            const int q = at < kappa ? at : at - kappa;
+            const double z = (double)zz[i * KS + q] + step;
+            const double lo = q > 0 ? (double)zz[i * KS + q - 1] : 0.0;
+            const double hi = q + 1 < n ? (double)zz[i * KS + q + 1] : pr.zmax;
+            if (!(lo < z && z < hi))
+                ok = false;
+            else
+                zz[i * KS + q] = (float)z;
+        }
+    } else {  // component-wise Gaussian random walk
+        const int ncomp = 1 + kappa + lam + 2;
+        int at = (int)(u1 * ncomp);
+        at = at > ncomp - 1 ? ncomp - 1 : at;
+        const double g = gauss(d1[1], d1[2]);
+        if (at == 0) {
+            double v = (double)cur.phib[i] + pr.step_phi * g;
+            ok = in_bounds_open(v, pr.phi_lo, pr.phi_hi);
+            prop.phib[i] = (float)v;
+        } else if (at <= kappa) {
+            double v = (double)cur.phic[i * KS + at - 1] + pr.step_phi * g;
+            ok = in_bounds_open(v, pr.phi_lo, pr.phi_hi);
+            prop.phic[i * KS + at - 1] = (float)v;
+        } else if (at <= kappa + lam) {
+            double v = (double)cur.mv[i * KS + at - 1 - kappa] + pr.step_m * g;
+            ok = in_bounds_open(v, 0.0, 1.0);
+            prop.mv[i * KS + at - 1 - kappa] = (float)v;
+        } else if (at == kappa + lam + 1) {
+            double v;
+            if (pr.tau_log_prior) {
+                double lt = log10((double)cur.tau[i]) + pr.step_tau * g;
+                ok = in_bounds_open(lt, pr.logtau_lo, pr.logtau_hi);
+                v = pow(10.0, lt);
+            } else {
+                v = (double)cur.tau[i] + pr.step_tau * g;
+                ok = in_bounds_open(v, 0.0, 1.0);
+            }
+            prop.tau[i] = (float)v;
+        } else {
+            double v = (double)cur.c[i] + pr.step_c * g;
+            ok = in_bounds_open(v, 0.0, 1.0);
+            prop.c[i] = (float)v;
+        }
+    }
+    if (!ok) copy_particle(prop, i, cur, i);
+    move_out[i] = (int8_t)move;
+    valid_out[i] = ok ? 1 : 0;
+}
+
+// Tempered Metropolis-Hastings test: accept when ln u < gamma_t (l' - l).
+// With prior-drawn birth properties and uniform move selection the prior and
+// proposal ratios cancel (App. E), and the random walks are symmetric inside
+// the uniform prior support.
+__global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const int8_t *valid, const double *gamma,
+                              Params pr, int stage, int sweep, int *acc, int *nprop) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    const int s = i / pr.N, j = i - s * pr.N;
+    const int mv = move[i];
+    atomicAdd(&nprop[s * kMoves + mv], 1);
+    if (!valid[i]) return;
+    uint32_t w[4];
+    block_draws(w, stream_key(pr.seed, s), (uint32_t)j, (uint32_t)kPurposeAccept, (uint32_t)stage, (uint32_t)sweep);
+    const double u = u01_53(w[0], w[1]);
+    const double dl = prop.ll[i] - cur.ll[i];
+    if (log(u) < gamma[s] * dl) {
+        copy_particle(cur, i, prop, i);
+        atomicAdd(&acc[s * kMoves + mv], 1);
+    }
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox(c, Key{k0, k1});
+    for (int q = 0; q < 4; ++q) out[4 * i + q] = c[q];
+}
+
+// Model ids from a plain int array (the standalone reweight / resample entry
+// points take the model of each particle directly).
+__global__ void split_model_kernel(const int *model, int n, int lp1, int *kappa, int *lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        kappa[i] = model[i] / lp1;
+        lam[i] = model[i] - (model[i] / lp1) * lp1;
+    }
+}
+
+__global__ void scatter_kernel(const double *Wg, const int *perm, int n, double *W) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) W[perm[i]] = Wg[i];
+}
+
+__global__ void gather_weights_kernel(const double *W, const int *perm, int n, double *Wg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Wg[i] = W[perm[i]];
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace aem
+
+// ========================================================================
+// Host side
+// ========================================================================
+using namespace aem;
+
+struct smc_state {
+    const aem_system *sys = nullptr;
+    smc_desc d{};
+    Params pr{};
+    int S = 0, N = 0, P = 0, M = 0, LMS = 0;
+    cudaStream_t stream = nullptr;
+    PState cur{}, alt{}, prop{};
+    std::vector<void *> allocs;
+    int8_t *move = nullptr, *valid = nullptr;
+    int *anc = nullptr, *perm = nullptr, *off = nullptr, *counts = nullptr, *acc = nullptr, *nprop = nullptr,
+        *done = nullptr;
+    double *Wg = nullptr, *gamma = nullptr, *logz = nullptr, *dgamma = nullptr;
+    unsigned long long *C = nullptr;
+    int8_t *m_nl = nullptr;
+    float *m_logsig = nullptr, *m_logh = nullptr, *m_m = nullptr, *m_logtau = nullptr, *m_c = nullptr;
+    double *y = nullptr, *eps_an = nullptr;
+    double eps_mn = 0.0;
+    int stage = 0;
+    std::vector<int> acc_prev, nprop_prev;
+    bool have_prev = false;
+};
+
+namespace {
+
+template <class T>
+int dalloc(smc_state *st, T **p, size_t n) {
+    void *q = nullptr;
+    AEM_CUDA_TRY(cudaMalloc(&q, n * sizeof(T) + 16));
+    st->allocs.push_back(q);
+    *p = (T *)q;
+    return AEM_OK;
+}
+
+int alloc_pstate(smc_state *st, PState *ps) {
+    const size_t P = st->P;
+    int rc;
+    if ((rc = dalloc(st, &ps->kappa, P)) || (rc = dalloc(st, &ps->lam, P)) || (rc = dalloc(st, &ps->phib, P)) ||
+        (rc = dalloc(st, &ps->tau, P)) || (rc = dalloc(st, &ps->c, P)) || (rc = dalloc(st, &ps->zc, P * KS)) ||
+        (rc = dalloc(st, &ps->phic, P * KS)) || (rc = dalloc(st, &ps->zm, P * KS)) ||
+        (rc = dalloc(st, &ps->mv, P * KS)) || (rc = dalloc(st, &ps->ll, P)))
+        return rc;
+    return AEM_OK;
+}
+
+int run_loglik(smc_state *st, PState ps) {
+    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
+                                                                st->m_logh, st->m_m, st->m_logtau, st->m_c);
+    AEM_CUDA_TRY(cudaGetLastError());
+    aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
+    return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream);
+}
+
+int check_desc(const smc_desc *d) {
+    if (!d) return fail(AEM_ERR_INVALID_ARG, "smc_create: desc is NULL");
+    if (d->n_particles < 2 || d->n_particles > AEM_SMC_MAX_PARTICLES)
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: n_particles outside 2..AEM_SMC_MAX_PARTICLES");
+    if (d->n_soundings < 1) return fail(AEM_ERR_INVALID_ARG, "smc_create: n_soundings < 1");
+    if (d->kappa_max < 0 || d->lambda_max < 0 || d->kappa_max >= AEM_SMC_SLOTS || d->lambda_max >= AEM_SMC_SLOTS ||
+        d->kappa_max + d->lambda_max + 1 > AEM_MAX_LAYERS)
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: kappa_max / lambda_max out of range");
+    if ((d->kappa_max + 1) * (d->lambda_max + 1) > AEM_SMC_MAX_MODELS)
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: too many models");
+    if (!(d->zmax > 0) || !(d->alpha > 0 && d->alpha < 1) || !(d->c_mut > 0 && d->c_mut < 1) || d->r_max < 1 ||
+        !(d->phi_hi > d->phi_lo) || d->bisect_iters < 1 || d->bisect_iters > 200)
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid zmax / alpha / c_mut / r_max / prior bounds");
+    if (d->tau_log_prior && !(d->logtau_hi > d->logtau_lo))
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid log10 tau bounds");
+    return AEM_OK;
+}
+
+}  // namespace
+
+extern "C" int smc_desc_defaults(smc_desc *d) {
+    if (!d) return fail(AEM_ERR_INVALID_ARG, "smc_desc_defaults: NULL");
+    *d = smc_desc{};
+    d->n_particles = 256;
+    d->n_soundings = 1;
+    d->kappa_max = 3;
+    d->lambda_max = 4;
+    d->zmax = 500.0;
+    d->alpha = 0.5;
+    d->c_mut = 0.01;
+    d->r_max = 10;
+    d->step_phi = 0.2;
+    d->step_m = 0.05;
+    d->step_tau = 0.05;
+    d->step_c = 0.05;
+    d->step_z = 10.0;
+    d->phi_lo = -4.0;
+    d->phi_hi = 2.0;
+    d->tau_log_prior = 0;
+    d->logtau_lo = -6.0;
+    d->logtau_hi = -1.0;
+    d->seed = 0;
+    d->bisect_iters = 60;
+    return AEM_OK;
+}
+
+extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const double *y_obs, const double *eps_an,
+                          double eps_mn, void *stream, smc_state **out) {
+    if (!out) return fail(AEM_ERR_INVALID_ARG, "smc_create: out is NULL");
+    *out = nullptr;
+    if (!sys || !y_obs || !eps_an) return fail(AEM_ERR_INVALID_ARG, "smc_create: NULL system or data");
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    smc_state *st = new smc_state();
+    st->sys = sys;
+    st->d = *desc;
+    st->S = desc->n_soundings;
+    st->N = desc->n_particles;
+    st->P = st->S * st->N;
+    st->M = (desc->kappa_max + 1) * (desc->lambda_max + 1);
+    st->LMS = desc->kappa_max + desc->lambda_max + 1;
+    st->stream = (cudaStream_t)stream;
+    st->eps_mn = eps_mn;
+    Params &p = st->pr;
+    p.N = st->N;
+    p.S = st->S;
+    p.kappa_max = desc->kappa_max;
+    p.lambda_max = desc->lambda_max;
+    p.M = st->M;
+    p.LMS = st->LMS;
+    p.tau_log_prior = desc->tau_log_prior;
+    p.zmax = desc->zmax;
+    p.phi_lo = desc->phi_lo;
+    p.phi_hi = desc->phi_hi;
+    p.logtau_lo = desc->logtau_lo;
+    p.logtau_hi = desc->logtau_hi;
+    p.step_phi = desc->step_phi;
+    p.step_m = desc->step_m;
+    p.step_tau = desc->step_tau;
+    p.step_c = desc->step_c;
+    p.step_z = desc->step_z;
+    p.seed = desc->seed;
+    const int G = sys->host.G;
+    const size_t P = st->P;
+    if ((rc = alloc_pstate(st, &st->cur)) || (rc = alloc_pstate(st, &st->alt)) || (rc = alloc_pstate(st, &st->prop)) ||
+        (rc = dalloc(st, &st->move, P)) || (rc = dalloc(st, &st->valid, P)) || (rc = dalloc(st, &st->anc, P)) ||
+        (rc = dalloc(st, &st->perm, P)) || (rc = dalloc(st, &st->off, (size_t)st->S * (st->M + 1))) ||
+        (rc = dalloc(st, &st->counts, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->acc, (size_t)st->S * kMoves)) ||
+        (rc = dalloc(st, &st->nprop, (size_t)st->S * kMoves)) || (rc = dalloc(st, &st->done, (size_t)st->S)) ||
+        (rc = dalloc(st, &st->Wg, P)) || (rc = dalloc(st, &st->gamma, (size_t)st->S)) ||
+        (rc = dalloc(st, &st->logz, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->dgamma, (size_t)st->S)) ||
+        (rc = dalloc(st, &st->C, P)) || (rc = dalloc(st, &st->m_nl, P)) ||
+        (rc = dalloc(st, &st->m_logsig, P * st->LMS)) || (rc = dalloc(st, &st->m_logh, P * st->LMS)) ||
+        (rc = dalloc(st, &st->m_m, P * st->LMS)) || (rc = dalloc(st, &st->m_logtau, P * st->LMS)) ||
+        (rc = dalloc(st, &st->m_c, P * st->LMS)) || (rc = dalloc(st, &st->y, (size_t)st->S * G)) ||
+        (rc = dalloc(st, &st->eps_an, (size_t)G))) {
+        smc_destroy(st);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(st->y, y_obs, sizeof(double) * st->S * G, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(st->eps_an, eps_an, sizeof(double) * G, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        smc_destroy(st);
+        return cuda_fail(e, "smc_create: upload data");
+    }
+    *out = st;
+    return AEM_OK;
+}
+
+extern "C" int smc_destroy(smc_state *st) {
+    if (!st) return AEM_OK;
+    for (void *q : st->allocs) cudaFree(q);
+    delete st;
+    return AEM_OK;
+}
+
+extern "C" int smc_init(smc_state *st) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_init: NULL state");
+    prior_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->pr);
+    AEM_CUDA_TRY(cudaGetLastError());
+    AEM_CUDA_TRY(cudaMemsetAsync(st->gamma, 0, sizeof(double) * st->S, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->logz, 0, sizeof(double) * st->S * st->M, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, st->stream));
+    st->stage = 0;
+    st->have_prev = false;
+    return run_loglik(st, st->cur);
+}
+
+static int launch_group(smc_state *st) {
+    group_kernel<<<st->S, kGroupThreads, st->N, st->stream>>>(st->cur.kappa, st->cur.lam, st->N,
+                                                              st->d.lambda_max + 1, st->M, st->perm, st->off,
+                                                              st->counts);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+extern "C" int smc_reweight(smc_state *st, double *gamma_out) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_reweight: NULL state");
+    int rc = launch_group(st);
+    if (rc) return rc;
+    st->stage += 1;
+    reweight_kernel<<<st->S, kGroupThreads, 0, st->stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
+                                                             st->d.alpha, st->d.bisect_iters, st->gamma, st->logz,
+                                                             st->Wg, st->dgamma, st->done);
+    AEM_CUDA_TRY(cudaGetLastError());
+    if (gamma_out) {
+        AEM_CUDA_TRY(cudaMemcpyAsync(gamma_out, st->gamma, sizeof(double) * st->S, cudaMemcpyDeviceToHost, st->stream));
+        AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    }
+    return AEM_OK;
+}
+
+extern "C" int smc_resample(smc_state *st) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_resample: NULL state");
+    resample_kernel<<<st->S, kGroupThreads, 0, st->stream>>>(st->Wg, st->perm, st->off, st->counts, st->N, st->M,
+                                                             nullptr, st->d.seed, st->stage, st->C, st->anc);
+    AEM_CUDA_TRY(cudaGetLastError());
+    gather_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->alt, st->cur, st->anc, st->P);
+    AEM_CUDA_TRY(cudaGetLastError());
+    PState t = st->cur;
+    st->cur = st->alt;
+    st->alt = t;
+    return AEM_OK;
+}
+
+extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_propose: NULL state");
+    propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid, st->pr,
+                                                                    stage, sweep);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+static int sweeps_for_stage(smc_state *st, int n_sweeps, int *R) {
+    if (n_sweeps > 0) {
+        *R = n_sweeps;
+        return AEM_OK;
+    }
+    if (!st->have_prev) {
+        *R = st->d.r_max;
+        return AEM_OK;
+    }
+    // App. B: R = ceil(log c / log(1 - p_min)) from the previous stage's
+    // acceptance rates (the first sounding's; soundings share R).
+    double pmin = 1.0;
+    for (int m = 0; m < kMoves; ++m) {
+        int np = st->nprop_prev[m];
+        double r = np > 0 ? (double)st->acc_prev[m] / np : 1.0;
+        pmin = r < pmin ? r : pmin;
+    }
+    int r;
+    if (pmin <= 0.0)
+        r = st->d.r_max;
+    else if (pmin >= 1.0)
+        r = 1;
+    else
+        r = (int)std::ceil(std::log(st->d.c_mut) / std::log(1.0 - pmin));
+    *R = r < 1 ? 1 : (r > st->d.r_max ? st->d.r_max : r);
+    return AEM_OK;
+}
+
+extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_mutate: NULL state");
+    int R = 0, rc;
+    if ((rc = sweeps_for_stage(st, n_sweeps, &R))) return rc;
+    AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, st->stream));
+    for (int sw = 0; sw < R; ++sw) {
+        if ((rc = smc_propose(st, st->stage, sw))) return rc;
+        if ((rc = run_loglik(st, st->prop))) return rc;
+        accept_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid,
+                                                                      st->gamma, st->pr, st->stage, sw, st->acc,
+                                                                      st->nprop);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
+    st->acc_prev.assign(st->S * kMoves, 0);
+    st->nprop_prev.assign(st->S * kMoves, 0);
+    AEM_CUDA_TRY(cudaMemcpyAsync(st->acc_prev.data(), st->acc, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost,
+                                 st->stream));
+    AEM_CUDA_TRY(cudaMemcpyAsync(st->nprop_prev.data(), st->nprop, sizeof(int) * st->S * kMoves,
+                                 cudaMemcpyDeviceToHost, st->stream));
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    st->have_prev = true;
+    return AEM_OK;
+}
+
+extern "C" int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_run: NULL state");
+    std::vector<double> g(st->S);
+    int rc, t = 0;
+    for (; t < max_stages; ++t) {
+        if ((rc = smc_reweight(st, g.data()))) return rc;
+        if ((rc = smc_resample(st))) return rc;
+        if ((rc = smc_mutate(st, n_sweeps))) return rc;
+        bool all = true;
+        for (double v : g) all = all && v >= 1.0;
+        if (all) {
+            ++t;
+            break;
+        }
+    }
+    if (stages_out) *stages_out = t;
+    return AEM_OK;
+}
+
+extern "C" int smc_model_odds(const smc_state *cst, double *post_k, double *log_bfipd, double *log_z_k) {
+    smc_state *st = const_cast<smc_state *>(cst);
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_model_odds: NULL state");
+    int rc = launch_group(st);
+    if (rc) return rc;
+    std::vector<int> cnt(st->S * st->M);
+    AEM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), st->counts, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st->stream));
+    if (log_z_k)
+        AEM_CUDA_TRY(cudaMemcpyAsync(log_z_k, st->logz, sizeof(double) * st->S * st->M, cudaMemcpyDeviceToHost,
+                                     st->stream));
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    const int L1 = st->d.lambda_max + 1;
+    for (int s = 0; s < st->S; ++s) {
+        double n_ip = 0, n_non = 0;
+        for (int k = 0; k < st->M; ++k) {
+            double v = cnt[s * st->M + k];
+            if (post_k) post_k[s * st->M + k] = v / st->N;
+            if (k % L1 == 0)
+                n_non += v;
+            else
+                n_ip += v;
+        }
+        if (log_bfipd) {
+            // B = (|M_kappa| sum_IP pi/p) / (|M_lambda| sum_nonIP pi/p) with uniform p(k)
+            if (n_non == 0)
+                log_bfipd[s] = INFINITY;
+            else if (n_ip == 0 || st->d.lambda_max == 0)
+                log_bfipd[s] = -INFINITY;
+            else
+                log_bfipd[s] = std::log(n_ip / (st->d.lambda_max * n_non));
+        }
+    }
+    return AEM_OK;
+}
+
+extern "C" int smc_stats(const smc_state *st, double *gamma, int *stage, int *accepted, int *proposed) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_stats: NULL state");
+    if (gamma) AEM_CUDA_TRY(cudaMemcpy(gamma, st->gamma, sizeof(double) * st->S, cudaMemcpyDeviceToHost));
+    if (stage) *stage = st->stage;
+    if (accepted) AEM_CUDA_TRY(cudaMemcpy(accepted, st->acc, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost));
+    if (proposed) AEM_CUDA_TRY(cudaMemcpy(proposed, st->nprop, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost));
+    return AEM_OK;
+}
+
+static PState pick(smc_state *st, int which) { return which == 1 ? st->prop : st->cur; }
+
+extern "C" int smc_get_particles(const smc_state *cst, int which, smc_particles_host *h) {
+    smc_state *st = const_cast<smc_state *>(cst);
+    if (!st || !h) return fail(AEM_ERR_INVALID_ARG, "smc_get_particles: NULL argument");
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    PState p = pick(st, which);
+    const size_t P = st->P;
+    AEM_CUDA_TRY(cudaMemcpy(h->kappa, p.kappa, sizeof(int) * P, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->lam, p.lam, sizeof(int) * P, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->phib, p.phib, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->tau, p.tau, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->c, p.c, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->zc, p.zc, sizeof(float) * P * KS, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->phic, p.phic, sizeof(float) * P * KS, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->zm, p.zm, sizeof(float) * P * KS, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->mv, p.mv, sizeof(float) * P * KS, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(h->ll, p.ll, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (h->move && which == 1) AEM_CUDA_TRY(cudaMemcpy(h->move, st->move, P, cudaMemcpyDeviceToHost));
+    if (h->valid && which == 1) AEM_CUDA_TRY(cudaMemcpy(h->valid, st->valid, P, cudaMemcpyDeviceToHost));
+    return AEM_OK;
+}
+
+extern "C" int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *gamma, const double *log_z,
+                                 int stage) {
+    if (!st || !h) return fail(AEM_ERR_INVALID_ARG, "smc_set_particles: NULL argument");
+    const size_t P = st->P;
+    PState p = st->cur;
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    AEM_CUDA_TRY(cudaMemcpy(p.kappa, h->kappa, sizeof(int) * P, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.lam, h->lam, sizeof(int) * P, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.phib, h->phib, sizeof(float) * P, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.tau, h->tau, sizeof(float) * P, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.c, h->c, sizeof(float) * P, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.zc, h->zc, sizeof(float) * P * KS, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.phic, h->phic, sizeof(float) * P * KS, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.zm, h->zm, sizeof(float) * P * KS, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.mv, h->mv, sizeof(float) * P * KS, cudaMemcpyHostToDevice));
+    AEM_CUDA_TRY(cudaMemcpy(p.ll, h->ll, sizeof(double) * P, cudaMemcpyHostToDevice));
+    if (gamma) AEM_CUDA_TRY(cudaMemcpy(st->gamma, gamma, sizeof(double) * st->S, cudaMemcpyHostToDevice));
+    if (log_z) AEM_CUDA_TRY(cudaMemcpy(st->logz, log_z, sizeof(double) * st->S * st->M, cudaMemcpyHostToDevice));
+    if (stage >= 0) st->stage = stage;
+    return AEM_OK;
+}
+
+extern "C" int smc_loglik_current(smc_state *st) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_loglik_current: NULL state");
+    return run_loglik(st, st->cur);
+}
+
+// ----------------------------------------------------- standalone entries
+extern "C" size_t aem_smc_workspace_bytes(int n, int n_models) {
+    if (n < 0 || n_models < 1) return 0;
+    size_t b = 0;
+    b += sizeof(int) * 2 * (size_t)n;                 // kappa, lam split of the model ids
+    b += sizeof(int) * (size_t)n;                     // perm
+    b += sizeof(int) * (size_t)(2 * n_models + 1);    // off, counts
+    b += sizeof(double) * (size_t)n;                  // grouped weights
+    b += sizeof(unsigned long long) * (size_t)n;      // integer CDF
+    b += sizeof(double) + sizeof(int) + 64 * 8;       // gamma, done, alignment slack
+    return b;
+}
+
+namespace {
+struct Workspace {
+    int *kappa, *lam, *perm, *off, *counts, *done;
+    double *Wg, *gamma;
+    unsigned long long *C;
+};
+
+Workspace carve(void *base, int n, int M) {
+    auto align = [](size_t v) { return (v + 63) & ~(size_t)63; };
+    char *p = (char *)base;
+    size_t o = 0;
+    Workspace w;
+    w.Wg = (double *)(p + o);
+    o = align(o + sizeof(double) * n);
+    w.C = (unsigned long long *)(p + o);
+    o = align(o + sizeof(unsigned long long) * n);
+    w.gamma = (double *)(p + o);
+    o = align(o + sizeof(double));
+    w.kappa = (int *)(p + o);
+    o = align(o + sizeof(int) * n);
+    w.lam = (int *)(p + o);
+    o = align(o + sizeof(int) * n);
+    w.perm = (int *)(p + o);
+    o = align(o + sizeof(int) * n);
+    w.off = (int *)(p + o);
+    o = align(o + sizeof(int) * (M + 1));
+    w.counts = (int *)(p + o);
+    o = align(o + sizeof(int) * M);
+    w.done = (int *)(p + o);
+    return w;
+}
+
+int check_standalone(int n, int n_models, const void *work, size_t bytes, const char *name) {
+    if (n < 1 || n > AEM_SMC_MAX_PARTICLES || n_models < 1 || n_models > AEM_SMC_MAX_MODELS)
+        return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n or n_models out of range");
+    if (!work || bytes < aem_smc_workspace_bytes(n, n_models) || ((uintptr_t)work & 63))
+        return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": workspace missing, too small or not 64-byte aligned");
+    return AEM_OK;
+}
+}  // namespace
+
+extern "C" int aem_reweight(const double *ll, const int *model, int n, int n_models, double gamma_prev, double alpha,
+                            int bisect_iters, double *dgamma, int *reached_one, double *logz_inc, double *W, void *work,
+                            size_t work_bytes, void *stream) {
+    int rc = check_standalone(n, n_models, work, work_bytes, "aem_reweight");
+    if (rc) return rc;
+    if (!ll || !model || !dgamma || !reached_one || !logz_inc || !W || !(alpha > 0 && alpha < 1) ||
+        !(gamma_prev >= 0 && gamma_prev < 1) || bisect_iters < 1 || bisect_iters > 200)
+        return fail(AEM_ERR_INVALID_ARG, "aem_reweight: NULL pointer or value out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace w = carve(work, n, n_models);
+    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, 1, w.kappa, w.lam);
+    group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
+    AEM_CUDA_TRY(cudaMemcpyAsync(w.gamma, &gamma_prev, sizeof(double), cudaMemcpyHostToDevice, s));
+    AEM_CUDA_TRY(cudaMemsetAsync(logz_inc, 0, sizeof(double) * n_models, s));
+    reweight_kernel<<<1, kGroupThreads, 0, s>>>(ll, w.perm, w.off, w.counts, n, n_models, alpha, bisect_iters,
+                                                w.gamma, logz_inc, w.Wg, dgamma, reached_one);
+    scatter_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.Wg, w.perm, n, W);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+extern "C" int aem_resample_systematic(const double *W, const int *model, int n, int n_models,
+                                       const unsigned long long *u40, int *ancestor, void *work, size_t work_bytes,
+                                       void *stream) {
+    int rc = check_standalone(n, n_models, work, work_bytes, "aem_resample_systematic");
+    if (rc) return rc;
+    if (!W || !model || !u40 || !ancestor) return fail(AEM_ERR_INVALID_ARG, "aem_resample_systematic: NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace w = carve(work, n, n_models);
+    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, 1, w.kappa, w.lam);
+    group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
+    gather_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(W, w.perm, n, w.Wg);
+    resample_kernel<<<1, kGroupThreads, 0, s>>>(w.Wg, w.perm, w.off, w.counts, n, n_models, u40, 0ull, 0, w.C,
+                                                ancestor);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+extern "C" int aem_philox4x32(const unsigned int *counters, unsigned int key0, unsigned int key1, unsigned int *out,
+                              int n, void *stream) {
+    if (n < 0 || (n > 0 && (!counters || !out))) return fail(AEM_ERR_INVALID_ARG, "aem_philox4x32: bad arguments");
+    if (n == 0) return AEM_OK;
+    philox_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(counters, key0, key1, out, n);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}

@@ -1,0 +1,188 @@
+"""Binding of the RJSMC stage entry points (smc_* and the standalone a7/a8
+kernels of include/aem_rjsmc.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import AEMError, check
+
+SLOTS = 10
+MOVES = ("sigma_birth", "sigma_death", "m_birth", "m_death", "depth", "perturb")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise AEMError("paper_2109_00661_gb300 needs a CUDA device; there is no CPU path")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def desc_defaults(**kw):
+    d = _lib.SMCDesc()
+    check(_lib.load().smc_desc_defaults(ctypes.byref(d)), "smc_desc_defaults")
+    for k, v in kw.items():
+        if not hasattr(d, k):
+            raise AEMError(f"unknown smc_desc field {k}")
+        setattr(d, k, v)
+    return d
+
+
+class Particles:
+    """Host copy of a particle set (numpy arrays)."""
+
+    FIELDS = (("kappa", np.int32, 1), ("lam", np.int32, 1), ("phib", np.float32, 1), ("tau", np.float32, 1),
+              ("c", np.float32, 1), ("zc", np.float32, SLOTS), ("phic", np.float32, SLOTS),
+              ("zm", np.float32, SLOTS), ("mv", np.float32, SLOTS), ("ll", np.float64, 1))
+
+    def __init__(self, P):
+        for name, dt, w in self.FIELDS:
+            setattr(self, name, np.zeros((P, w) if w > 1 else P, dtype=dt))
+        self.move = np.zeros(P, dtype=np.int8)
+        self.valid = np.zeros(P, dtype=np.int8)
+
+    def struct(self):
+        return _lib.ParticlesHost(*[getattr(self, n).ctypes.data for n, _, _ in self.FIELDS],
+                                  self.move.ctypes.data, self.valid.ctypes.data)
+
+
+class SMC:
+    """smc_state: RJSMC over S independent soundings of N particles each."""
+
+    def __init__(self, system, y_obs, eps_an, eps_mn, stream=None, **desc):
+        torch = _torch()
+        lib = _lib.load()
+        self.desc = desc_defaults(**desc)
+        self.S, self.N = self.desc.n_soundings, self.desc.n_particles
+        self.P = self.S * self.N
+        self.M = (self.desc.kappa_max + 1) * (self.desc.lambda_max + 1)
+        y = np.ascontiguousarray(np.broadcast_to(np.asarray(y_obs, dtype=np.float64), (self.S, system.G)))
+        ea = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_an, dtype=np.float64), (system.G,)))
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.smc_create(system.handle, ctypes.byref(self.desc), y.ctypes.data, ea.ctypes.data, float(eps_mn),
+                             ctypes.c_void_p(self._stream_obj.cuda_stream), ctypes.byref(h)), "smc_create")
+        self._h = h
+        self.system = system
+
+    def init(self):
+        check(_lib.load().smc_init(self._h), "smc_init")
+
+    def reweight(self):
+        g = np.zeros(self.S)
+        check(_lib.load().smc_reweight(self._h, g.ctypes.data), "smc_reweight")
+        return g
+
+    def resample(self):
+        check(_lib.load().smc_resample(self._h), "smc_resample")
+
+    def mutate(self, n_sweeps=0):
+        check(_lib.load().smc_mutate(self._h, int(n_sweeps)), "smc_mutate")
+
+    def propose(self, stage, sweep):
+        check(_lib.load().smc_propose(self._h, int(stage), int(sweep)), "smc_propose")
+
+    def loglik_current(self):
+        check(_lib.load().smc_loglik_current(self._h), "smc_loglik_current")
+
+    def run(self, max_stages=1000, n_sweeps=0):
+        t = ctypes.c_int()
+        check(_lib.load().smc_run(self._h, int(max_stages), int(n_sweeps), ctypes.byref(t)), "smc_run")
+        return t.value
+
+    def model_odds(self):
+        post = np.zeros((self.S, self.M))
+        lb = np.zeros(self.S)
+        lz = np.zeros((self.S, self.M))
+        check(_lib.load().smc_model_odds(self._h, post.ctypes.data, lb.ctypes.data, lz.ctypes.data), "smc_model_odds")
+        return post, lb, lz
+
+    def stats(self):
+        g = np.zeros(self.S)
+        st = ctypes.c_int()
+        acc = np.zeros((self.S, 6), dtype=np.int32)
+        prop = np.zeros((self.S, 6), dtype=np.int32)
+        check(_lib.load().smc_stats(self._h, g.ctypes.data, ctypes.byref(st), acc.ctypes.data, prop.ctypes.data),
+              "smc_stats")
+        return dict(gamma=g, stage=st.value, accepted=acc, proposed=prop)
+
+    def get_particles(self, which=0):
+        p = Particles(self.P)
+        s = p.struct()
+        check(_lib.load().smc_get_particles(self._h, int(which), ctypes.byref(s)), "smc_get_particles")
+        return p
+
+    def set_particles(self, p, gamma=None, log_z=None, stage=-1):
+        s = p.struct()
+        g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+        lz = None if log_z is None else np.ascontiguousarray(log_z, dtype=np.float64)
+        check(_lib.load().smc_set_particles(self._h, ctypes.byref(s), None if g is None else g.ctypes.data,
+                                            None if lz is None else lz.ctypes.data, int(stage)), "smc_set_particles")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().smc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _workspace(n, n_models, device):
+    torch = _torch()
+    nbytes = int(_lib.load().aem_smc_workspace_bytes(int(n), int(n_models)))
+    return torch.empty(nbytes + 64, dtype=torch.uint8, device=device), nbytes
+
+
+def _aligned(buf):
+    p = buf.data_ptr()
+    return p + ((64 - p % 64) % 64)
+
+
+def reweight(ll, model, n_models, gamma_prev, alpha, bisect_iters=60, stream=None):
+    """aem_reweight on device tensors: returns (dgamma, reached_one, logz_inc[n_models], W[n])."""
+    torch = _torch()
+    n = ll.numel()
+    dev = ll.device
+    ws, nbytes = _workspace(n, n_models, dev)
+    dg = torch.empty(1, dtype=torch.float64, device=dev)
+    done = torch.empty(1, dtype=torch.int32, device=dev)
+    inc = torch.empty(n_models, dtype=torch.float64, device=dev)
+    W = torch.empty(n, dtype=torch.float64, device=dev)
+    check(_lib.load().aem_reweight(ll.data_ptr(), model.data_ptr(), n, n_models, float(gamma_prev), float(alpha),
+                                   int(bisect_iters), dg.data_ptr(), done.data_ptr(), inc.data_ptr(), W.data_ptr(),
+                                   _aligned(ws), nbytes, _stream(stream)), "aem_reweight")
+    return dg, done, inc, W
+
+
+def resample_systematic(W, model, n_models, u40, stream=None):
+    """aem_resample_systematic on device tensors: ancestor index of every particle."""
+    torch = _torch()
+    n = W.numel()
+    ws, nbytes = _workspace(n, n_models, W.device)
+    anc = torch.empty(n, dtype=torch.int32, device=W.device)
+    check(_lib.load().aem_resample_systematic(W.data_ptr(), model.data_ptr(), n, n_models, u40.data_ptr(),
+                                              anc.data_ptr(), _aligned(ws), nbytes, _stream(stream)),
+          "aem_resample_systematic")
+    return anc
+
+
+def philox4x32(counters, key0, key1, stream=None):
+    """aem_philox4x32 on a device tensor of (n, 4) int32 counters (uint32 bit patterns)."""
+    torch = _torch()
+    n = counters.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=counters.device)
+    check(_lib.load().aem_philox4x32(counters.data_ptr(), int(key0), int(key1), out.data_ptr(), n, _stream(stream)),
+          "aem_philox4x32")
+    return out

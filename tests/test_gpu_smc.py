@@ -1,0 +1,248 @@
+"""Parity of the CUDA RJSMC stage (through the C ABI) with the serial oracle:
+bit-exact Philox streams and resampling, reweighting to rounding, identical
+prior draws and proposals given the same state, and statistical agreement of
+the model odds over independent runs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import rjsmc as R
+from paper_2109_00661_gb300 import inputs as I
+from parity_util import bound32, kappa, loglik_bound, oracle_system
+
+pytestmark = pytest.mark.gpu
+
+NAME = "sounding-g20-f40-k120"
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2109_00661_gb300 as lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2109_00661_gb300 import smc
+    return smc
+
+
+@pytest.fixture(scope="module")
+def gsys(L):
+    return L.System(**I.system_kwargs(NAME))
+
+
+@pytest.fixture(scope="module")
+def data():
+    s = oracle_system(NAME)
+    y_true = O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0]
+    return I.noisy(y_true, seed=0)
+
+
+def test_philox_bit_exact(torch, S):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, (1000, 4), dtype=np.uint64)
+    ctr[:10] = 0
+    for key in [(0, 0), (123456789, 987654321), (2 ** 32 - 1, 7)]:
+        ref = R.philox4x32(ctr, key)
+        got = S.philox4x32(torch.as_tensor(ctr.astype(np.uint32).view(np.int32), device="cuda"), *key)
+        got = got.cpu().numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got, ref)
+
+
+def population(seed, N, K, spread=15.0):
+    rng = np.random.default_rng(seed)
+    model = rng.integers(0, K, N)
+    model[: K // 3] = 0  # some models may be empty, model 0 never is
+    ll = rng.normal(-40.0, spread, N) - 3.0 * model
+    return ll, model
+
+
+@pytest.mark.parametrize("case", [(0, 256, 20, 0.0), (1, 4096, 100, 0.3), (2, 1000, 7, 0.9), (3, 64, 1, 0.0)])
+def test_reweight_matches_oracle(torch, S, case):
+    seed, N, K, g0 = case
+    ll, model = population(seed, N, K)
+    dg, done, inc, W = S.reweight(torch.as_tensor(ll, device="cuda"),
+                                  torch.as_tensor(model.astype(np.int32), device="cuda"), K, g0, 0.5)
+    dg_ref, done_ref, inc_ref, W_ref = R.reweight(ll, model, K, g0, 0.5)
+    assert int(done.item()) == int(done_ref)
+    assert abs(dg.item() - dg_ref) <= 1e-10 * max(dg_ref, 1e-300) + 1e-15
+    present = np.bincount(model, minlength=K) > 0
+    assert np.allclose(inc.cpu().numpy()[present], inc_ref[present], rtol=1e-9, atol=1e-9)
+    assert np.allclose(W.cpu().numpy(), W_ref, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", [(0, 300, 9), (1, 4096, 100), (2, 17, 3), (3, 1, 1)])
+def test_resample_bit_exact(torch, S, case):
+    seed, N, K = case
+    rng = np.random.default_rng(seed)
+    model = rng.integers(0, K, N)
+    W = np.zeros(N)
+    for k in range(K):
+        idx = np.nonzero(model == k)[0]
+        if idx.size:
+            w = rng.exponential(1.0, idx.size) ** 4
+            W[idx] = w / w.sum()
+    u40 = rng.integers(0, 1 << 40, K, dtype=np.uint64)
+    ref = R.resample_systematic(W, model, K, u40)
+    got = S.resample_systematic(torch.as_tensor(W, device="cuda"), torch.as_tensor(model.astype(np.int32), device="cuda"),
+                                K, torch.as_tensor(u40.astype(np.int64), device="cuda"))
+    assert np.array_equal(got.cpu().numpy(), ref)
+
+
+def settings(**kw):
+    base = dict(n_particles=128, kappa_max=3, lambda_max=4, n_sweeps=10, seed=11)
+    base.update(kw)
+    return R.SMCSettings(**base)
+
+
+def gpu_smc(S, gsys, data, st: R.SMCSettings, soundings=1):
+    return S.SMC(gsys, np.tile(data, (soundings, 1)), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles,
+                 n_soundings=soundings, kappa_max=st.kappa_max, lambda_max=st.lambda_max, zmax=st.zmax,
+                 seed=st.seed, r_max=st.r_max)
+
+
+def to_oracle(p, i):
+    k, l = int(p.kappa[i]), int(p.lam[i])
+    f = lambda v: float(np.float64(v))
+    return R.Particle(k, l, f(p.phib[i]), [f(v) for v in p.zc[i, :k]], [f(v) for v in p.phic[i, :k]],
+                      [f(v) for v in p.zm[i, :l]], [f(v) for v in p.mv[i, :l]], f(p.tau[i]), f(p.c[i]))
+
+
+def test_prior_draws_match_oracle(S, gsys, data):
+    st = settings()
+    sm = gpu_smc(S, gsys, data, st)
+    sm.init()
+    p = sm.get_particles(0)
+    for i in range(st.n_particles):
+        ref = R.sample_prior(st, i)
+        assert (int(p.kappa[i]), int(p.lam[i])) == (ref.kappa, ref.lam)
+        f32 = lambda v: np.float32(v)
+        assert p.phib[i] == f32(ref.phib) and p.tau[i] == f32(ref.tau) and p.c[i] == f32(ref.c)
+        assert np.array_equal(p.zc[i, :ref.kappa], np.float32(ref.zc))
+        assert np.array_equal(p.phic[i, :ref.kappa], np.float32(ref.phic))
+        assert np.array_equal(p.zm[i, :ref.lam], np.float32(ref.zm))
+        assert np.array_equal(p.mv[i, :ref.lam], np.float32(ref.mv))
+
+
+def test_prior_loglik_matches_oracle(S, gsys, data):
+    st = settings()
+    sm = gpu_smc(S, gsys, data, st)
+    sm.init()
+    p = sm.get_particles(0)
+    parts = [to_oracle(p, i) for i in range(st.n_particles)]
+    mb = R.merged_batch(parts, st.kappa_max + st.lambda_max + 1)
+    s = oracle_system(NAME)
+    y, imh = O.forward(mb, s, mode=O.HANKEL_RULE, want_imh=True)
+    ll_ref = O.loglik(y, data, I.EPS_AN, I.EPS_MN)
+    bound = loglik_bound(y, data, bound32(kappa(imh, s["T"], y), s["T"].shape[1]))
+    assert np.all(np.abs(p.ll - ll_ref) <= bound + 1e-9 * np.abs(ll_ref))
+
+
+@pytest.mark.parametrize("stage,sweep", [(1, 0), (3, 7), (12, 2)])
+def test_proposals_match_oracle(S, gsys, data, stage, sweep):
+    st = settings(n_particles=512)
+    sm = gpu_smc(S, gsys, data, st)
+    sm.init()
+    sm.propose(stage, sweep)
+    cur = sm.get_particles(0)
+    prop = sm.get_particles(1)
+    moves = np.zeros(6, dtype=int)
+    for i in range(st.n_particles):
+        mv, q = R.propose(to_oracle(cur, i), st, i, stage, sweep)
+        moves[mv] += 1
+        assert prop.move[i] == mv
+        assert bool(prop.valid[i]) == (q is not None)
+        if q is None:
+            continue
+        assert (int(prop.kappa[i]), int(prop.lam[i])) == (q.kappa, q.lam)
+        got = np.concatenate([[prop.phib[i], prop.tau[i], prop.c[i]], prop.zc[i, :q.kappa], prop.phic[i, :q.kappa],
+                              prop.zm[i, :q.lam], prop.mv[i, :q.lam]]).astype(np.float64)
+        ref = np.concatenate([[q.phib, q.tau, q.c], q.zc, q.phic, q.zm, q.mv]).astype(np.float32).astype(np.float64)
+        assert np.allclose(got, ref, rtol=2e-7, atol=1e-30), (i, mv, got, ref)
+    assert np.all(moves > 0)
+
+
+def test_stage_reweight_through_state_api(S, gsys, data):
+    """smc_reweight on the sampler's own particles equals the oracle step on
+    the same log-likelihoods and model ids."""
+    st = settings(n_particles=1024)
+    sm = gpu_smc(S, gsys, data, st)
+    sm.init()
+    p = sm.get_particles(0)
+    model = p.kappa * (st.lambda_max + 1) + p.lam
+    g = sm.reweight()
+    dg_ref, done_ref, inc_ref, _ = R.reweight(p.ll, model, st.n_models, 0.0, 0.5)
+    assert abs(g[0] - (1.0 if done_ref else dg_ref)) <= 1e-10 * max(dg_ref, 1e-300)
+    _, _, lz = sm.model_odds()
+    present = np.bincount(model, minlength=st.n_models) > 0
+    assert np.allclose(lz[0][present], inc_ref[present], rtol=1e-9, atol=1e-9)
+
+
+def test_model_odds_consistent_with_counts(S, gsys, data):
+    st = settings(n_particles=256)
+    sm = gpu_smc(S, gsys, data, st, soundings=3)
+    sm.init()
+    post, lb, _ = sm.model_odds()
+    p = sm.get_particles(0)
+    for s in range(3):
+        sl = slice(s * 256, (s + 1) * 256)
+        model = p.kappa[sl] * (st.lambda_max + 1) + p.lam[sl]
+        counts = np.bincount(model, minlength=st.n_models)
+        assert np.allclose(post[s], counts / 256)
+        ref_post, ref_lb = R.model_odds(counts, st.kappa_max, st.lambda_max)
+        assert lb[s] == pytest.approx(ref_lb)
+    # soundings draw from independent streams
+    assert not np.array_equal(p.kappa[:256], p.kappa[256:512])
+
+
+def run_gpu(S, gsys, data, seed, N=256):
+    st = settings(n_particles=N, seed=seed)
+    sm = gpu_smc(S, gsys, data, st)
+    sm.init()
+    stages = sm.run(max_stages=200, n_sweeps=10)
+    post, lb, lz = sm.model_odds()
+    info = sm.stats()
+    return stages, post[0], lb[0], info
+
+
+def test_full_rjsmc_reaches_gamma_one(S, gsys, data):
+    stages, post, lb, info = run_gpu(S, gsys, data, seed=3)
+    assert info["gamma"][0] == 1.0
+    assert 1 < stages < 200
+    assert abs(post.sum() - 1.0) < 1e-12
+    assert info["proposed"][0].sum() == 256 * 10
+
+
+@pytest.mark.slow
+def test_model_odds_statistical_parity(S, gsys, data):
+    """Mean log BFIPD and the chargeable-model probability of the GPU sampler
+    agree with the serial oracle within 3 pooled standard errors over
+    independent seeds (trajectories diverge after the first floating-point
+    difference, so only the statistics can be compared)."""
+    gpu_lb, gpu_ip = [], []
+    for seed in range(12):
+        _, post, lb, _ = run_gpu(S, gsys, data, seed=100 + seed)
+        gpu_lb.append(lb)
+        gpu_ip.append(post.reshape(4, 5)[:, 1:].sum())
+    s = oracle_system(NAME)
+    lik = R.ForwardLik(s, data, I.EPS_AN, I.EPS_MN, lmax=8)
+    orc_lb, orc_ip = [], []
+    for seed in range(5):
+        res = R.run(settings(n_particles=256, seed=200 + seed), lik)
+        post, lb = R.model_odds(res.counts, 3, 4)
+        orc_lb.append(lb)
+        orc_ip.append(post.reshape(4, 5)[:, 1:].sum())
+    for g, o in ((gpu_ip, orc_ip), (np.clip(gpu_lb, -20, 20), np.clip(orc_lb, -20, 20))):
+        g, o = np.asarray(g), np.asarray(o)
+        se = math.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
+        print(f"\ngpu mean {g.mean():.3f} sd {g.std():.3f} | oracle mean {o.mean():.3f} sd {o.std():.3f} | se {se:.3f}")
+        assert abs(g.mean() - o.mean()) <= 3 * se + 0.02
