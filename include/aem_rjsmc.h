@@ -264,6 +264,27 @@ int aem_reweight(const double *ll, const int *model, int n, int n_models, double
  * [0, 2^40): ancestor [n] of every particle (bit-exact integer arithmetic). */
 int aem_resample_systematic(const double *W, const int *model, int n, int n_models, const unsigned long long *u40,
                             int *ancestor, void *work, size_t work_bytes, void *stream);
+/* Resampling without any allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc or pass a workspace, e.g. code that
+ * runs inside a host framework which owns all device memory through its own
+ * pre-planned pool, or a latency-critical loop where an allocation (and the
+ * device synchronisation it can cause) is not allowed.  Same inputs, outputs
+ * and bit-exact result as aem_resample_systematic, but the scratch lives in a
+ * fixed static device array of 512 KiB that every GPU loading the library
+ * holds until the process exits.  Limits: n <= AEM_NOALLOC_MAX_PARTICLES,
+ * n_models <= AEM_NOALLOC_MAX_MODELS; larger problems return
+ * AEM_ERR_INVALID_ARG.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, which allocates nothing); make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that may overlap on the GPU (different streams, or different host
+ * threads on one device) race and must be serialised by the caller.  The
+ * array keeps the last call's contents; every word a call reads is written
+ * earlier in the same call, so no clearing is needed.  Calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
+#define AEM_NOALLOC_MAX_PARTICLES 16384
+#define AEM_NOALLOC_MAX_MODELS 100
+int aem_resample_systematic_noalloc(const double *W, const int *model, int n, int n_models,
+                                    const unsigned long long *u40, int *ancestor, void *stream);
 /* Philox4x32-10 of n counters [device, n x 4] under key (key0, key1). */
 int aem_philox4x32(const unsigned int *counters, unsigned int key0, unsigned int key1, unsigned int *out, int n,
                    void *stream);

@@ -109,6 +109,7 @@ SIGNATURES = {
     "aem_resample_systematic": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                  c_void_p], c_int),
     "aem_philox4x32": ([c_void_p, ctypes.c_uint, ctypes.c_uint, c_void_p, c_int, c_void_p], c_int),
+    "aem_resample_systematic_noalloc": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p], c_int),
 }
 
 

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1098,4 +1099,54 @@ extern "C" int aem_philox4x32(const unsigned int *counters, unsigned int key0, u
     philox_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(counters, key0, key1, out, n);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
+}
+
+// ------------------------------------------- resampling without allocation
+// Scratch for aem_resample_systematic_noalloc: one fixed array per GPU that
+// loads the library, sized for the largest accepted problem and kept until the
+// process exits.  Host code must not pass the symbol itself to a kernel (on
+// the host it names a stand-in, not device memory); it passes the device
+// address obtained below.
+namespace {
+constexpr size_t kNoAllocScratchBytes = 512 * 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress allocates nothing).
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    AEM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(AEM_ERR_UNSUPPORTED, "aem_resample_systematic_noalloc: device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "aem_resample_systematic_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return AEM_OK;
+}
+}  // namespace
+
+extern "C" int aem_resample_systematic_noalloc(const double *W, const int *model, int n, int n_models,
+                                                const unsigned long long *u40, int *ancestor, void *stream) {
+    if (n < 1 || n > AEM_NOALLOC_MAX_PARTICLES || n_models < 1 || n_models > AEM_NOALLOC_MAX_MODELS)
+        return fail(AEM_ERR_INVALID_ARG,
+                    "aem_resample_systematic_noalloc: n or n_models exceeds the maximum of the static scratch "
+                    "(n <= AEM_NOALLOC_MAX_PARTICLES, n_models <= AEM_NOALLOC_MAX_MODELS)");
+    if (aem_smc_workspace_bytes(n, n_models) + 64 > kNoAllocScratchBytes)
+        return fail(AEM_ERR_INVALID_ARG, "aem_resample_systematic_noalloc: problem exceeds the static scratch");
+    if (!W || !model || !u40 || !ancestor)
+        return fail(AEM_ERR_INVALID_ARG, "aem_resample_systematic_noalloc: NULL pointer");
+    void *work = nullptr;
+    int rc = noalloc_scratch(&work);
+    if (rc) return rc;
+    // every scratch word the kernels read is written earlier in the same call,
+    // so nothing has to be cleared between calls
+    return aem_resample_systematic(W, model, n, n_models, u40, ancestor, work, kNoAllocScratchBytes, stream);
 }

@@ -178,6 +178,18 @@ def resample_systematic(W, model, n_models, u40, stream=None):
     return anc
 
 
+def resample_systematic_noalloc(W, model, n_models, u40, stream=None):
+    """aem_resample_systematic_noalloc: the same resampling with the library's
+    static scratch instead of a workspace (the output tensor is the caller's)."""
+    torch = _torch()
+    n = W.numel()
+    anc = torch.empty(n, dtype=torch.int32, device=W.device)
+    check(_lib.load().aem_resample_systematic_noalloc(W.data_ptr(), model.data_ptr(), n, n_models, u40.data_ptr(),
+                                                      anc.data_ptr(), _stream(stream)),
+          "aem_resample_systematic_noalloc")
+    return anc
+
+
 def philox4x32(counters, key0, key1, stream=None):
     """aem_philox4x32 on a device tensor of (n, 4) int32 counters (uint32 bit patterns)."""
     torch = _torch()
