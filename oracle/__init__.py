@@ -55,7 +55,7 @@ def lib():
             d = ctypes.c_double
             i = ctypes.c_int
             p = ctypes.c_void_p
-            _lib.orc_forward.argtypes = [i, i, p, p, p, p, p, p, i, d, d, d, i, p, i, p, i, i, d, p, p, i]
+            _lib.orc_forward.argtypes = [i, i, p, p, p, p, p, p, i, d, d, d, i, p, i, p, i, i, d, p, p, i, p]
             _lib.orc_forward.restype = i
             _lib.orc_tmatrix.argtypes = [i, p, i, p, p]
             _lib.orc_colecole.argtypes = [i, d, d, d, d, d, p]
@@ -130,13 +130,15 @@ def tmatrix(freqs, times):
     return T
 
 
-def forward(models, system, mode=QUAD_REFLECTION, rtol=1e-11, nthreads=None, want_imh=False):
+def forward(models, system, mode=QUAD_REFLECTION, rtol=1e-11, nthreads=None, want_imh=False, want_absh=False):
     """Gates -dBz/dt (T/s per the system current) for a batch of merged-layer models.
 
     models: dict with int 'nlayers' [P] and float arrays 'logsig', 'logh', 'm',
     'logtau', 'c' of shape [P, LMAX] (log10 of sigma_inf in S/m, thickness in
     m and tau in s).  system: dict with 'a', 'h', 'freqs', 'times', 'K',
-    'cc_form', 'current' and optionally a precomputed 'T'.
+    'cc_form', 'current' and optionally a precomputed 'T'.  With the Hankel
+    rule, want_absh also returns sum_k |w_k| |R_0(lambda_k, w_f)| per node,
+    the magnitude scale of the rule's sum.
     """
     nl = np.ascontiguousarray(models["nlayers"], dtype=np.int32)
     P = len(nl)
@@ -151,15 +153,19 @@ def forward(models, system, mode=QUAD_REFLECTION, rtol=1e-11, nthreads=None, wan
     F, G = len(freqs), len(times)
     y = np.zeros((P, G))
     imh = np.zeros((P, F)) if want_imh else None
+    absh = np.zeros((P, F)) if want_absh else None
+    if want_absh and mode != HANKEL_RULE:
+        raise ValueError("want_absh needs the Hankel rule mode")
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     rc = lib().orc_forward(P, LMAX, _ptr(nl), *[_ptr(a) for a in arrs], int(system.get("cc_form", 0)),
                            float(system["a"]), float(system["h"]), float(system.get("current", 1.0)), F,
                            _ptr(freqs), G, _ptr(T), int(mode), int(system.get("K", 200)), float(rtol),
-                           _ptr(imh), _ptr(y), int(nthreads))
+                           _ptr(imh), _ptr(y), int(nthreads), _ptr(absh))
     if rc != 0:
         raise ValueError("oracle forward: layer count out of range")
-    return (y, imh) if want_imh else y
+    out = (y,) + ((imh,) if want_imh else ()) + ((absh,) if want_absh else ())
+    return out if len(out) > 1 else y
 
 
 def loglik(y_model, y_obs, eps_an, eps_mn):

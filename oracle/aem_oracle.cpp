@@ -501,7 +501,7 @@ struct OracleModelView {
 
 static void forward_one(const OracleModelView &mv, int p, int cc_form, double a, double h, double current,
                         int F, const double *freqs, int G, const double *T, int hankel_mode, int K,
-                        double rtol, double *imh_row, double *y_row) {
+                        double rtol, double *imh_row, double *y_row, double *absh_row) {
     int L = mv.nlayers[p];
     std::vector<double> sig(L), thick(L), mm(L), tau(L), cc(L);
     for (int n = 0; n < L; ++n) {
@@ -521,7 +521,13 @@ static void forward_one(const OracleModelView &mv, int p, int cc_form, double a,
         cd H;
         if (hankel_mode == 2) {
             H = cd(0.0, 0.0);
-            for (int k = 0; k < K; ++k) H += ck[k] * r0_reflection(L, s.data(), thick.data(), lam[k]);
+            double mag = 0.0;  // sum of |term| of the rule: the scale of its rounding error
+            for (int k = 0; k < K; ++k) {
+                cd R = r0_reflection(L, s.data(), thick.data(), lam[k]);
+                H += ck[k] * R;
+                mag += std::fabs(ck[k]) * std::abs(R);
+            }
+            if (absh_row) absh_row[f] = mag;
         } else {
             H = hz_quadrature(L, s.data(), thick.data(), a, h, current, hankel_mode, rtol);
         }
@@ -540,7 +546,8 @@ static void forward_one(const OracleModelView &mv, int p, int cc_form, double a,
 extern "C" int orc_forward(int P, int LMAX, const int *nlayers, const double *logsig, const double *logh,
                            const double *m, const double *logtau, const double *c, int cc_form, double a,
                            double h, double current, int F, const double *freqs, int G, const double *T,
-                           int hankel_mode, int K, double rtol, double *imh, double *y, int nthreads) {
+                           int hankel_mode, int K, double rtol, double *imh, double *y, int nthreads,
+                           double *absh) {
     OracleModelView mv{LMAX, nlayers, logsig, logh, m, logtau, c};
     for (int p = 0; p < P; ++p)
         if (nlayers[p] < 1 || nlayers[p] > LMAX) return -1;
@@ -550,7 +557,8 @@ extern "C" int orc_forward(int P, int LMAX, const int *nlayers, const double *lo
         pool.emplace_back([&, tid]() {
             for (int p = tid; p < P; p += nthreads)
                 forward_one(mv, p, cc_form, a, h, current, F, freqs, G, T, hankel_mode, K, rtol,
-                            imh ? imh + (size_t)p * F : nullptr, y ? y + (size_t)p * G : nullptr);
+                            imh ? imh + (size_t)p * F : nullptr, y ? y + (size_t)p * G : nullptr,
+                            absh ? absh + (size_t)p * F : nullptr);
         });
     }
     for (auto &th : pool) th.join();

@@ -41,16 +41,7 @@ __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
 
 // ---- precision-specific primitives ------------------------------------
 struct FP32Ops {
-    using R = float;
-    // Hardware approximations (MUFU): rsqrt, rcp and sqrt(v) = v * rsqrt(v)
-    // for v > 0 (every argument here is strictly positive).
-    static __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
-    static __device__ __forceinline__ float sq(float v) { return v * rsqrtf(v); }
-    static __device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
-    static __device__ __forceinline__ void expsincos(float re, float im, float *e, float *s, float *c) {
-        *e = __expf(re);
-        __sincosf(im, s, c);
-    }
+    using R = float;  // the FP32 path has its own kernel (forward_f32_kernel below)
 };
 
 struct FP64Ops {
@@ -135,11 +126,8 @@ __device__ __forceinline__ typename Ops::R im_r0(typename Ops::R lam, typename O
 template <class R>
 __device__ __forceinline__ R pow10r(R v);
 template <>
-__device__ __forceinline__ float pow10r<float>(float v) { return exp10f(v); }
-template <>
 __device__ __forceinline__ double pow10r<double>(double v) { return exp10(v); }
 
-__device__ __forceinline__ void sincospi_r(float v, float *s, float *c) { sincospif(v, s, c); }
 __device__ __forceinline__ void sincospi_r(double v, double *s, double *c) { sincospi(v, s, c); }
 
 template <class R>
@@ -346,6 +334,388 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
     return AEM_OK;
 }
 
+
+// ===================================================================== FP32
+// FP32 hot path.  Each thread carries TWO Hankel abscissae of the same
+// frequency (k and k + K/2) through the layer recursion together, packed in
+// 64-bit register pairs and advanced with the sm_100+ paired FP32 instructions
+// (add/sub/mul/fma .f32x2): one issue slot per operation on both abscissae.
+// The special functions (rsqrt, rcp, ex2, sin, cos) stay scalar.
+//
+// The recursion is carried in w = sqrt(2) u, which folds the constants:
+//   r = (s_a - s_b) / (u_a + u_b)^2 = B / (w_a + w_b)^2,  B = 2 (s_a - s_b)
+//   E = exp(-2 u h) = exp2(e w.x) (cos(e ln2 w.y) + i sin(e ln2 w.y)),
+//   e = -sqrt(2) h log2(e).
+// Principal root of 2 (lambda^2 + s) with x = lambda^2 + Re s, y = Im s > 0:
+//   t = |x + i y| + |x|, rr = rsqrt(t); (t rr, y rr) is (Re w, Im w) when
+//   x >= 0 and (Im w, Re w) otherwise.
+// The Moebius step (N, D) <- (r D + N E, D + r N E) keeps R_0 = N / D.
+typedef unsigned long long u64;
+
+__device__ __forceinline__ float rsqrt_approx(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float v) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ void sincos_approx(float v, float *s, float *c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(v));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(v));
+}
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(u64 r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+struct C2x2 {  // two complex numbers: re = (re_a, re_b), im = (im_a, im_b)
+    u64 re, im;
+};
+
+// w for both abscissae; sxx = (Re s, Re s), yyy = (Im s ^2, ...), syy = (Im s, Im s)
+__device__ __forceinline__ C2x2 wroot2(u64 lam2, u64 sxx, u64 yyy, u64 syy) {
+    const u64 x = add2(lam2, sxx);
+    const u64 v = fma2(x, x, yyy);
+    float v0, v1, x0, x1;
+    up2(v, v0, v1);
+    up2(x, x0, x1);
+    const u64 mod = mul2(v, pk2(rsqrt_approx(v0), rsqrt_approx(v1)));
+    float m0, m1;
+    up2(mod, m0, m1);
+    const float t0 = m0 + fabsf(x0), t1 = m1 + fabsf(x1);
+    const u64 rr = pk2(rsqrt_approx(t0), rsqrt_approx(t1));
+    const u64 p = mul2(pk2(t0, t1), rr), o = mul2(syy, rr);
+    float p0, p1, o0, o1;
+    up2(p, p0, p1);
+    up2(o, o0, o1);
+    C2x2 w;
+    w.re = pk2(x0 >= 0.f ? p0 : o0, x1 >= 0.f ? p1 : o1);
+    w.im = pk2(x0 >= 0.f ? o0 : p0, x1 >= 0.f ? o1 : p1);
+    return w;
+}
+
+// r = B / (wa + wb)^2 = B (cre - 2 i pp), (wx - i wy) = conj(q) / |q|^2.
+// Bv = ((Bx, Bx), (By, By)), Cv = ((-2 Bx, -2 Bx), (2 By, 2 By)).
+__device__ __forceinline__ C2x2 rcoef2(ulonglong2 Bv, ulonglong2 Cv, C2x2 a, C2x2 b) {
+    const u64 qx = add2(a.re, b.re), qy = add2(a.im, b.im);
+    float q0, q1;
+    up2(fma2(qx, qx, mul2(qy, qy)), q0, q1);
+    const u64 ir = pk2(rcp_approx(q0), rcp_approx(q1));
+    const u64 wx = mul2(qx, ir), wy = mul2(qy, ir);
+    const u64 cre = mul2(sub2(wx, wy), add2(wx, wy));
+    const u64 pp = mul2(wx, wy);
+    C2x2 r;
+    r.re = fma2(Bv.x, cre, mul2(Cv.y, pp));
+    r.im = fma2(Bv.y, cre, mul2(Cv.x, pp));
+    return r;
+}
+
+// he = ((e, e), (e ln2, e ln2)) of the layer below the interface.
+__device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
+    float a0, a1, f0, f1;
+    up2(mul2(he.x, wb.re), a0, a1);
+    up2(mul2(he.y, wb.im), f0, f1);
+    float s0, c0, s1, c1;
+    sincos_approx(f0, &s0, &c0);
+    sincos_approx(f1, &s1, &c1);
+    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
+    const u64 Ex = mul2(e, pk2(c0, c1)), Ey = mul2(e, pk2(s0, s1));
+    const u64 Px = sub2(mul2(N.re, Ex), mul2(N.im, Ey));
+    const u64 Py = fma2(N.re, Ey, mul2(N.im, Ex));
+    const u64 Nx = sub2(fma2(r.re, D.re, Px), mul2(r.im, D.im));
+    const u64 Ny = fma2(r.re, D.im, fma2(r.im, D.re, Py));
+    const u64 Dx = sub2(fma2(r.re, Px, D.re), mul2(r.im, Py));
+    const u64 Dy = fma2(r.re, Py, fma2(r.im, Px, D.im));
+    N.re = Nx;
+    N.im = Ny;
+    D.re = Dx;
+    D.im = Dy;
+}
+
+// Im R_0 for the two abscissae of one work item.
+__device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 *__restrict__ RS,
+                                           const u64 *__restrict__ RY, const ulonglong2 *__restrict__ RB,
+                                           const ulonglong2 *__restrict__ RC, ulonglong2 RAB, ulonglong2 RAC,
+                                           const ulonglong2 *__restrict__ HE, int L, float &out0, float &out1) {
+    const C2x2 air = {wair, 0ull};
+    ulonglong2 a = RS[L - 1];
+    C2x2 wb = wroot2(lam2, a.x, a.y, RY[L - 1]);
+    if (L == 1) {
+        up2(rcoef2(RAB, RAC, air, wb).im, out0, out1);
+        return;
+    }
+    a = RS[L - 2];
+    C2x2 wn = wroot2(lam2, a.x, a.y, RY[L - 2]);
+    C2x2 N = rcoef2(RB[L - 2], RC[L - 2], wn, wb);
+    C2x2 D = {pk2(1.f, 1.f), 0ull};
+    ulonglong2 he = HE[L - 2];
+    wb = wn;
+#pragma unroll 2
+    for (int n = L - 3; n >= 0; --n) {
+        a = RS[n];
+        wn = wroot2(lam2, a.x, a.y, RY[n]);
+        const C2x2 r = rcoef2(RB[n], RC[n], wn, wb);
+        mobius2(N, D, r, wb, he);
+        he = HE[n];
+        wb = wn;
+    }
+    mobius2(N, D, rcoef2(RAB, RAC, air, wb), wb, he);
+    float n0, n1, d0, d1;
+    up2(sub2(mul2(N.im, D.re), mul2(N.re, D.im)), n0, n1);
+    up2(fma2(D.re, D.re, mul2(D.im, D.im)), d0, d1);
+    out0 = n0 * rcp_approx(d0);
+    out1 = n1 * rcp_approx(d1);
+}
+
+// Shared memory (dynamic), in order: RS[F*LS], RB[F*LS], RC[F*LS], RAB[F],
+// RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), stmp[F*LS], hwp[K2] (float2),
+// imh_w[kWarps*F], imh[F], T[G*F] (float).
+#ifndef AEM_F32_MIN_BLOCKS
+#define AEM_F32_MIN_BLOCKS 4  // resident CTAs per SM the register allocation must allow (<= 64 registers)
+#endif
+__global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kernel(ModelsView<FP32Ops> mv, int F, int G, int K,
+                                                               int cc_form, int LS,
+                                                               const float *__restrict__ g_omega,
+                                                               const float *__restrict__ g_lam,
+                                                               const float *__restrict__ g_hw,
+                                                               const float *__restrict__ g_T,
+                                                               float *__restrict__ gates_out,
+                                                               float *__restrict__ imh_out,
+                                                               const double *__restrict__ y_obs, int obs_per,
+                                                               const double *__restrict__ eps_an, double eps_mn,
+                                                               double *__restrict__ ll_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K2 = (K + 1) / 2;
+    ulonglong2 *RS = reinterpret_cast<ulonglong2 *>(smem_raw);
+    ulonglong2 *RB = RS + (size_t)F * LS;
+    ulonglong2 *RC = RB + (size_t)F * LS;
+    ulonglong2 *RAB = RC + (size_t)F * LS;
+    ulonglong2 *RAC = RAB + F;
+    ulonglong2 *lamp = RAC + F;
+    u64 *RY = reinterpret_cast<u64 *>(lamp + K2);
+    float2 *stmp = reinterpret_cast<float2 *>(RY + (size_t)F * LS);
+    float2 *hwp = stmp + (size_t)F * LS;
+    float *imh_w = reinterpret_cast<float *>(hwp + K2);
+    float *imh = imh_w + (size_t)kWarps * F;
+    float *Ts = imh + F;
+    __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
+    __shared__ float lsig[AEM_MAX_LAYERS], lm[AEM_MAX_LAYERS], ltau[AEM_MAX_LAYERS], lc[AEM_MAX_LAYERS];
+    __shared__ double ll_part[kWarps];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < G * F; i += blockDim.x) Ts[i] = g_T[i];
+    // abscissa pairs (k, k + K2); an odd K pads the last pair with a zero weight
+    for (int k = tid; k < K2; k += blockDim.x) {
+        const int kb = k + K2 < K ? k + K2 : K - 1;
+        const float la = g_lam[k], lb = g_lam[kb];
+        lamp[k] = make_ulonglong2(pk2(la * la, lb * lb),
+                                  pk2(1.41421356237309505f * la, 1.41421356237309505f * lb));
+        hwp[k] = make_float2(g_hw[k], k + K2 < K ? g_hw[kb] : 0.f);
+    }
+    const float mu0 = (float)kMu0;
+    const int FK2 = F * K2;
+
+    for (int p = blockIdx.x; p < mv.n; p += gridDim.x) {
+        const int L = mv.nlayers[p];
+        __syncthreads();
+        if (tid < L) {
+            const size_t o = (size_t)p * mv.lmax + tid;
+            lsig[tid] = exp10f(mv.logsig[o]);
+            const float e = -1.41421356237309505f * 1.44269504088896341f * exp10f(mv.logh[o]);
+            HE[tid] = make_ulonglong2(pk2(e, e), pk2(e * 0.69314718055994531f, e * 0.69314718055994531f));
+            lm[tid] = mv.m[o];
+            ltau[tid] = exp10f(mv.logtau[o]);
+            lc[tid] = mv.c[o];
+        }
+        for (int i = tid; i < kWarps * F; i += blockDim.x) imh_w[i] = 0.f;
+        __syncthreads();
+        // Cole-Cole per (frequency, layer): x = (w tau)^c e^{i pi c / 2}, s = i w mu0 sigma
+        for (int i = tid; i < F * L; i += blockDim.x) {
+            const int f = i / L, n = i - f * L;
+            const float w = g_omega[f];
+            const float sig = lsig[n], mm = lm[n];
+            float sr = sig, si = 0.f;
+            if (mm != 0.f) {
+                const float cc = lc[n];
+                const float mag = expf(cc * logf(w * ltau[n]));
+                float sp, cp;
+                sincospif(0.5f * cc, &sp, &cp);
+                const float xr = 1.f + mag * cp, xi = mag * sp;
+                const float den = xr * xr + xi * xi;
+                if (cc_form == AEM_CC_PAPER) {
+                    sr = sig * (1.f - mm * xr / den);
+                    si = sig * (mm * xi / den);
+                } else {
+                    const float br = 1.f + (1.f - mm) * mag * cp, bi = (1.f - mm) * mag * sp;
+                    const float bd = br * br + bi * bi;
+                    sr = sig * (xr * br + xi * bi) / bd;
+                    si = sig * (xi * br - xr * bi) / bd;
+                }
+            }
+            const float sx = -w * mu0 * si, sy = w * mu0 * sr;
+            RS[(size_t)f * LS + n] = make_ulonglong2(pk2(sx, sx), pk2(sy * sy, sy * sy));
+            RY[(size_t)f * LS + n] = pk2(sy, sy);
+            stmp[(size_t)f * LS + n] = make_float2(sx, sy);
+        }
+        __syncthreads();
+        for (int i = tid; i < F * L; i += blockDim.x) {
+            const int f = i / L, n = i - f * L;
+            const float2 a = stmp[(size_t)f * LS + n];
+            if (n + 1 < L) {
+                const float2 b = stmp[(size_t)f * LS + n + 1];
+                const float bx = 2.f * (a.x - b.x), by = 2.f * (a.y - b.y);
+                RB[(size_t)f * LS + n] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
+                RC[(size_t)f * LS + n] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
+            }
+            if (n == 0) {
+                const float bx = -2.f * a.x, by = -2.f * a.y;
+                RAB[f] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
+                RAC[f] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
+            }
+        }
+        __syncthreads();
+
+        int f = tid / K2, k = tid - (tid / K2) * K2;
+        for (int base = 0; base < FK2; base += blockDim.x) {
+            const int item = base + tid;
+            float val = 0.f;
+            int fl = -1;
+            if (item < FK2) {
+                fl = f;
+                const ulonglong2 lw = lamp[k];
+                float r0, r1;
+                const size_t o = (size_t)f * LS;
+                im_r0_pair(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
+                const float2 hw = hwp[k];
+                val = fmaf(hw.x, r0, hw.y * r1);
+            }
+            // segmented warp reduction over lanes that share a frequency
+            unsigned pending = __ballot_sync(kFull, fl >= 0);
+            while (pending) {
+                const int leader = __ffs(pending) - 1;
+                const int fsel = __shfl_sync(kFull, fl, leader);
+                const float part = warp_sum<float>(fl == fsel ? val : 0.f);
+                if (lane == leader) imh_w[warp * F + fsel] += part;
+                pending &= ~__ballot_sync(kFull, fl == fsel);
+            }
+            k += blockDim.x;
+            while (k >= K2) {
+                k -= K2;
+                ++f;
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < F; j += blockDim.x) {
+            float acc = 0.f;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) acc += imh_w[w * F + j];
+            imh[j] = acc;
+        }
+        __syncthreads();
+
+        double term = 0.0;
+        if (tid < G) {
+            float acc = 0.f;
+            for (int j = 0; j < F; ++j) acc = fmaf(Ts[tid * F + j], imh[j], acc);
+            if (gates_out) gates_out[(size_t)p * G + tid] = acc;
+            if (ll_out) {
+                const double yh = (double)acc;
+                const double ea = eps_an[tid];
+                const double v = ea * ea + (eps_mn * yh) * (eps_mn * yh);
+                const double *yo = y_obs + (obs_per > 0 ? (size_t)(p / obs_per) * G : 0);
+                const double rr = yo[tid] - yh;
+                term = rr * rr / v + log(2.0 * kPi * v);
+            }
+        }
+        if (imh_out)
+            for (int j = tid; j < F; j += blockDim.x) imh_out[(size_t)p * F + j] = imh[j];
+        if (ll_out) {
+            if (warp * 32 < G) {
+                const double t = warp_sum<double>(term);
+                if (lane == 0) ll_part[warp] = t;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double acc = 0.0;
+                for (int w = 0; w * 32 < G; ++w) acc += ll_part[w];
+                ll_out[p] = -0.5 * acc;
+            }
+        }
+    }
+}
+
+size_t smem_bytes_f32(int F, int G, int K, int LS) {
+    const size_t K2 = (K + 1) / 2;
+    return sizeof(ulonglong2) * ((size_t)3 * F * LS + 2 * (size_t)F + K2) + sizeof(u64) * (size_t)F * LS +
+           sizeof(float2) * ((size_t)F * LS + K2) + sizeof(float) * ((size_t)kWarps * F + F + (size_t)G * F);
+}
+
+template <class Models>
+int launch_forward_f32(const aem_system *sys, const Models *models, float *gates, float *imh, const double *y_obs,
+                       int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name) {
+    if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
+    if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
+        return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
+    if (models->n_models == 0) return AEM_OK;
+    if (!gates && !imh && !ll) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": no output requested");
+    if (!models->nlayers || !models->logsig || !models->logh || !models->m || !models->logtau || !models->c)
+        return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL model array");
+    if (ll && (!y_obs || !eps_an)) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL y_obs or eps_an");
+    const SystemTables &h = sys->host;
+    ModelsView<FP32Ops> mv{models->n_models, models->lmax, models->nlayers, models->logsig, models->logh,
+                           models->m, models->logtau, models->c};
+    const int LS = models->lmax;
+    const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
+    auto kern = forward_f32_kernel;
+    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the kernel reads its tables from shared memory only: give the SM's
+    // unified L1/shared storage to shared memory so more CTAs stay resident
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0;
+    AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)sys->num_sms * per_sm;
+    if (grid > models->n_models) grid = models->n_models;
+    kern<<<(unsigned)grid, kThreads, smem, (cudaStream_t)stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f,
+                                                                   sys->d_lam_f, sys->d_hw_f, sys->d_T_f, gates, imh,
+                                                                   y_obs, obs_per, eps_an, eps_mn, ll);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
 }  // namespace
 }  // namespace aem
 
@@ -353,9 +723,8 @@ namespace aem {
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
                          cudaStream_t stream) {
-    return launch_forward<FP32Ops>(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding,
-                                   eps_an, eps_mn, ll, (void *)stream, sys->d_omega_f, sys->d_lam_f, sys->d_hw_f,
-                                   sys->d_T_f, "loglik (SMC)");
+    return launch_forward_f32(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding, eps_an,
+                              eps_mn, ll, (void *)stream, "loglik (SMC)");
 }
 }  // namespace aem
 
@@ -363,9 +732,7 @@ using namespace aem;
 
 extern "C" int aem_forward_f32(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh,
                                void *stream) {
-    return launch_forward<FP32Ops>(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream,
-                                   sys ? sys->d_omega_f : nullptr, sys ? sys->d_lam_f : nullptr,
-                                   sys ? sys->d_hw_f : nullptr, sys ? sys->d_T_f : nullptr, "aem_forward_f32");
+    return launch_forward_f32(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream, "aem_forward_f32");
 }
 
 extern "C" int aem_forward_f64(const aem_system *sys, const aem_models_f64 *models, double *gates, double *imh,
@@ -378,9 +745,7 @@ extern "C" int aem_forward_f64(const aem_system *sys, const aem_models_f64 *mode
 extern "C" int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               const double *eps_an, double eps_mn, double *ll, float *gates, void *stream) {
     if (!ll && models && models->n_models > 0) return fail(AEM_ERR_INVALID_ARG, "aem_loglik_f32: ll is NULL");
-    return launch_forward<FP32Ops>(sys, models, gates, nullptr, y_obs, 0, eps_an, eps_mn, ll, stream,
-                                   sys ? sys->d_omega_f : nullptr, sys ? sys->d_lam_f : nullptr,
-                                   sys ? sys->d_hw_f : nullptr, sys ? sys->d_T_f : nullptr, "aem_loglik_f32");
+    return launch_forward_f32(sys, models, gates, nullptr, y_obs, 0, eps_an, eps_mn, ll, stream, "aem_loglik_f32");
 }
 
 extern "C" int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,

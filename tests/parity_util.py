@@ -1,11 +1,25 @@
-"""Shared parity helpers: per-gate condition numbers of the step-off
-transform and the error bounds the forward-model tests derive from them."""
+"""Shared parity helpers: condition numbers of the forward model's last two
+steps and the per-gate error bounds the forward-model tests derive from them.
+
+Gate g of y = T Im H is a sum of terms of both signs.  Three perturbations are
+propagated (each delta is a component accuracy asserted on its own):
+  * the spectrum: |d Im H_f| <= delta_s * A_f with A_f = sum_k |w_k| |R_0(lambda_k, w_f)|
+    (the magnitude scale of the Hankel sum) -> kappa_H,g = sum_f |T_gf| A_f;
+  * rounding of T and of the G x F dot product in the working precision
+    -> kappa_g = sum_f |T_gf| |Im H_f|;
+  * the two independently built tables differ by <= delta_T of each row's
+    largest entry -> kappa_T,g = max_f |T_gf| * sum_f |Im H_f|;
+all divided by max(|y_g|, eps_an).
+"""
 import numpy as np
 
 import oracle as O
 from paper_2109_00661_gb300 import inputs as I
 
 EPS_AN = I.EPS_AN
+DELTA_S32 = 1e-5   # FP32 spectrum, relative to A_f
+DELTA_S64 = 1e-12  # FP64 spectrum, relative to A_f
+DELTA_T = 1e-8     # table agreement, relative to each row's largest entry
 
 _T_cache = {}
 
@@ -22,21 +36,38 @@ def rel_err(gpu, ref):
     return np.abs(gpu - ref) / np.maximum(np.abs(ref), EPS_AN)
 
 
-def kappa(imh, T, y):
-    """Condition numbers of each gate of y = T imh: elementwise (kappa) and
-    against a perturbation of T bounded by its row maximum (kappa_T)."""
+def kappa(imh, T, y, absh=None):
     den = np.maximum(np.abs(y), EPS_AN)
     k = (np.abs(imh) @ np.abs(T).T) / den
     kT = np.sum(np.abs(imh), axis=1, keepdims=True) * np.max(np.abs(T), axis=1)[None, :] / den
-    return np.stack([k, kT])
+    kH = (np.abs(absh if absh is not None else imh) @ np.abs(T).T) / den
+    return np.stack([k, kT, kH])
+
+
+def oracle_ref(models, name, cc_form=0):
+    """Oracle gates, spectrum, Hankel-sum magnitudes and per-gate condition
+    numbers on the same discretisation as the GPU (the K-point rule)."""
+    s = oracle_system(name, cc_form)
+    y, imh, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    return y, imh, absh, kappa(imh, s["T"], y, absh)
+
+
+def spectrum_err(imh, imh_ref, absh):
+    return np.abs(imh - imh_ref) / absh
 
 
 def bound64(kap):
-    return 1e-7 + kap[0] * 1e-9 + kap[1] * 1e-8
+    return 1e-7 + kap[2] * DELTA_S64 + kap[0] * 2.0 ** -52 * 64 + kap[1] * DELTA_T
 
 
 def bound32(kap, F):
-    return 1e-4 + kap[0] * (1e-5 + (F + 1) * 2.0 ** -24) + kap[1] * 1e-8
+    return 1e-4 + kap[2] * DELTA_S32 + kap[0] * (F + 1) * 2.0 ** -24 + kap[1] * DELTA_T
+
+
+def assert_within(e, bound, what):
+    r = e / bound
+    i = np.unravel_index(np.argmax(r), r.shape)
+    assert r.max() <= 1.0, f"{what}: error {e[i]:.3e} exceeds bound {bound[i]:.3e} at {i}"
 
 
 def loglik_bound(y_model, y_obs, gate_bound, eps_an=EPS_AN, eps_mn=I.EPS_MN):

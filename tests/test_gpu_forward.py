@@ -9,14 +9,13 @@ The step-off transform y = T Im H is a sum of large terms of both signs for
 late gates, near zero crossings and over resistive ground; its condition
 number kappa_g = sum_f |T_gf| |Im H_f| / max(|y_g|, eps_an) reaches 1e5-1e6 on
 the random-model workload.  A relative error delta in the spectrum or in T can
-therefore move a gate by up to kappa_g * delta.  The two transform tables are
-built by independent quadratures and agree to delta_T = 1e-8 of each row's
-largest entry (asserted below); that difference reaches a gate through
-kappa_T,g = max_f |T_gf| * sum_f |Im H_f| / max(|y_g|, eps_an).  The
-tolerances are the stated per-gate bounds plus these propagated terms, with
-each delta one of the component accuracies asserted separately:
-  FP64:  e_g <= 1e-7 + kappa_g * 1e-9 + kappa_T,g * 1e-8
-  FP32:  e_g <= 1e-4 + kappa_g * (1e-5 + (F + 1) * 2^-24) + kappa_T,g * 1e-8
+therefore move a gate by up to kappa_g * delta.  The tolerances are the stated
+per-gate bounds plus the propagated terms of tests/parity_util.py, with each
+delta one of the component accuracies asserted separately (the spectrum
+relative to the Hankel sum's magnitude A_f, the two transform tables relative
+to each row's largest entry):
+  FP64:  e_g <= 1e-7 + kappa_H,g 1e-12 + kappa_g 2^-46 + kappa_T,g 1e-8
+  FP32:  e_g <= 1e-4 + kappa_H,g 1e-5 + kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8
 and the fraction of gates inside the plain 1e-4 FP32 bound is reported.
 """
 import numpy as np
@@ -24,6 +23,8 @@ import pytest
 
 import oracle as O
 from paper_2109_00661_gb300 import inputs as I
+from parity_util import (DELTA_S32, DELTA_S64, DELTA_T, assert_within, bound32, bound64, kappa, loglik_bound,
+                         oracle_ref, oracle_system, rel_err, spectrum_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -52,62 +53,12 @@ def gpu_system(L, name, cc_form=0):
     return _sys_cache[key]
 
 
-_T_cache = {}
-
-
-def oracle_system(name, cc_form=0):
-    s = I.oracle_system(name, cc_form)
-    if name not in _T_cache:
-        _T_cache[name] = O.tmatrix(s["freqs"], s["times"])
-    s["T"] = _T_cache[name]
-    return s
-
-
 def as_f32_inputs(models):
     """Round the model parameters to float32 so both sides see identical inputs."""
     out = dict(models)
     for k in ("logsig", "logh", "m", "logtau", "c"):
         out[k] = np.asarray(models[k], dtype=np.float32).astype(np.float64)
     return out
-
-
-def rel_err(gpu, ref):
-    return np.abs(gpu - ref) / np.maximum(np.abs(ref), EPS_AN)
-
-
-def kappa(imh, T, y):
-    """Condition numbers of each gate of y = T imh: elementwise (kappa) and
-    against a perturbation of T bounded by its row maximum (kappa_T)."""
-    den = np.maximum(np.abs(y), EPS_AN)
-    k = (np.abs(imh) @ np.abs(T).T) / den
-    kT = np.sum(np.abs(imh), axis=1, keepdims=True) * np.max(np.abs(T), axis=1)[None, :] / den
-    return np.stack([k, kT])
-
-
-def oracle_ref(models, name, cc_form=0):
-    """Oracle gates, spectrum and per-gate condition numbers (same discretisation)."""
-    s = oracle_system(name, cc_form)
-    y, imh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True)
-    return y, imh, kappa(imh, s["T"], y)
-
-
-def bound64(kap):
-    return 1e-7 + kap[0] * 1e-9 + kap[1] * 1e-8
-
-
-def bound32(kap, F):
-    return 1e-4 + kap[0] * (1e-5 + (F + 1) * 2.0 ** -24) + kap[1] * 1e-8
-
-
-def assert_within(e, bound, what):
-    r = e / bound
-    i = np.unravel_index(np.argmax(r), r.shape)
-    assert r.max() <= 1.0, f"{what}: error {e[i]:.3e} exceeds bound {bound[i]:.3e} at {i}"
-
-
-def spectrum_err(imh, imh_ref):
-    scale = np.max(np.abs(imh_ref), axis=1, keepdims=True)
-    return np.abs(imh - imh_ref) / (np.abs(imh_ref) + 1e-6 * scale)
 
 
 @pytest.mark.parametrize("name", list(I.CONFIGS))
@@ -121,36 +72,36 @@ def test_tables_match_oracle(lib, name):
     assert np.max(np.abs(hw - hw_o)) <= 1e-12 * np.max(np.abs(hw_o))
     # independently built transform matrices: compare row by row
     for g in range(T.shape[0]):
-        assert np.max(np.abs(T[g] - s["T"][g])) <= 1e-8 * np.max(np.abs(s["T"][g]))
+        assert np.max(np.abs(T[g] - s["T"][g])) <= DELTA_T * np.max(np.abs(s["T"][g]))
 
 
 @pytest.mark.parametrize("name", list(I.CONFIGS))
 @pytest.mark.parametrize("P", [1, 37, 300])
 def test_forward_f64_matches_oracle(lib, torch_mod, name, P):
     models = I.random_models(P, seed=100 + P)
-    y_ref, imh_ref, kap = oracle_ref(models, name)
+    y_ref, imh_ref, absh, kap = oracle_ref(models, name)
     y, imh = lib.forward_f64(gpu_system(lib, name), I.to_torch(models, torch_mod.float64), want_imh=True)
     y, imh = y.cpu().numpy(), imh.cpu().numpy()
     assert y.shape == y_ref.shape
     # spectrum: same rule, same recursion, FP64 on both sides
-    es = spectrum_err(imh, imh_ref)
-    assert es.max() < 1e-9, f"spectrum error {es.max():.3e}"
+    es = spectrum_err(imh, imh_ref, absh)
+    assert es.max() < DELTA_S64, f"spectrum error {es.max():.3e}"
     assert_within(rel_err(y, y_ref), bound64(kap), "FP64 gates")
 
 
 @pytest.mark.parametrize("name", list(I.CONFIGS))
 def test_forward_f32_matches_oracle(lib, torch_mod, name):
     models = as_f32_inputs(I.random_models(1000, seed=7))
-    y_ref, imh_ref, kap = oracle_ref(models, name)
+    y_ref, imh_ref, absh, kap = oracle_ref(models, name)
     y, imh = lib.forward_f32(gpu_system(lib, name), I.to_torch(models, torch_mod.float32), want_imh=True)
     y, imh = y.cpu().numpy().astype(np.float64), imh.cpu().numpy().astype(np.float64)
-    es = spectrum_err(imh, imh_ref)
+    es = spectrum_err(imh, imh_ref, absh)
     e = rel_err(y, y_ref)
     F = imh.shape[1]
     print(f"\n{name}: FP32 spectrum error max {es.max():.2e} p99 {np.quantile(es, 0.99):.2e}; "
           f"per-gate error max {e.max():.2e} median {np.median(e):.2e} p99 {np.quantile(e, 0.99):.2e}; "
           f"within 1e-4: {np.mean(e <= 1e-4):.4f} of gates; e/kappa max {np.max(e / kap[0]):.2e}")
-    assert es.max() < 1e-5, f"spectrum error {es.max():.3e}"
+    assert es.max() < DELTA_S32, f"spectrum error {es.max():.3e}"
     assert_within(e, bound32(kap, F), "FP32 gates")
 
 
@@ -171,11 +122,11 @@ def test_forward_edge_cases(lib, torch_mod):
     models["m"][8:] = 0.0
     models["logsig"][10] = rng.uniform(-0.1, 0.0, LM)  # very conductive
     models["logsig"][11] = rng.uniform(-4.0, -3.9, LM)  # very resistive
-    y_ref, _, kap = oracle_ref(models, name)
+    y_ref, _, _, kap = oracle_ref(models, name)
     y = lib.forward_f64(sysg, I.to_torch(models, torch_mod.float64)).cpu().numpy()
     assert_within(rel_err(y, y_ref), bound64(kap), "FP64 gates")
     m32 = as_f32_inputs(models)
-    y_ref, _, kap = oracle_ref(m32, name)
+    y_ref, _, _, kap = oracle_ref(m32, name)
     y = lib.forward_f32(sysg, I.to_torch(m32, torch_mod.float32)).cpu().numpy().astype(np.float64)
     assert_within(rel_err(y, y_ref), bound32(kap, sysg.F), "FP32 gates")
 
@@ -183,7 +134,7 @@ def test_forward_edge_cases(lib, torch_mod):
 def test_pelton_form(lib, torch_mod):
     name = "sounding-g20-f40-k120"
     models = I.random_models(40, seed=11)
-    y_ref, _, kap = oracle_ref(models, name, cc_form=1)
+    y_ref, _, _, kap = oracle_ref(models, name, cc_form=1)
     y = lib.forward_f64(gpu_system(lib, name, cc_form=1), I.to_torch(models, torch_mod.float64)).cpu().numpy()
     assert_within(rel_err(y, y_ref), bound64(kap), "FP64 gates (Pelton)")
 
@@ -220,7 +171,7 @@ def test_loglik_matches_oracle(lib, torch_mod, prec):
     y_true = O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0]
     y_obs = I.noisy(y_true, seed=0)
     models = as_f32_inputs(I.random_models(200, seed=13, layers_max=5))
-    y_model, _, kap = oracle_ref(models, name)
+    y_model, _, _, kap = oracle_ref(models, name)
     ll_ref = O.loglik(y_model, y_obs, I.EPS_AN, I.EPS_MN)
     dt = torch_mod.float32 if prec == "f32" else torch_mod.float64
     fn = lib.loglik_f32 if prec == "f32" else lib.loglik_f64
@@ -232,11 +183,7 @@ def test_loglik_matches_oracle(lib, torch_mod, prec):
     assert np.all(np.abs(ll - ll_own) <= 1e-12 * np.maximum(1.0, np.abs(ll_own)))
     # 2) against the oracle's predictions: |d ll| <= sum_g |d ll / d yhat_g| |d yhat_g|
     bound = bound64(kap) if prec == "f64" else bound32(kap, sysg.F)
-    dy = bound * np.maximum(np.abs(y_model), I.EPS_AN)
-    v = I.EPS_AN ** 2 + (I.EPS_MN * y_model) ** 2
-    r = y_obs - y_model
-    dll = np.abs(r / v + (I.EPS_MN ** 2 * y_model / v) * (r ** 2 / v - 1.0))
-    assert np.all(np.abs(ll - ll_ref) <= 2.0 * np.sum(dll * dy, axis=1) + 1e-9 * np.abs(ll_ref))
+    assert np.all(np.abs(ll - ll_ref) <= loglik_bound(y_model, y_obs, bound) + 1e-9 * np.abs(ll_ref))
 
 
 def test_full_size_sampled_parity(lib, torch_mod):
@@ -248,7 +195,7 @@ def test_full_size_sampled_parity(lib, torch_mod):
     y = lib.forward_f32(sysg, I.to_torch(models, torch_mod.float32))
     torch_mod.cuda.synchronize()
     idx = np.random.default_rng(5).choice(1 << 20, 48, replace=False)
-    y_ref, _, kap = oracle_ref(I.subset(models, idx), name)
+    y_ref, _, _, kap = oracle_ref(I.subset(models, idx), name)
     e = rel_err(y[idx].cpu().numpy().astype(np.float64), y_ref)
     assert_within(e, bound32(kap, sysg.F), "FP32 gates at full size")
     assert torch_mod.isfinite(y).all()

@@ -141,9 +141,9 @@ def test_prior_loglik_matches_oracle(S, gsys, data):
     parts = [to_oracle(p, i) for i in range(st.n_particles)]
     mb = R.merged_batch(parts, st.kappa_max + st.lambda_max + 1)
     s = oracle_system(NAME)
-    y, imh = O.forward(mb, s, mode=O.HANKEL_RULE, want_imh=True)
+    y, imh, absh = O.forward(mb, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
     ll_ref = O.loglik(y, data, I.EPS_AN, I.EPS_MN)
-    bound = loglik_bound(y, data, bound32(kappa(imh, s["T"], y), s["T"].shape[1]))
+    bound = loglik_bound(y, data, bound32(kappa(imh, s["T"], y, absh), s["T"].shape[1]))
     assert np.all(np.abs(p.ll - ll_ref) <= bound + 1e-9 * np.abs(ll_ref))
 
 
