@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--models", type=int, default=P_PER_GPU)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rjsmc", action="store_true")
+    ap.add_argument("--rjsmc-only", action="store_true", help="run only the RJSMC measurement (profiling)")
     return ap.parse_args()
 
 
@@ -133,6 +135,39 @@ def cpu_baseline(target_seconds=15.0):
                       f"{cores} threads), {elapsed:.1f} s"}
 
 
+def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0):
+    """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
+    gamma = 1) for a batch of independent soundings on the sounding system
+    (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s."""
+    from paper_2109_00661_gb300 import smc as S
+    sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
+    y_true = L.forward_f32(sysg, I.to_torch(truth, torch.float32))[0].cpu().numpy().astype(np.float64)
+    y_obs = np.stack([I.noisy(y_true, seed=1000 + s) for s in range(n_soundings)])
+    sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n_soundings,
+               kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sm.init()
+    stages = sm.run(max_stages=500, n_sweeps=sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    post, lb, _ = sm.model_odds()
+    evals = n_soundings * n_particles * (1 + stages * sweeps)
+    out = {"value": n_soundings / sec, "unit": "soundings/s", "seconds": sec, "stages": stages,
+           "forward_evals_per_s": evals / sec,
+           "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
+                     f"{sweeps} sweeps/stage, alpha=0.5, sounding system G=20 F=40 K=120",
+           "median_log_bfipd": float(np.median(np.clip(lb, -50, 50))),
+           "mean_p_ip": float(np.mean(post.reshape(n_soundings, kappa_max + 1, lambda_max + 1)[:, :, 1:].sum(axis=(1, 2))))}
+    sm.close()
+    sysg.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -186,6 +221,9 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.rjsmc_only:
+        print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())}), flush=True)
+        return
     sysg = L.System(**I.system_kwargs(WORKLOAD))
     F, K, G = sysg.F, sysg.K, sysg.G
     P = args.models
@@ -265,7 +303,9 @@ def main():
         flops = steps_work * FLOPS_PER_LAYER_STEP
         achieved = flops / (ms * 1e-3) / 1e12
         peak = 2.0 * peaks["fp32_fma_per_s"] / 1e12
-        mufu_frac = steps_work * MUFU_PER_LAYER_STEP / (ms * 1e-3) / peaks["mufu_per_s"]
+        # the special-function unit: layer-steps x 6 MUFU ops against the
+        # measured rate of the same mix (rsqrt, rsqrt, rcp, ex2, sin, cos)
+        mufu_frac = steps_work * MUFU_PER_LAYER_STEP / (ms * 1e-3) / peaks["mufu_mix_per_s"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -283,6 +323,13 @@ def main():
             "peaks_measured": peaks,
             "e2e": e2e,
         }
+        if not args.no_rjsmc:
+            # RJSMC soundings/s: the single-sounding configuration (N = 256,
+            # kappa <= 3, lambda <= 4, 10 sweeps per stage, 3-layer IP truth)
+            # batched over 128 soundings, and the large one (N = 4096,
+            # kappa, lambda <= 9, 20 sweeps, 5-layer truth) over 4 soundings
+            line["rjsmc"] = rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())
+            line["rjsmc_large"] = rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer())
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -290,11 +290,12 @@ int aem_philox4x32(const unsigned int *counters, unsigned int key0, unsigned int
                    void *stream);
 
 /* ------------------------------------------------------------------------
- * Device throughput probes used for the roofline denominators: FP32 FMA and
- * MUFU (ex2/sin/cos/rsqrt/rcp) operation rates measured by dependency-free
- * loops on every SM.  Synchronous.  Results in operations per second.
+ * Device throughput probes used for the roofline denominators: FP32 FMA,
+ * MUFU ex2, FP64 FMA and the forward recursion's special-function mix (two
+ * rsqrt, rcp, ex2, sin, cos per layer-step) measured by independent
+ * dependency chains on every SM.  Synchronous.  Operations per second.
  * ---------------------------------------------------------------------- */
-int aem_probe_peaks(double *fp32_fma_per_s, double *mufu_per_s, double *fp64_fma_per_s, double *sm_clock_hz);
+int aem_probe_peaks(double *fp32_fma_per_s, double *mufu_ex2_per_s, double *fp64_fma_per_s, double *mufu_mix_per_s);
 
 #ifdef __cplusplus
 }

@@ -149,9 +149,10 @@ def loglik_f64(system, models, y_obs, eps_an, eps_mn, want_gates=False, stream=N
 
 
 def probe_peaks():
-    """aem_probe_peaks: measured FP32 FMA/s, MUFU op/s, FP64 FMA/s and SM clock (Hz)."""
+    """aem_probe_peaks: measured FP32 FMA/s, MUFU ex2/s, FP64 FMA/s and the
+    forward recursion's MUFU mix (ops/s)."""
     _torch()
     out = [ctypes.c_double() for _ in range(4)]
     check(_lib.load().aem_probe_peaks(*[ctypes.byref(o) for o in out]), "aem_probe_peaks")
-    return dict(fp32_fma_per_s=out[0].value, mufu_per_s=out[1].value, fp64_fma_per_s=out[2].value,
-                sm_clock_hz=out[3].value)
+    return dict(fp32_fma_per_s=out[0].value, mufu_ex2_per_s=out[1].value, fp64_fma_per_s=out[2].value,
+                mufu_mix_per_s=out[3].value)

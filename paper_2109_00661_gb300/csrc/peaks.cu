@@ -1,8 +1,7 @@
 // Throughput probes for the roofline denominators of the forward kernel,
 // which is bound by the FP32 and MUFU (special-function) pipes rather than by
 // HBM or the tensor cores.  Each probe runs independent dependency chains on
-// every resident warp of every SM and counts operations per second; the SM
-// clock during the run comes from clock64() against the event time.
+// every resident warp of every SM and counts operations per second.
 #include <cuda_runtime.h>
 
 #include "aem_internal.h"
@@ -13,22 +12,19 @@ namespace {
 constexpr int kProbeThreads = 256;
 constexpr int kChains = 8;
 
-__global__ void __launch_bounds__(kProbeThreads) fma32_probe(float *sink, int iters, long long *cycles) {
+__global__ void __launch_bounds__(kProbeThreads) fma32_probe(float *sink, int iters) {
     float a[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) a[c] = threadIdx.x * 1e-3f + c;
     const float m = 0.999999f, b = 1e-7f;
-    long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c) a[c] = fmaf(a[c], m, b);
     }
-    long long t1 = clock64();
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < kChains; ++c) s += a[c];
     if (s == 12345.f) sink[0] = s;
-    if (threadIdx.x == 0 && blockIdx.x == 0) cycles[0] = t1 - t0;
 }
 
 __global__ void __launch_bounds__(kProbeThreads) fma64_probe(double *sink, int iters) {
@@ -65,6 +61,32 @@ __global__ void __launch_bounds__(kProbeThreads) mufu_probe(float *sink, int ite
     if (s == 12345.f) sink[0] = s;
 }
 
+// The forward recursion's special-function mix per layer-step: two rsqrt,
+// one rcp, one ex2, one sin and one cos (their rates differ: ex2 issues at
+// twice the rate of the others on this part).
+__global__ void __launch_bounds__(kProbeThreads) mufu_mix_probe(float *sink, int iters) {
+    float a[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = 0.5f + 0.01f * c;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            float v = a[c], r;
+            asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+            asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(r));
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(-r));
+            asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+            asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(r));
+            a[c] = v;
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += a[c];
+    if (s == 12345.f) sink[0] = s;
+}
+
 template <class Kern, class... Args>
 int time_kernel(Kern k, int grid, float *ms, Args... args) {
     cudaEvent_t e0, e1;
@@ -88,32 +110,26 @@ int time_kernel(Kern k, int grid, float *ms, Args... args) {
 using namespace aem;
 
 extern "C" int aem_probe_peaks(double *fp32_fma_per_s, double *mufu_per_s, double *fp64_fma_per_s,
-                               double *sm_clock_hz) {
+                               double *mufu_mix_per_s) {
     int dev = 0, sms = 0;
     AEM_CUDA_TRY(cudaGetDevice(&dev));
     AEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = sms * (2048 / kProbeThreads);
     const double threads = (double)grid * kProbeThreads;
     float *sink = nullptr;
-    long long *cyc = nullptr;
     AEM_CUDA_TRY(cudaMalloc(&sink, 64));
-    AEM_CUDA_TRY(cudaMalloc(&cyc, sizeof(long long)));
     int rc = AEM_OK;
     float ms = 0.f;
     const int it32 = 1 << 14, itmufu = 1 << 11, it64 = 1 << 9;
-    if ((rc = time_kernel(fma32_probe, grid, &ms, sink, it32, cyc))) goto done;
-    {
-        long long cycles = 0;
-        cudaMemcpy(&cycles, cyc, sizeof(cycles), cudaMemcpyDeviceToHost);
-        if (fp32_fma_per_s) *fp32_fma_per_s = threads * it32 * kChains / (ms * 1e-3);
-        if (sm_clock_hz) *sm_clock_hz = (double)cycles / (ms * 1e-3);
-    }
+    if ((rc = time_kernel(fma32_probe, grid, &ms, sink, it32))) goto done;
+    if (fp32_fma_per_s) *fp32_fma_per_s = threads * it32 * kChains / (ms * 1e-3);
     if ((rc = time_kernel(mufu_probe, grid, &ms, sink, itmufu))) goto done;
     if (mufu_per_s) *mufu_per_s = threads * itmufu * kChains / (ms * 1e-3);
     if ((rc = time_kernel(fma64_probe, grid, &ms, (double *)sink, it64))) goto done;
     if (fp64_fma_per_s) *fp64_fma_per_s = threads * it64 * kChains / (ms * 1e-3);
+    if ((rc = time_kernel(mufu_mix_probe, grid, &ms, sink, itmufu / 4))) goto done;
+    if (mufu_mix_per_s) *mufu_mix_per_s = threads * (itmufu / 4) * kChains * 6.0 / (ms * 1e-3);
 done:
     cudaFree(sink);
-    cudaFree(cyc);
     return rc;
 }
