@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rjsmc", action="store_true")
     ap.add_argument("--rjsmc-only", action="store_true", help="run only the RJSMC measurement (profiling)")
+    ap.add_argument("--flight-line", type=int, default=0, metavar="S",
+                    help="run only the flight-line sampler: S soundings x 2048 particles in one sampler")
     return ap.parse_args()
 
 
@@ -135,14 +137,17 @@ def cpu_baseline(target_seconds=15.0):
                       f"{cores} threads), {elapsed:.1f} s"}
 
 
-def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0):
+def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
+                  reduce=None):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
     (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s."""
     from paper_2109_00661_gb300 import smc as S
     sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
-    y_true = L.forward_f32(sysg, I.to_torch(truth, torch.float32))[0].cpu().numpy().astype(np.float64)
-    y_obs = np.stack([I.noisy(y_true, seed=1000 + s) for s in range(n_soundings)])
+    y_true = L.forward_f32(sysg, I.to_torch(truth, torch.float32)).cpu().numpy().astype(np.float64)
+    if y_true.shape[0] == 1:  # one truth for every sounding, independent noise draws
+        y_true = np.repeat(y_true, n_soundings, axis=0)
+    y_obs = np.stack([I.noisy(y_true[s], seed=1000 + s) for s in range(n_soundings)])
     sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n_soundings,
                kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps)
     stream = torch.cuda.current_stream()
@@ -157,7 +162,10 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     sec = e0.elapsed_time(e1) * 1e-3
     post, lb, _ = sm.model_odds()
     evals = n_soundings * n_particles * (1 + stages * sweeps)
-    out = {"value": n_soundings / sec, "unit": "soundings/s", "seconds": sec, "stages": stages,
+    world_soundings = n_soundings
+    if reduce is not None:  # ranks run disjoint soundings: sum the work, take the slowest time
+        sec, world_soundings, evals = reduce(sec, n_soundings, evals)
+    out = {"value": world_soundings / sec, "unit": "soundings/s", "seconds": sec, "stages": stages,
            "forward_evals_per_s": evals / sec,
            "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
                      f"{sweeps} sweeps/stage, alpha=0.5, sounding system G=20 F=40 K=120",
@@ -209,6 +217,7 @@ def main():
 
     import paper_2109_00661_gb300 as L
     from paper_2109_00661_gb300 import inputs as I
+    from paper_2109_00661_gb300.shard import job_throughput
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -221,6 +230,11 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.flight_line:
+        truth, _ = I.flight_line(args.flight_line)
+        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth)
+        print(json.dumps({"flight_line": out}), flush=True)
+        return
     if args.rjsmc_only:
         print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())}), flush=True)
         return
@@ -262,7 +276,7 @@ def main():
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * P / (ms_max * 1e-3)
+    value = job_throughput([P] * world, [ms_max * 1e-3] * world)
 
     # end to end through the public API: pinned host inputs -> device -> loglik -> host
     e2e = None
@@ -299,6 +313,40 @@ def main():
         e2e = {"value": world * P / (float(te.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # the plain double-precision form of the same kernel on a 65,536-model block
+    fp64 = None
+    if rank == 0:
+        m64 = I.to_torch(I.subset(models_np, np.arange(1 << 16)), torch.float64)
+        L.loglik_f64(sysg, m64, y_obs, eps_an, I.EPS_MN)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        L.loglik_f64(sysg, m64, y_obs, eps_an, I.EPS_MN)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"value": (1 << 16) / (g0.elapsed_time(g1) * 1e-3), "unit": UNIT, "models": 1 << 16,
+                "dtype": "f64"}
+
+    # RJSMC soundings/s: the single-sounding configuration (N = 256, kappa <= 3,
+    # lambda <= 4, 10 sweeps per stage, 3-layer IP truth) batched over 128
+    # soundings per GPU, and the large one (N = 4096, kappa, lambda <= 9, 20
+    # sweeps, 5-layer truth) over 4 soundings per GPU; ranks run disjoint
+    # soundings (weak scaling by sounding)
+    def reduce(sec, n, evals):
+        if world == 1:
+            return sec, n, evals
+        t_ = torch.tensor([sec], dtype=torch.float64, device="cuda")
+        w_ = torch.tensor([float(n), float(evals)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w_, op=dist.ReduceOp.SUM)
+        return float(t_.item()), float(w_[0].item()), float(w_[1].item())
+
+    rjsmc = None
+    if not args.no_rjsmc:
+        rjsmc = (rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
+                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce))
+
     if rank == 0:
         flops = steps_work * FLOPS_PER_LAYER_STEP
         achieved = flops / (ms * 1e-3) / 1e12
@@ -323,13 +371,10 @@ def main():
             "peaks_measured": peaks,
             "e2e": e2e,
         }
-        if not args.no_rjsmc:
-            # RJSMC soundings/s: the single-sounding configuration (N = 256,
-            # kappa <= 3, lambda <= 4, 10 sweeps per stage, 3-layer IP truth)
-            # batched over 128 soundings, and the large one (N = 4096,
-            # kappa, lambda <= 9, 20 sweeps, 5-layer truth) over 4 soundings
-            line["rjsmc"] = rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())
-            line["rjsmc_large"] = rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer())
+        if fp64 is not None:
+            line["fp64_plain"] = fp64
+        if rjsmc is not None:
+            line["rjsmc"], line["rjsmc_large"] = rjsmc
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -107,3 +107,22 @@ def to_torch(models, dtype, device="cuda"):
 
 def subset(models, idx):
     return {k: np.asarray(v)[idx] for k, v in models.items()}
+
+
+def flight_line(n_soundings):
+    """Synthetic flight line: sounding s at x = s / (S - 1) over a 3-layer earth
+    (sigma 0.01, 0.1, 0.01 S/m) whose chargeable second layer (30 m thick,
+    tau = 1e-3 s, c = 0.5) starts at depth 50 - 30 cos(2 pi x) m (20..80 m)
+    with chargeability 0.25 (1 - cos(2 pi x)) (0..0.5)."""
+    S = n_soundings
+    x = np.arange(S) / max(S - 1, 1)
+    depth = 50.0 - 30.0 * np.cos(2 * np.pi * x)
+    m = 0.25 * (1.0 - np.cos(2 * np.pi * x))
+    return dict(
+        nlayers=np.full(S, 3, dtype=np.int8),
+        logsig=np.tile(np.log10([0.01, 0.1, 0.01]), (S, 1)),
+        logh=np.stack([np.log10(depth), np.full(S, np.log10(30.0)), np.zeros(S)], axis=1),
+        m=np.stack([np.zeros(S), m, np.zeros(S)], axis=1),
+        logtau=np.full((S, 3), -3.0),
+        c=np.full((S, 3), 0.5),
+    ), x
