@@ -137,6 +137,17 @@ int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *models, const do
 int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
                    const double *eps_an, double eps_mn, double *ll, double *gates, void *stream);
 
+/* Gradient of the log-likelihood above (FP32 forward model) with respect to
+ * every merged layer's parameters, by reverse-mode differentiation of the
+ * forward model of Section 2 and the likelihood of Section 2.3.2.
+ * grad: [device] P*lmax*5 floats, row-major [model][layer][parameter] with
+ * parameters (log10 sigma, log10 thickness, m, log10 tau, c); the basement's
+ * thickness entry and layers >= nlayers are 0.  ll: [device] P doubles (may
+ * be NULL).  Only the paper's Cole-Cole form (AEM_CC_PAPER) is supported;
+ * other forms return AEM_ERR_UNSUPPORTED. */
+int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                        const double *eps_an, double eps_mn, double *ll, float *grad, void *stream);
+
 /* ------------------------------------------------------------------------
  * RJSMC stage (Algorithm 1 with the adaptive choices of Section 3.2 and
  * Appendices B-E).

@@ -195,3 +195,31 @@ def merge(zc, logsig, zm, mval):
     L = lib().orc_merge(len(zc), _ptr(zc), _ptr(logsig), len(zm), _ptr(zm), _ptr(mval), _ptr(th), _ptr(ls),
                         _ptr(mm))
     return th[:L], ls[:L], mm[:L]
+
+
+PARAMS = ("logsig", "logh", "m", "logtau", "c")
+
+
+def loglik_grad_fd(models, system, y_obs, eps_an, eps_mn, step=1e-5, mode=HANKEL_RULE):
+    """FP64 gradient of the log-likelihood by central differences with respect
+    to every layer's (log10 sigma, log10 h, m, log10 tau, c): returns
+    (ll [P], grad [P, LMAX, 5]); entries past each model's layer count and the
+    basement thickness are 0."""
+    base = {k: np.array(models[k], dtype=np.float64, copy=True) for k in PARAMS}
+    nl = np.asarray(models["nlayers"])
+    P, LMAX = base["logsig"].shape
+    ll0 = loglik(forward(dict(base, nlayers=nl), system, mode=mode), y_obs, eps_an, eps_mn)
+    grad = np.zeros((P, LMAX, 5))
+    for pi, name in enumerate(PARAMS):
+        for n in range(LMAX):
+            active = (n < nl) & ~((name == "logh") & (n == nl - 1))
+            if not np.any(active):
+                continue
+            lp = {k: v.copy() for k, v in base.items()}
+            lm = {k: v.copy() for k, v in base.items()}
+            lp[name][:, n] += step
+            lm[name][:, n] -= step
+            fp = loglik(forward(dict(lp, nlayers=nl), system, mode=mode), y_obs, eps_an, eps_mn)
+            fm = loglik(forward(dict(lm, nlayers=nl), system, mode=mode), y_obs, eps_an, eps_mn)
+            grad[:, n, pi] = np.where(active, (fp - fm) / (2 * step), 0.0)
+    return ll0, grad

@@ -15,8 +15,8 @@ import numpy as np
 from . import _lib
 from ._lib import AEMError, check
 
-__all__ = ["System", "forward_f32", "forward_f64", "loglik_f32", "loglik_f64", "probe_peaks", "AEMError",
-           "CC_PAPER", "CC_PELTON"]
+__all__ = ["System", "forward_f32", "forward_f64", "loglik_f32", "loglik_f64", "loglik_grad_f32", "loglik",
+           "probe_peaks", "AEMError", "CC_PAPER", "CC_PELTON"]
 
 CC_PAPER = 0
 CC_PELTON = 1
@@ -146,6 +146,65 @@ def loglik_f64(system, models, y_obs, eps_an, eps_mn, want_gates=False, stream=N
     """aem_loglik_f64: the same likelihood on the double-precision forward model."""
     return _loglik(_lib.load().aem_loglik_f64, models, _torch().float64, y_obs, eps_an, eps_mn, system,
                    want_gates, stream)
+
+
+def loglik_grad_f32(system, models, y_obs, eps_an, eps_mn, stream=None):
+    """aem_loglik_grad_f32: (ll [P] float64, grad [P, lmax, 5] float32) with the
+    gradient taken with respect to (log10 sigma, log10 h, m, log10 tau, c)."""
+    torch = _torch()
+    ms = _models_struct(models, torch.float32)
+    P, lmax = ms.n_models, ms.lmax
+    dev = models["logsig"].device
+    y_obs = torch.as_tensor(y_obs, dtype=torch.float64, device=dev).contiguous()
+    eps_an = torch.as_tensor(eps_an, dtype=torch.float64, device=dev).expand(system.G).contiguous()
+    ll = torch.empty(P, dtype=torch.float64, device=dev)
+    grad = torch.empty((P, lmax, 5), dtype=torch.float32, device=dev)
+    check(_lib.load().aem_loglik_grad_f32(system.handle, ctypes.byref(ms), _dptr(y_obs), _dptr(eps_an),
+                                          float(eps_mn), _dptr(ll), _dptr(grad), _stream_ptr(stream)),
+          "aem_loglik_grad_f32")
+    return ll, grad
+
+
+PARAMS = ("logsig", "logh", "m", "logtau", "c")
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class _LogLik(torch.autograd.Function):
+        """ll(models) with the adjoint kernel's gradient as its backward: the
+        forward call runs aem_loglik_grad_f32 once (likelihood and gradient in
+        one launch) and backward only scales the stored gradient."""
+
+        @staticmethod
+        def forward(ctx, system, nlayers, y_obs, eps_an, eps_mn, logsig, logh, m, logtau, c):
+            models = dict(nlayers=nlayers, logsig=logsig.detach(), logh=logh.detach(), m=m.detach(),
+                          logtau=logtau.detach(), c=c.detach())
+            ll, grad = loglik_grad_f32(system, models, y_obs, eps_an, eps_mn)
+            ctx.save_for_backward(grad)
+            return ll
+
+        @staticmethod
+        def backward(ctx, g_ll):
+            (grad,) = ctx.saved_tensors
+            scale = g_ll.to(grad.dtype)[:, None]
+            return (None, None, None, None, None, *[scale * grad[:, :, i] for i in range(5)])
+
+    return _LogLik
+
+
+_LOGLIK_FN = None
+
+
+def loglik(system, models, y_obs, eps_an, eps_mn):
+    """Differentiable FP32 log-likelihood: a torch.autograd.Function whose
+    backward is the reverse-mode adjoint kernel.  models holds float32 CUDA
+    tensors (logsig, logh, m, logtau, c) of shape [P, lmax] (any of which may
+    require grad) and int8 nlayers [P]; returns ll [P] float64."""
+    global _LOGLIK_FN
+    if _LOGLIK_FN is None:
+        _LOGLIK_FN = _autograd_function()
+    return _LOGLIK_FN.apply(system, models["nlayers"], y_obs, eps_an, eps_mn, *[models[k] for k in PARAMS])
 
 
 def probe_peaks():

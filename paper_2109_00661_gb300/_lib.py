@@ -88,6 +88,8 @@ SIGNATURES = {
     "aem_loglik_f64": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                         c_void_p], c_int),
     "aem_probe_peaks": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "aem_loglik_grad_f32": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
+                             c_void_p], c_int),
     "smc_desc_defaults": ([ctypes.POINTER(SMCDesc)], c_int),
     "smc_create": ([c_void_p, ctypes.POINTER(SMCDesc), c_void_p, c_void_p, c_double, c_void_p,
                     ctypes.POINTER(c_void_p)], c_int),

@@ -1,0 +1,127 @@
+"""The reverse-mode gradient of the log-likelihood (FP32, through the C ABI)
+against central finite differences of the FP64 oracle and of the GPU's own
+FP64 forward model, on models near the single-sounding truth.
+
+Bar: per model, the relative gradient error |g - g_ref|_2 / |g_ref|_2 <= 1e-3;
+per component, |g - g_ref| <= 5e-3 max(|g_ref|, 1e-2 max_j |g_ref_j|) (the
+floor keeps near-zero components of a model from dominating)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2109_00661_gb300 import inputs as I
+from parity_util import bound32, loglik_bound, oracle_ref, oracle_system
+
+pytestmark = pytest.mark.gpu
+
+NAME = "sounding-g20-f40-k120"
+
+
+def near_truth(P, seed, L=3):
+    rng = np.random.default_rng(seed)
+    base_sig = np.log10([0.01, 0.1, 0.01, 0.03, 0.005])[:L]
+    base_h = np.log10([20.0, 30.0, 25.0, 40.0, 1.0])[:L]
+    m = dict(nlayers=np.full(P, L, dtype=np.int8),
+             logsig=base_sig + rng.uniform(-0.2, 0.2, (P, L)),
+             logh=base_h + rng.uniform(-0.1, 0.1, (P, L)),
+             m=rng.uniform(0.05, 0.5, (P, L)),
+             logtau=np.full((P, L), -3.0) + rng.uniform(-0.3, 0.3, (P, L)),
+             c=rng.uniform(0.3, 0.9, (P, L)))
+    for k in ("logsig", "logh", "m", "logtau", "c"):
+        m[k] = m[k].astype(np.float32).astype(np.float64)
+    return m
+
+
+def within(g, ref):
+    scale = np.maximum(np.abs(ref), 1e-2 * np.max(np.abs(ref), axis=(1, 2), keepdims=True))
+    return np.abs(g - ref) / scale
+
+
+def norm_err(g, ref):
+    return np.linalg.norm((g - ref).reshape(len(g), -1), axis=1) / np.linalg.norm(ref.reshape(len(g), -1), axis=1)
+
+
+def check(g, ref, what):
+    e = within(g, ref)
+    ne = norm_err(g, ref)
+    i = np.unravel_index(np.argmax(e), e.shape)
+    print(f"\n{what}: relative gradient error (norm) max {ne.max():.2e} median {np.median(ne):.2e}; "
+          f"component max {e.max():.2e} at (model, layer, param) {i}: {g[i]:.6e} vs {ref[i]:.6e}")
+    assert ne.max() <= 1e-3
+    assert e.max() <= 5e-3
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    import paper_2109_00661_gb300 as L
+    sysg = L.System(**I.system_kwargs(NAME))
+    s = oracle_system(NAME)
+    y_obs = I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=0)
+    return torch, L, sysg, s, y_obs
+
+
+@pytest.mark.parametrize("L_layers", [1, 3, 5])
+def test_gradient_matches_oracle_fd(setup, L_layers):
+    torch, L, sysg, s, y_obs = setup
+    models = near_truth(12, seed=L_layers, L=L_layers)
+    ll_ref, g_ref = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN)
+    ll, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    g = g.cpu().numpy().astype(np.float64)
+    check(g, g_ref, f"{L_layers} layers vs oracle FD")
+    # the likelihood value it returns is the FP32 forward path's, within the
+    # first-order bound the per-gate FP32 error bound gives
+    y_model, _, _, kap = oracle_ref(models, NAME)
+    bound = loglik_bound(y_model, y_obs, bound32(kap, sysg.F)) + 1e-9 * np.abs(ll_ref)
+    assert np.all(np.abs(ll.cpu().numpy() - ll_ref) <= bound)
+
+
+def test_gradient_matches_fd_of_gpu_fp64(setup):
+    torch, L, sysg, s, y_obs = setup
+    models = near_truth(8, seed=11, L=4)
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    g = g.cpu().numpy().astype(np.float64)
+    step = 1e-5
+    ref = np.zeros_like(g)
+    for pi, name in enumerate(O.PARAMS):
+        for n in range(4):
+            if name == "logh" and n == 3:
+                continue
+            lp = {k: np.array(v, copy=True) for k, v in models.items()}
+            lm = {k: np.array(v, copy=True) for k, v in models.items()}
+            lp[name][:, n] += step
+            lm[name][:, n] -= step
+            fp = L.loglik_f64(sysg, I.to_torch(lp, torch.float64), y_obs, I.EPS_AN, I.EPS_MN).cpu().numpy()
+            fm = L.loglik_f64(sysg, I.to_torch(lm, torch.float64), y_obs, I.EPS_AN, I.EPS_MN).cpu().numpy()
+            ref[:, n, pi] = (fp - fm) / (2 * step)
+    check(g, ref, "4 layers vs FD of the GPU FP64 forward")
+
+
+def test_gradient_zero_padding_and_unsupported_form(setup):
+    torch, L, sysg, s, y_obs = setup
+    models = near_truth(4, seed=3, L=3)
+    for k in ("logsig", "logh", "m", "logtau", "c"):
+        models[k] = np.concatenate([models[k], np.zeros((4, 2))], axis=1)  # lmax 5, 3 layers used
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    g = g.cpu().numpy()
+    assert np.all(g[:, 3:, :] == 0) and np.all(g[:, 2, 1] == 0)
+    pel = L.System(**I.system_kwargs(NAME), cc_form=L.CC_PELTON)
+    with pytest.raises(L.AEMError):
+        L.loglik_grad_f32(pel, I.to_torch(near_truth(2, seed=4), torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+
+
+def test_autograd_function(setup):
+    """The torch.autograd.Function path returns the adjoint kernel's gradient,
+    scaled by the upstream gradient, on every parameter tensor."""
+    torch, L, sysg, s, y_obs = setup
+    models = near_truth(6, seed=5, L=3)
+    tm = I.to_torch(models, torch.float32)
+    for k in L.PARAMS:
+        tm[k].requires_grad_(True)
+    ll = L.loglik(sysg, tm, y_obs, I.EPS_AN, I.EPS_MN)
+    w = torch.arange(1, 7, dtype=torch.float64, device=ll.device)
+    (ll * w).sum().backward()
+    ll2, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    assert torch.equal(ll.detach(), ll2)
+    for i, k in enumerate(L.PARAMS):
+        assert torch.allclose(tm[k].grad, w.float()[:, None] * g[:, :, i], rtol=1e-6, atol=0)

@@ -200,3 +200,23 @@ def test_merge_direct_sum():
     assert np.allclose(th[:-1], [10.0, 20.0, 20.0])
     assert np.allclose(ls, [-2.0, -1.0, -1.0, -3.0])
     assert np.allclose(m, [0.0, 0.0, 0.4, 0.4])
+
+
+def test_fd_gradient_is_step_consistent():
+    """The oracle's central-difference gradient agrees between two step sizes
+    (its truncation error is O(step^2): below 1e-5 of the gradient scale at the
+    default step of 1e-5)."""
+    from paper_2109_00661_gb300 import inputs as I
+    rng = np.random.default_rng(8)
+    P = 4
+    models = dict(nlayers=np.full(P, 3), logsig=np.log10([[0.01, 0.1, 0.01]] * P) + rng.uniform(-0.2, 0.2, (P, 3)),
+                  logh=np.log10([[20.0, 30.0, 1.0]] * P) + rng.uniform(-0.1, 0.1, (P, 3)),
+                  m=rng.uniform(0.05, 0.5, (P, 3)), logtau=np.full((P, 3), -3.0) + rng.uniform(-0.3, 0.3, (P, 3)),
+                  c=rng.uniform(0.3, 0.9, (P, 3)))
+    s = I.oracle_system("sounding-g20-f40-k120")
+    s["T"] = O.tmatrix(s["freqs"], s["times"])
+    y_obs = I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=0)
+    _, g1 = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN, step=2e-5)
+    _, g2 = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN, step=1e-5)
+    scale = np.max(np.abs(g2), axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(g1 - g2) / scale) < 1e-5
