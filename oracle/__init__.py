@@ -18,6 +18,12 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                    sine transform of w / (1 + (w tau)^2).
   forward       -- the above plus the late-time t^(-5/2) law at h = 30 m.
   loglik        -- hand-computed two-gate example (Section 2.3.2).
+  loglik_grad_fd -- central differences of loglik; step-convergence pin.
+  rjsmc.*       -- see oracle/rjsmc.py: toy closed-form evidence and model
+                   probabilities, bisection / resampling definitions; the
+                   Langevin move by invariance of a Gaussian target and the
+                   particle-space gradient against the chain rule of the
+                   merged-layer gradient.
 """
 from __future__ import annotations
 

@@ -15,6 +15,12 @@ one particle at a time, in the order the paper states the steps:
   odds       pi(k|y) = N_k / N (Section 3.2.1) and the BFIPD statistic of
              Section 2.3.3.
 
+Beyond the paper's kernels, an optional within-model Langevin (MALA) move on
+the particle's continuous parameters, with the gradient of the tempered
+target gamma_t l taken by central differences of the likelihood and the
+Metropolis-Hastings test including the proposal-density ratio (Roberts &
+Tweedie 1996); it leaves pi_t invariant like the paper's random walks do.
+
 Random numbers come from Philox4x32-10 (Salmon et al., SC 2011) written out
 here from its published definition, keyed per sounding and counted per
 (particle, draw, stage, sweep), so the GPU sampler can reproduce the same
@@ -122,6 +128,8 @@ class SMCSettings:
     seed: int = 0
     sounding: int = 0
     bisect_iters: int = 60
+    n_langevin: int = 0         # Langevin sweeps per stage after the random-walk sweeps
+    langevin_h: float = 0.5     # Langevin step, in units of the random-walk scales
 
     @property
     def n_models(self):
@@ -440,6 +448,124 @@ def accept_uniform(s: SMCSettings, i: int, stage: int, sweep: int):
     return float(u01_53(d[0], d[1]))
 
 
+# ------------------------------------------------- Langevin (MALA) moves
+PURPOSE_LANGEVIN_ACCEPT = 68
+PURPOSE_LANGEVIN0 = 72  # normal j: purpose 72 + j // 2, words 2 (j % 2) and 2 (j % 2) + 1
+
+
+def theta_of(p: Particle, s: SMCSettings):
+    """The continuous parameters of a particle in a fixed order:
+    (phi_b, phi_c[0..kappa), z_c[0..kappa), z_m[0..lambda), m[0..lambda), tau, c),
+    tau as log10 tau under the log-uniform prior (the random walk's coordinate)."""
+    t = math.log10(p.tau) if s.tau_log_prior else p.tau
+    return np.array([p.phib] + list(p.phic) + list(p.zc) + list(p.zm) + list(p.mv) + [t, p.c], dtype=np.float64)
+
+
+def with_theta(p: Particle, s: SMCSettings, theta) -> Particle:
+    k, l = p.kappa, p.lam
+    th = [float(v) for v in theta]
+    tau = 10.0 ** th[1 + 2 * k + 2 * l] if s.tau_log_prior else th[1 + 2 * k + 2 * l]
+    return Particle(k, l, th[0], th[1 + k:1 + 2 * k], th[1:1 + k], th[1 + 2 * k:1 + 2 * k + l],
+                    th[1 + 2 * k + l:1 + 2 * k + 2 * l], tau, th[2 + 2 * k + 2 * l])
+
+
+def theta_scales(p: Particle, s: SMCSettings):
+    """Per-component scale of the preconditioner: the random-walk step of the
+    component's kind."""
+    k, l = p.kappa, p.lam
+    return np.array([s.step_phi] * (1 + k) + [s.step_z] * (k + l) + [s.step_m] * l + [s.step_tau, s.step_c])
+
+
+def theta_in_support(p: Particle, s: SMCSettings) -> bool:
+    """Uniform prior support with ordered interfaces in each profile."""
+    if not in_prior(p, s):
+        return False
+    return all(a < b for a, b in zip(p.zc, p.zc[1:])) and all(a < b for a, b in zip(p.zm, p.zm[1:]))
+
+
+def theta_grad_fd(parts, s: SMCSettings, loglik, step=1e-5):
+    """d l / d theta by central differences of l(merge(theta)) with step
+    step * max(|theta_j|, 1e-3) in each component.  Returns (l, [grad per particle])."""
+    ll = np.asarray(loglik(parts), dtype=np.float64)
+    grads = []
+    for p in parts:
+        th = theta_of(p, s)
+        plus, minus, hs = [], [], []
+        for j in range(len(th)):
+            hj = step * max(abs(th[j]), 1e-3)
+            a = th.copy()
+            b = th.copy()
+            a[j] += hj
+            b[j] -= hj
+            plus.append(with_theta(p, s, a))
+            minus.append(with_theta(p, s, b))
+            hs.append(hj)
+        lp = np.asarray(loglik(plus), dtype=np.float64)
+        lm = np.asarray(loglik(minus), dtype=np.float64)
+        grads.append((lp - lm) / (2.0 * np.asarray(hs)))
+    return ll, grads
+
+
+def langevin_normals(s: SMCSettings, i: int, stage: int, sweep: int, d: int):
+    out = np.zeros(d)
+    for j in range(d):
+        w = draws(s.seed, s.sounding, i, PURPOSE_LANGEVIN0 + j // 2, stage, sweep)[0]
+        out[j] = float(gauss_pair(w[2 * (j % 2)], w[2 * (j % 2) + 1]))
+    return out
+
+
+def langevin_log_q(theta_to, theta_from, grad_from, scales, gamma, h):
+    """log q(theta_to | theta_from) up to a constant for the preconditioned
+    Langevin proposal N(theta + (h^2/2) D gamma grad, h^2 D), D = diag(scales^2)."""
+    mean = theta_from + 0.5 * h * h * scales * scales * gamma * grad_from
+    z = (theta_to - mean) / (h * scales)
+    return -0.5 * float(np.sum(z * z))
+
+
+def langevin_propose(p: Particle, grad, s: SMCSettings, i: int, stage: int, sweep: int, gamma: float):
+    """Returns (proposal or None outside the support, log q(proposal | p))."""
+    th = theta_of(p, s)
+    sc = theta_scales(p, s)
+    h = s.langevin_h
+    xi = langevin_normals(s, i, stage, sweep, len(th))
+    th_new = th + 0.5 * h * h * sc * sc * gamma * np.asarray(grad) + h * sc * xi
+    q = with_theta(p, s, th_new)
+    if not theta_in_support(q, s):
+        return None, 0.0
+    return q, -0.5 * float(np.sum(xi * xi))
+
+
+def langevin_accept_uniform(s: SMCSettings, i: int, stage: int, sweep: int):
+    d = draws(s.seed, s.sounding, i, PURPOSE_LANGEVIN_ACCEPT, stage, sweep)[0]
+    return float(u01_53(d[0], d[1]))
+
+
+def langevin_sweeps(parts, s: SMCSettings, stage: int, gamma: float, grad_fn, n_sweeps: int):
+    """n_sweeps MALA sweeps over every particle at gamma_t.  grad_fn maps a list
+    of particles to (l, [d l / d theta]).  Returns (particles, l, accepted, proposed)."""
+    ll, grads = grad_fn(parts)
+    parts = list(parts)
+    grads = list(grads)
+    ll = np.array(ll, dtype=np.float64)
+    acc = 0
+    for sweep in range(n_sweeps):
+        props = [langevin_propose(parts[i], grads[i], s, i, stage, sweep, gamma) for i in range(len(parts))]
+        live = [i for i in range(len(parts)) if props[i][0] is not None]
+        if live:
+            ll_new, g_new = grad_fn([props[i][0] for i in live])
+        for n, i in enumerate(live):
+            q, lq_fwd = props[i]
+            lq_rev = langevin_log_q(theta_of(parts[i], s), theta_of(q, s), g_new[n], theta_scales(q, s), gamma,
+                                    s.langevin_h)
+            u = langevin_accept_uniform(s, i, stage, sweep)
+            if math.log(u) < gamma * (ll_new[n] - ll[i]) + lq_rev - lq_fwd:
+                parts[i] = q
+                ll[i] = ll_new[n]
+                grads[i] = g_new[n]
+                acc += 1
+    return parts, ll, acc, n_sweeps * len(parts)
+
+
 # ------------------------------------------------------------------- driver
 @dataclass
 class SMCResult:
@@ -451,6 +577,8 @@ class SMCResult:
     accept: np.ndarray = None
     proposed: np.ndarray = None
     sweeps: list = field(default_factory=list)
+    langevin_accept: int = 0
+    langevin_proposed: int = 0
 
 
 class ForwardLik:
@@ -476,10 +604,11 @@ class ForwardLik:
         return self.O.loglik(y, self.y_obs, self.eps_an, self.eps_mn)
 
 
-def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=propose):
+def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=propose, grad_fn=None):
     """Algorithm 1: initialise from the prior, then reweight / resample /
     mutate until gamma = 1.  `loglik` maps a list of particles to their
-    log-likelihoods."""
+    log-likelihoods; with s.n_langevin > 0 every stage ends with that many
+    Langevin sweeps driven by grad_fn (default: theta_grad_fd on loglik)."""
     N = s.n_particles
     parts = [prior(s, i) for i in range(N)]
     ll = np.asarray(loglik(parts), dtype=np.float64)
@@ -518,6 +647,11 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
                     parts[i] = q
                     ll[i] = ll_new[i]
                     acc_stage[mv] += 1
+        if s.n_langevin > 0:
+            gfn = grad_fn if grad_fn is not None else (lambda ps: theta_grad_fd(ps, s, loglik))
+            parts, ll, la, lp = langevin_sweeps(parts, s, stage, gamma, gfn, s.n_langevin)
+            res.langevin_accept += la
+            res.langevin_proposed += lp
         acc += acc_stage
         prop += prop_stage
         rates = np.where(prop_stage > 0, acc_stage / np.maximum(prop_stage, 1), 1.0)
