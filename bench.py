@@ -138,10 +138,12 @@ def cpu_baseline(target_seconds=15.0):
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
-                  reduce=None):
+                  reduce=None, n_langevin=0):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
-    (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s."""
+    (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s.  With
+    n_langevin > 0 every stage ends with that many adjoint-driven Langevin
+    sweeps (adapted step)."""
     from paper_2109_00661_gb300 import smc as S
     sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
     y_true = L.forward_f32(sysg, I.to_torch(truth, torch.float32)).cpu().numpy().astype(np.float64)
@@ -149,7 +151,7 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
         y_true = np.repeat(y_true, n_soundings, axis=0)
     y_obs = np.stack([I.noisy(y_true[s], seed=1000 + s) for s in range(n_soundings)])
     sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n_soundings,
-               kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps)
+               kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps, n_langevin=n_langevin)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -162,14 +164,21 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     sec = e0.elapsed_time(e1) * 1e-3
     post, lb, _ = sm.model_odds()
     evals = n_soundings * n_particles * (1 + stages * sweeps)
+    lang = None
+    if n_langevin:
+        acc, prop, h = sm.langevin_stats()
+        lang = {"sweeps_per_stage": n_langevin, "gradient_evals": n_soundings * n_particles * stages * (n_langevin + 1),
+                "last_stage_acceptance": float(acc.sum() / max(prop.sum(), 1)), "median_step_h": float(np.median(h))}
     world_soundings = n_soundings
     if reduce is not None:  # ranks run disjoint soundings: sum the work, take the slowest time
         sec, world_soundings, evals = reduce(sec, n_soundings, evals)
     out = {"value": world_soundings / sec, "unit": "soundings/s", "seconds": sec, "stages": stages,
            "forward_evals_per_s": evals / sec,
            "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
-                     f"{sweeps} sweeps/stage, alpha=0.5, sounding system G=20 F=40 K=120",
+                     f"{sweeps} sweeps/stage" + (f" + {n_langevin} Langevin sweeps/stage" if n_langevin else "") +
+                     ", alpha=0.5, sounding system G=20 F=40 K=120",
            "median_log_bfipd": float(np.median(np.clip(lb, -50, 50))),
+           "langevin": lang,
            "mean_p_ip": float(np.mean(post.reshape(n_soundings, kappa_max + 1, lambda_max + 1)[:, :, 1:].sum(axis=(1, 2))))}
     sm.close()
     sysg.close()
@@ -328,6 +337,28 @@ def main():
         fp64 = {"value": (1 << 16) / (g0.elapsed_time(g1) * 1e-3), "unit": UNIT, "models": 1 << 16,
                 "dtype": "f64"}
 
+    # the adjoint: log-likelihood and its gradient with respect to every
+    # layer's (log10 sigma, log10 h, m, log10 tau, c) for 65,536 of the same
+    # random models (1..10 layers), one aem_loglik_grad_f32 launch per step
+    adjoint = None
+    if rank == 0 and not args.no_rjsmc:
+        na = 1 << 16
+        ma = I.to_torch(I.subset(models_np, np.arange(na)), torch.float32)
+        for _ in range(3):
+            L.loglik_grad_f32(sysg, ma, y_obs, eps_an, I.EPS_MN, stream=stream)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            L.loglik_grad_f32(sysg, ma, y_obs, eps_an, I.EPS_MN, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1) / args.steps
+        adjoint = {"value": na / (ams * 1e-3), "unit": "gradient evals/s", "models": na, "ms_per_launch": ams,
+                   "dtype": "f32", "relative_cost_vs_loglik": (ams / na) / (ms / P),
+                   "config": f"{WORKLOAD}: {na} random models, 1..10 layers, 5 parameters per layer"}
+
     # RJSMC soundings/s: the single-sounding configuration (N = 256, kappa <= 3,
     # lambda <= 4, 10 sweeps per stage, 3-layer IP truth) batched over 128
     # soundings per GPU, and the large one (N = 4096, kappa, lambda <= 9, 20
@@ -345,7 +376,9 @@ def main():
     rjsmc = None
     if not args.no_rjsmc:
         rjsmc = (rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
-                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce))
+                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce),
+                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce,
+                               n_langevin=2))
 
     if rank == 0:
         flops = steps_work * FLOPS_PER_LAYER_STEP
@@ -374,7 +407,9 @@ def main():
         if fp64 is not None:
             line["fp64_plain"] = fp64
         if rjsmc is not None:
-            line["rjsmc"], line["rjsmc_large"] = rjsmc
+            line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"] = rjsmc
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

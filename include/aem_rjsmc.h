@@ -166,6 +166,9 @@ int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *models, con
 #define AEM_SMC_SLOTS 10           /* interface slots per profile: kappa_max, lambda_max <= 9 */
 #define AEM_SMC_MAX_MODELS 100     /* (kappa_max + 1) (lambda_max + 1) */
 #define AEM_SMC_MAX_PARTICLES 16384 /* particles per sounding */
+/* Particle-space gradient row: phi_b, phi_c[SLOTS], z_c[SLOTS], z_m[SLOTS],
+ * m[SLOTS], tau coordinate, c (slots past kappa / lambda are 0). */
+#define AEM_SMC_GRAD_DIM (3 + 4 * AEM_SMC_SLOTS)
 
 typedef struct {
     int n_particles;   /* N per sounding, 2..AEM_SMC_MAX_PARTICLES */
@@ -182,6 +185,9 @@ typedef struct {
     double logtau_lo, logtau_hi;
     unsigned long long seed;
     int bisect_iters;                      /* bisection iterations for gamma_t (1..200) */
+    int n_langevin;                        /* Langevin sweeps per stage after the random walks (0..1000; 0: off) */
+    double langevin_h;                     /* initial Langevin step h in units of the random-walk scales (> 0) */
+    int langevin_adapt;                    /* 1: after each stage h <- h exp(2 (rate - 0.574)), in [1e-6, 10] */
 } smc_desc;
 
 typedef struct smc_state smc_state;
@@ -197,7 +203,8 @@ typedef struct {
 } smc_particles_host;
 
 /* Fills *d with the defaults (N = 256, kappa_max = 3, lambda_max = 4,
- * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2)). */
+ * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2),
+ * no Langevin sweeps, langevin_h = 0.1, langevin_adapt = 1). */
 int smc_desc_defaults(smc_desc *d);
 
 /* Synchronous.  y_obs [host, S x G] observed gates per sounding; eps_an [host, G];
@@ -229,7 +236,20 @@ int smc_resample(smc_state *st);
  * conductive birth, conductive death, chargeable birth, chargeable death,
  * depth move and Gaussian random walk (impossible moves count as rejected),
  * evaluates the proposals through the FP32 forward model and accepts with
- * probability min(1, exp(gamma_t (l' - l))).  Synchronises at the end. */
+ * probability min(1, exp(gamma_t (l' - l))).  Then desc.n_langevin
+ * within-model Langevin (MALA) sweeps, a move the paper does not use: with
+ * theta the particle's continuous parameters (phi_b, phi_c, z_c, z_m, m, the
+ * tau coordinate, c), D = diag(s_j^2) of the random-walk steps and h the
+ * sounding's current step (desc.langevin_h after smc_init; with
+ * desc.langevin_adapt, updated after each call from that call's Langevin
+ * acceptance rate towards 0.574, Roberts & Rosenthal 1998), the proposal is
+ *   theta' = theta + (h^2 / 2) D gamma_t grad l(theta) + h D^(1/2) xi,
+ * the gradient coming from the adjoint kernel (aem_loglik_grad_f32) mapped
+ * through the direct sum; it is accepted when
+ *   ln u < gamma_t (l' - l) + log q(theta | theta') - log q(theta' | theta)
+ * and rejected outside the prior support or the interface order.  The
+ * Langevin tests compare likelihoods from the adjoint kernel on both sides.
+ * Synchronises at the end. */
 int smc_mutate(smc_state *st, int n_sweeps);
 
 /* Proposal step only (for inspection): proposals for (stage, sweep) from the
@@ -238,6 +258,33 @@ int smc_propose(smc_state *st, int stage, int sweep);
 
 /* Re-evaluates the log-likelihood of the current particles. */
 int smc_loglik_current(smc_state *st);
+
+/* Log-likelihood (into the current particles' ll) and the gradient of the
+ * log-likelihood with respect to each current particle's parameters, by the
+ * adjoint kernel and the chain rule through the direct sum (Section 2.1).
+ * grad_host: [host] P x AEM_SMC_GRAD_DIM floats (may be NULL: the gradient is
+ * then only kept on the device for smc_langevin_propose); the tau slot is
+ * d l / d tau [s] with the uniform tau prior and d l / d log10 tau with the
+ * log-uniform one.  Synchronous when grad_host is not NULL. */
+int smc_grad_current(smc_state *st, float *grad_host);
+
+/* Langevin proposal step only (for inspection): proposals for (stage, sweep)
+ * from the current particles and the gradient of the last smc_grad_current
+ * into the proposal set (valid flags as for smc_propose), at each sounding's
+ * current gamma and step.  AEM_ERR_INVALID_ARG when no gradient of the current
+ * particles is held (none computed, or the particles changed since). */
+int smc_langevin_propose(smc_state *st, int stage, int sweep);
+
+/* n_sweeps (0..1000) Langevin sweeps alone, at the current stage and each
+ * sounding's current gamma and step (sweep counters 0..n_sweeps-1, as
+ * smc_mutate uses them after its random-walk sweeps; the step is not
+ * adapted).  Synchronises at the end. */
+int smc_langevin(smc_state *st, int n_sweeps);
+
+/* Synchronous.  accepted / proposed [S]: Langevin counts of the last
+ * smc_mutate or smc_langevin call; h [S]: each sounding's current step.  Any
+ * pointer may be NULL. */
+int smc_langevin_stats(const smc_state *st, int *accepted, int *proposed, double *h);
 
 /* Runs reweight / resample / mutate until gamma = 1 for every sounding or
  * max_stages stages (Alg. 1).  stages_out may be NULL. */

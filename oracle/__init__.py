@@ -19,6 +19,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   forward       -- the above plus the late-time t^(-5/2) law at h = 30 m.
   loglik        -- hand-computed two-gate example (Section 2.3.2).
   loglik_grad_fd -- central differences of loglik; step-convergence pin.
+  forward_jacobian_fd -- central differences of the gates; the chain rule
+                   sum_g dl/dy_g J_g reproduces loglik_grad_fd.
   rjsmc.*       -- see oracle/rjsmc.py: toy closed-form evidence and model
                    probabilities, bisection / resampling definitions; the
                    Langevin move by invariance of a Gaussian target and the
@@ -229,3 +231,27 @@ def loglik_grad_fd(models, system, y_obs, eps_an, eps_mn, step=1e-5, mode=HANKEL
             fm = loglik(forward(dict(lm, nlayers=nl), system, mode=mode), y_obs, eps_an, eps_mn)
             grad[:, n, pi] = np.where(active, (fp - fm) / (2 * step), 0.0)
     return ll0, grad
+
+
+def forward_jacobian_fd(models, system, step=1e-5, mode=HANKEL_RULE):
+    """FP64 Jacobian of the gates with respect to every layer's (log10 sigma,
+    log10 h, m, log10 tau, c) by central differences: returns (y [P, G],
+    jac [P, G, LMAX, 5]), zero past each model's layer count and for the
+    basement thickness."""
+    base = {k: np.array(models[k], dtype=np.float64, copy=True) for k in PARAMS}
+    nl = np.asarray(models["nlayers"])
+    P, LMAX = base["logsig"].shape
+    y0 = forward(dict(base, nlayers=nl), system, mode=mode)
+    jac = np.zeros((P, y0.shape[1], LMAX, 5))
+    for pi, name in enumerate(PARAMS):
+        for n in range(LMAX):
+            active = (n < nl) & ~((name == "logh") & (n == nl - 1))
+            if not np.any(active):
+                continue
+            lp = {k: v.copy() for k, v in base.items()}
+            lm = {k: v.copy() for k, v in base.items()}
+            lp[name][:, n] += step
+            lm[name][:, n] -= step
+            d = (forward(dict(lp, nlayers=nl), system, mode=mode) - forward(dict(lm, nlayers=nl), system, mode=mode))
+            jac[:, :, n, pi] = np.where(active[:, None], d / (2 * step), 0.0)
+    return y0, jac

@@ -129,7 +129,8 @@ class SMCSettings:
     sounding: int = 0
     bisect_iters: int = 60
     n_langevin: int = 0         # Langevin sweeps per stage after the random-walk sweeps
-    langevin_h: float = 0.5     # Langevin step, in units of the random-walk scales
+    langevin_h: float = 0.1     # initial Langevin step, in units of the random-walk scales
+    langevin_adapt: bool = True  # adapt the step between stages towards LANGEVIN_TARGET acceptance
 
     @property
     def n_models(self):
@@ -450,6 +451,8 @@ def accept_uniform(s: SMCSettings, i: int, stage: int, sweep: int):
 
 # ------------------------------------------------- Langevin (MALA) moves
 PURPOSE_LANGEVIN_ACCEPT = 68
+LANGEVIN_TARGET = 0.574          # optimal MALA acceptance rate (Roberts & Rosenthal 1998)
+LANGEVIN_H_MIN, LANGEVIN_H_MAX = 1e-6, 10.0
 PURPOSE_LANGEVIN0 = 72  # normal j: purpose 72 + j // 2, words 2 (j % 2) and 2 (j % 2) + 1
 
 
@@ -522,11 +525,11 @@ def langevin_log_q(theta_to, theta_from, grad_from, scales, gamma, h):
     return -0.5 * float(np.sum(z * z))
 
 
-def langevin_propose(p: Particle, grad, s: SMCSettings, i: int, stage: int, sweep: int, gamma: float):
+def langevin_propose(p: Particle, grad, s: SMCSettings, i: int, stage: int, sweep: int, gamma: float, h=None):
     """Returns (proposal or None outside the support, log q(proposal | p))."""
     th = theta_of(p, s)
     sc = theta_scales(p, s)
-    h = s.langevin_h
+    h = s.langevin_h if h is None else h
     xi = langevin_normals(s, i, stage, sweep, len(th))
     th_new = th + 0.5 * h * h * sc * sc * gamma * np.asarray(grad) + h * sc * xi
     q = with_theta(p, s, th_new)
@@ -540,23 +543,30 @@ def langevin_accept_uniform(s: SMCSettings, i: int, stage: int, sweep: int):
     return float(u01_53(d[0], d[1]))
 
 
-def langevin_sweeps(parts, s: SMCSettings, stage: int, gamma: float, grad_fn, n_sweeps: int):
-    """n_sweeps MALA sweeps over every particle at gamma_t.  grad_fn maps a list
-    of particles to (l, [d l / d theta]).  Returns (particles, l, accepted, proposed)."""
+def langevin_step_update(h, accepted, proposed):
+    """Between stages: h <- h exp(2 (rate - LANGEVIN_TARGET)), clamped."""
+    rate = accepted / proposed if proposed > 0 else LANGEVIN_TARGET
+    return min(max(h * math.exp(2.0 * (rate - LANGEVIN_TARGET)), LANGEVIN_H_MIN), LANGEVIN_H_MAX)
+
+
+def langevin_sweeps(parts, s: SMCSettings, stage: int, gamma: float, grad_fn, n_sweeps: int, h=None):
+    """n_sweeps MALA sweeps over every particle at gamma_t with step h (default
+    s.langevin_h).  grad_fn maps a list of particles to (l, [d l / d theta]).
+    Returns (particles, l, accepted, proposed)."""
+    h = s.langevin_h if h is None else h
     ll, grads = grad_fn(parts)
     parts = list(parts)
     grads = list(grads)
     ll = np.array(ll, dtype=np.float64)
     acc = 0
     for sweep in range(n_sweeps):
-        props = [langevin_propose(parts[i], grads[i], s, i, stage, sweep, gamma) for i in range(len(parts))]
+        props = [langevin_propose(parts[i], grads[i], s, i, stage, sweep, gamma, h) for i in range(len(parts))]
         live = [i for i in range(len(parts)) if props[i][0] is not None]
         if live:
             ll_new, g_new = grad_fn([props[i][0] for i in live])
         for n, i in enumerate(live):
             q, lq_fwd = props[i]
-            lq_rev = langevin_log_q(theta_of(parts[i], s), theta_of(q, s), g_new[n], theta_scales(q, s), gamma,
-                                    s.langevin_h)
+            lq_rev = langevin_log_q(theta_of(parts[i], s), theta_of(q, s), g_new[n], theta_scales(q, s), gamma, h)
             u = langevin_accept_uniform(s, i, stage, sweep)
             if math.log(u) < gamma * (ll_new[n] - ll[i]) + lq_rev - lq_fwd:
                 parts[i] = q
@@ -579,6 +589,7 @@ class SMCResult:
     sweeps: list = field(default_factory=list)
     langevin_accept: int = 0
     langevin_proposed: int = 0
+    langevin_h: list = field(default_factory=list)
 
 
 class ForwardLik:
@@ -618,6 +629,7 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
     acc = np.zeros(6)
     prop = np.zeros(6)
     p_min = 0.0
+    h_lang = s.langevin_h
     for stage in range(1, max_stages + 1):
         model = np.array([p.model(s) for p in parts])
         dg, done, inc, W = reweight(ll, model, s.n_models, gamma, s.alpha, s.bisect_iters)
@@ -649,9 +661,12 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
                     acc_stage[mv] += 1
         if s.n_langevin > 0:
             gfn = grad_fn if grad_fn is not None else (lambda ps: theta_grad_fd(ps, s, loglik))
-            parts, ll, la, lp = langevin_sweeps(parts, s, stage, gamma, gfn, s.n_langevin)
+            parts, ll, la, lp = langevin_sweeps(parts, s, stage, gamma, gfn, s.n_langevin, h_lang)
             res.langevin_accept += la
             res.langevin_proposed += lp
+            res.langevin_h.append(h_lang)
+            if s.langevin_adapt:
+                h_lang = langevin_step_update(h_lang, la, lp)
         acc += acc_stage
         prop += prop_stage
         rates = np.where(prop_stage > 0, acc_stage / np.maximum(prop_stage, 1), 1.0)

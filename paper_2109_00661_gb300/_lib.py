@@ -67,6 +67,9 @@ class SMCDesc(ctypes.Structure):
         ("logtau_hi", c_double),
         ("seed", ctypes.c_ulonglong),
         ("bisect_iters", c_int),
+        ("n_langevin", c_int),
+        ("langevin_h", c_double),
+        ("langevin_adapt", c_int),
     ]
 
 
@@ -100,6 +103,10 @@ SIGNATURES = {
     "smc_mutate": ([c_void_p, c_int], c_int),
     "smc_propose": ([c_void_p, c_int, c_int], c_int),
     "smc_loglik_current": ([c_void_p], c_int),
+    "smc_grad_current": ([c_void_p, c_void_p], c_int),
+    "smc_langevin_propose": ([c_void_p, c_int, c_int], c_int),
+    "smc_langevin": ([c_void_p, c_int], c_int),
+    "smc_langevin_stats": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_run": ([c_void_p, c_int, c_int, c_void_p], c_int),
     "smc_model_odds": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_stats": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                                                           const float *__restrict__ g_lam,
                                                           const float *__restrict__ g_hw,
                                                           const float *__restrict__ g_T,
-                                                          const double *__restrict__ y_obs,
+                                                          const double *__restrict__ y_obs, int obs_per,
                                                           const double *__restrict__ eps_an, double eps_mn,
                                                           double *__restrict__ ll_out, float *__restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
             const double yh = (double)acc;
             const double ea = eps_an[tid];
             const double v = ea * ea + (eps_mn * yh) * (eps_mn * yh);
-            const double r = y_obs[tid] - yh;
+            const double r = y_obs[(size_t)(p / obs_per) * G + tid] - yh;
             term = r * r / v + log(2.0 * kPi * v);
             dldy[tid] = r / v + (eps_mn * eps_mn * yh / v) * (r * r / v - 1.0);
         }
@@ -333,15 +333,11 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
 
 using namespace aem;
 
-extern "C" int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
-                                   const double *eps_an, double eps_mn, double *ll, float *grad, void *stream) {
-    if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: NULL system or models");
-    if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
-        return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
-    if (models->n_models == 0) return AEM_OK;
-    if (!grad || !y_obs || !eps_an || !models->nlayers || !models->logsig || !models->logh || !models->m ||
-        !models->logtau || !models->c)
-        return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: NULL pointer");
+namespace aem {
+
+int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                              int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
+                              cudaStream_t stream) {
     const SystemTables &h = sys->host;
     if (h.cc_form != AEM_CC_PAPER)
         return fail(AEM_ERR_UNSUPPORTED, "aem_loglik_grad_f32: only the paper's Cole-Cole form is differentiated");
@@ -358,9 +354,23 @@ extern "C" int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *
     if (grid > models->n_models) grid = models->n_models;
     GradModels gm{models->n_models, models->lmax, models->nlayers, models->logsig, models->logh,
                   models->m, models->logtau, models->c};
-    kern<<<(unsigned)grid, kGT, smem, (cudaStream_t)stream>>>(gm, h.F, h.G, h.K, LS, sys->d_omega_f, sys->d_lam_f,
-                                                              sys->d_hw_f, sys->d_T_f, y_obs, eps_an, eps_mn, ll,
-                                                              grad);
+    kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, sys->d_omega_f, sys->d_lam_f, sys->d_hw_f,
+                                                sys->d_T_f, y_obs, models_per_sounding, eps_an, eps_mn, ll, grad);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
+}
+
+}  // namespace aem
+
+extern "C" int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                                   const double *eps_an, double eps_mn, double *ll, float *grad, void *stream) {
+    if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: NULL system or models");
+    if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
+        return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
+    if (models->n_models == 0) return AEM_OK;
+    if (!grad || !y_obs || !eps_an || !models->nlayers || !models->logsig || !models->logh || !models->m ||
+        !models->logtau || !models->c)
+        return fail(AEM_ERR_INVALID_ARG, "aem_loglik_grad_f32: NULL pointer");
+    return loglik_grad_f32_soundings(sys, models, y_obs, models->n_models, eps_an, eps_mn, ll, grad,
+                                     (cudaStream_t)stream);
 }

@@ -7,6 +7,9 @@
 //               Gaussian random walks, then the batched forward model and the
 //               tempered Metropolis-Hastings test;
 //   odds      - model counts, pi(k|y) = N_k / N and the BFIPD statistic.
+// Optionally each stage ends with within-model Langevin (MALA) sweeps on the
+// particles' continuous parameters, driven by the adjoint gradient of the
+// log-likelihood (adjoint.cu) mapped back through the direct sum.
 // Soundings are independent: per-sounding kernels run one CTA per sounding,
 // per-particle kernels one thread per particle.  Random numbers come from
 // Philox4x32-10 keyed by (seed, sounding) and counted by (particle, purpose,
@@ -30,6 +33,15 @@ constexpr int kMoves = 6;
 constexpr int kGroupThreads = 1024;
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kPurposeMove = 64, kPurposeValue = 65, kPurposeAccept = 66, kPurposeResample = 67;
+// Langevin: acceptance uniform, and normal j of the proposal from words
+// 2 (j % 2), 2 (j % 2) + 1 of the block with purpose kPurposeLangevin0 + j / 2.
+constexpr int kPurposeLangevinAccept = 68, kPurposeLangevin0 = 72;
+// Particle-space gradient slots: phi_b, phi_c[KS], z_c[KS], z_m[KS], m[KS],
+// tau coordinate, c.
+constexpr int GD = AEM_SMC_GRAD_DIM;
+constexpr int G_PHIB = 0, G_PHIC = 1, G_ZC = 1 + AEM_SMC_SLOTS, G_ZM = 1 + 2 * AEM_SMC_SLOTS,
+              G_MV = 1 + 3 * AEM_SMC_SLOTS, G_TAU = 1 + 4 * AEM_SMC_SLOTS, G_C = 2 + 4 * AEM_SMC_SLOTS;
+static_assert(G_C + 1 == AEM_SMC_GRAD_DIM, "gradient slot layout");
 // Prior draw layout: draw d is word d % 4 of the block with purpose d / 4.
 constexpr int kPriorSlots = 16;
 constexpr int D_KAPPA = 0, D_LAM = 1, D_PHIB = 2, D_TAU = 3, D_C = 4, D_ZC = 5, D_PHIC = D_ZC + kPriorSlots,
@@ -570,6 +582,202 @@ __global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const
     }
 }
 
+// ------------------------------------------------- Langevin (MALA) moves
+// Chain rule from the merged-layer gradient [P][LMS][5] of (log10 sigma,
+// log10 h, m, log10 tau, c) to the particle's parameters, following the
+// direct sum of merge_kernel (same interface order, same tie rule): a layer's
+// log10 sigma belongs to phi_b or the conductive value above it, its m to the
+// chargeable value above it; an interface at merged position q thickens layer
+// q and thins layer q + 1; tau and c are shared by every layer.
+__global__ void pgrad_kernel(PState st, const float *mgrad, int P, int LMS, int tau_log_prior, float *pg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const int kappa = st.kappa[i], lam = st.lam[i];
+    float z[2 * KS];
+    int src[2 * KS];  // >= 0: conductive index; < 0: -(chargeable index) - 1
+    int a = 0, b = 0, n = 0;
+    while (a < kappa || b < lam) {
+        float za = a < kappa ? st.zc[i * KS + a] : 3.0e38f;
+        float zb = b < lam ? st.zm[i * KS + b] : 3.0e38f;
+        if (za <= zb) {
+            src[n] = a;
+            z[n++] = za;
+            ++a;
+        } else {
+            src[n] = -b - 1;
+            z[n++] = zb;
+            ++b;
+        }
+    }
+    const int L = n + 1;
+    float g[GD];
+#pragma unroll
+    for (int q = 0; q < GD; ++q) g[q] = 0.f;
+    double dl_dh[2 * KS + 1];
+    double slt = 0.0, sc = 0.0;
+    const double ln10 = 2.302585092994046;
+    int ic = 0, jm = 0;
+    for (int q = 0; q < L; ++q) {
+        const float top = q == 0 ? 0.f : z[q - 1];
+        if (q > 0) {
+            while (ic < kappa && st.zc[i * KS + ic] <= top) ++ic;
+            while (jm < lam && st.zm[i * KS + jm] <= top) ++jm;
+        }
+        const float *gm = mgrad + ((size_t)i * LMS + q) * 5;
+        if (ic == 0)
+            g[G_PHIB] += gm[0];
+        else
+            g[G_PHIC + ic - 1] += gm[0];
+        if (jm > 0) g[G_MV + jm - 1] += gm[2];
+        if (q < L - 1) {
+            double th = (double)z[q] - (double)top;
+            th = th > 1e-30 ? th : 1e-30;
+            dl_dh[q] = (double)gm[1] / (th * ln10);
+        }
+        slt += gm[3];
+        sc += gm[4];
+    }
+    for (int q = 0; q < n; ++q) {
+        const double d = dl_dh[q] - (q + 1 < n ? dl_dh[q + 1] : 0.0);
+        if (src[q] >= 0)
+            g[G_ZC + src[q]] += (float)d;
+        else
+            g[G_ZM - src[q] - 1] += (float)d;
+    }
+    g[G_TAU] = tau_log_prior ? (float)slt : (float)(slt / ((double)st.tau[i] * ln10));
+    g[G_C] = (float)sc;
+#pragma unroll
+    for (int q = 0; q < GD; ++q) pg[(size_t)i * GD + q] = g[q];
+}
+
+// Component j of the particle's continuous vector theta (phi_b, phi_c[kappa],
+// z_c[kappa], z_m[lambda], m[lambda], tau coordinate, c): its storage, its
+// gradient slot and its preconditioner scale (the random walk's step).
+struct ThetaRef {
+    float *x;
+    int slot;
+    double scale;
+    bool is_tau;
+};
+
+__device__ inline ThetaRef theta_ref(PState ps, int i, int j, int kappa, int lam, const Params &pr) {
+    if (j == 0) return {&ps.phib[i], G_PHIB, pr.step_phi, false};
+    j -= 1;
+    if (j < kappa) return {&ps.phic[i * KS + j], G_PHIC + j, pr.step_phi, false};
+    j -= kappa;
+    if (j < kappa) return {&ps.zc[i * KS + j], G_ZC + j, pr.step_z, false};
+    j -= kappa;
+    if (j < lam) return {&ps.zm[i * KS + j], G_ZM + j, pr.step_z, false};
+    j -= lam;
+    if (j < lam) return {&ps.mv[i * KS + j], G_MV + j, pr.step_m, false};
+    j -= lam;
+    if (j == 0) return {&ps.tau[i], G_TAU, pr.step_tau, true};
+    return {&ps.c[i], G_C, pr.step_c, false};
+}
+
+__device__ inline double theta_value(const ThetaRef &r, const Params &pr) {
+    const double v = (double)*r.x;
+    return (r.is_tau && pr.tau_log_prior) ? log10(v) : v;
+}
+
+__device__ inline bool ordered_open(const float *z, int n, double zmax) {
+    for (int q = 0; q < n; ++q) {
+        const double lo = q > 0 ? (double)z[q - 1] : 0.0;
+        if (!((double)z[q] > lo)) return false;
+    }
+    return n == 0 || (double)z[n - 1] < zmax;
+}
+
+// Preconditioned Langevin proposal at gamma_t:
+//   theta' = theta + (h^2 / 2) D gamma_t grad l(theta) + h D^(1/2) xi,
+//   D = diag(scale_j^2), xi ~ N(0, I);
+// valid when theta' is inside the uniform prior support with ordered
+// interfaces; lq = log q(theta' | theta) = -|xi|^2 / 2 (+ const).
+__global__ void langevin_propose_kernel(PState cur, PState prop, const float *gcur, const double *gamma,
+                                        const double *lang_h, Params pr, int stage, int sweep, int8_t *valid_out,
+                                        double *lq) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    const int s = i / pr.N, jp = i - s * pr.N;
+    const Key key = stream_key(pr.seed, s);
+    copy_particle(prop, i, cur, i);
+    const int kappa = cur.kappa[i], lam = cur.lam[i];
+    const int d = 3 + 2 * kappa + 2 * lam;
+    const double gm = gamma[s], h = lang_h[s];
+    double lqf = 0.0;
+    uint32_t w[4];
+    for (int j = 0; j < d; ++j) {
+        if ((j & 1) == 0)
+            block_draws(w, key, (uint32_t)jp, (uint32_t)(kPurposeLangevin0 + j / 2), (uint32_t)stage,
+                        (uint32_t)sweep);
+        const double xi = gauss(w[2 * (j & 1)], w[2 * (j & 1) + 1]);
+        const ThetaRef rc = theta_ref(cur, i, j, kappa, lam, pr);
+        const ThetaRef rp = theta_ref(prop, i, j, kappa, lam, pr);
+        const double sc = rc.scale;
+        const double th = theta_value(rc, pr) + 0.5 * h * h * sc * sc * gm * (double)gcur[(size_t)i * GD + rc.slot] +
+                          h * sc * xi;
+        *rp.x = (float)((rp.is_tau && pr.tau_log_prior) ? pow(10.0, th) : th);
+        lqf -= 0.5 * xi * xi;
+    }
+    bool ok = in_bounds_open(prop.phib[i], pr.phi_lo, pr.phi_hi) && in_bounds_open(prop.c[i], 0.0, 1.0);
+    for (int q = 0; q < kappa; ++q) ok = ok && in_bounds_open(prop.phic[i * KS + q], pr.phi_lo, pr.phi_hi);
+    for (int q = 0; q < lam; ++q) ok = ok && in_bounds_open(prop.mv[i * KS + q], 0.0, 1.0);
+    ok = ok && ordered_open(prop.zc + (size_t)i * KS, kappa, pr.zmax) &&
+         ordered_open(prop.zm + (size_t)i * KS, lam, pr.zmax);
+    if (pr.tau_log_prior)
+        ok = ok && prop.tau[i] > 0.f && in_bounds_open(log10((double)prop.tau[i]), pr.logtau_lo, pr.logtau_hi);
+    else
+        ok = ok && in_bounds_open(prop.tau[i], 0.0, 1.0);
+    if (!ok) copy_particle(prop, i, cur, i);
+    valid_out[i] = ok ? 1 : 0;
+    lq[i] = lqf;
+}
+
+// Metropolis-Hastings test of the Langevin proposal at gamma_t:
+//   ln u < gamma_t (l' - l) + log q(theta | theta') - log q(theta' | theta);
+// on acceptance the particle and its gradient row take the proposal's.
+__global__ void langevin_accept_kernel(PState cur, PState prop, float *gcur, const float *gprop,
+                                       const int8_t *valid, const double *lq, const double *gamma,
+                                       const double *lang_h, Params pr, int stage, int sweep, int *lacc,
+                                       int *lprop) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    const int s = i / pr.N, jp = i - s * pr.N;
+    atomicAdd(&lprop[s], 1);
+    if (!valid[i]) return;
+    const int kappa = cur.kappa[i], lam = cur.lam[i];
+    const int d = 3 + 2 * kappa + 2 * lam;
+    const double gm = gamma[s], h = lang_h[s];
+    double lqr = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const ThetaRef rc = theta_ref(cur, i, j, kappa, lam, pr);
+        const ThetaRef rp = theta_ref(prop, i, j, kappa, lam, pr);
+        const double sc = rc.scale;
+        const double mean = theta_value(rp, pr) + 0.5 * h * h * sc * sc * gm * (double)gprop[(size_t)i * GD + rp.slot];
+        const double zz = (theta_value(rc, pr) - mean) / (h * sc);
+        lqr -= 0.5 * zz * zz;
+    }
+    uint32_t w[4];
+    block_draws(w, stream_key(pr.seed, s), (uint32_t)jp, (uint32_t)kPurposeLangevinAccept, (uint32_t)stage,
+                (uint32_t)sweep);
+    const double u = u01_53(w[0], w[1]);
+    if (log(u) < gm * (prop.ll[i] - cur.ll[i]) + lqr - lq[i]) {
+        copy_particle(cur, i, prop, i);
+        for (int q = 0; q < GD; ++q) gcur[(size_t)i * GD + q] = gprop[(size_t)i * GD + q];
+        atomicAdd(&lacc[s], 1);
+    }
+}
+
+// Between stages: h <- h exp(2 (rate - 0.574)) per sounding, clamped to
+// [1e-6, 10] (0.574: the optimal MALA acceptance of Roberts & Rosenthal 1998).
+__global__ void langevin_adapt_kernel(const int *lacc, const int *lprop, int S, double *lang_h) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double rate = lprop[s] > 0 ? (double)lacc[s] / lprop[s] : 0.574;
+    const double h = lang_h[s] * exp(2.0 * (rate - 0.574));
+    lang_h[s] = h < 1e-6 ? 1e-6 : (h > 10.0 ? 10.0 : h);
+}
+
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -625,6 +833,12 @@ struct smc_state {
     float *m_logsig = nullptr, *m_logh = nullptr, *m_m = nullptr, *m_logtau = nullptr, *m_c = nullptr;
     double *y = nullptr, *eps_an = nullptr;
     double eps_mn = 0.0;
+    // Langevin: merged-layer gradient, particle-space gradients of the current
+    // and proposed particles, log q(theta' | theta), per-sounding counts.
+    float *mgrad = nullptr, *gcur = nullptr, *gprop = nullptr;
+    double *lq = nullptr, *lang_h = nullptr;
+    int *lacc = nullptr, *lprop = nullptr;
+    bool gcur_valid = false;
     int stage = 0;
     std::vector<int> acc_prev, nprop_prev;
     bool have_prev = false;
@@ -660,6 +874,23 @@ int run_loglik(smc_state *st, PState ps) {
     return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream);
 }
 
+// Log-likelihood and particle-space gradient of a particle set: merge, the
+// adjoint kernel on the merged models, then the chain rule back to the
+// particle's parameters.
+int run_grad(smc_state *st, PState ps, float *pg) {
+    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
+                                                                st->m_logh, st->m_m, st->m_logtau, st->m_c);
+    AEM_CUDA_TRY(cudaGetLastError());
+    aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
+    int rc = loglik_grad_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->mgrad,
+                                       st->stream);
+    if (rc) return rc;
+    pgrad_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(ps, st->mgrad, st->P, st->LMS,
+                                                                 st->d.tau_log_prior, pg);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
 int check_desc(const smc_desc *d) {
     if (!d) return fail(AEM_ERR_INVALID_ARG, "smc_create: desc is NULL");
     if (d->n_particles < 2 || d->n_particles > AEM_SMC_MAX_PARTICLES)
@@ -675,6 +906,8 @@ int check_desc(const smc_desc *d) {
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid zmax / alpha / c_mut / r_max / prior bounds");
     if (d->tau_log_prior && !(d->logtau_hi > d->logtau_lo))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid log10 tau bounds");
+    if (d->n_langevin < 0 || d->n_langevin > 1000 || !(d->langevin_h > 0))
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: n_langevin outside 0..1000 or langevin_h <= 0");
     return AEM_OK;
 }
 
@@ -703,6 +936,9 @@ extern "C" int smc_desc_defaults(smc_desc *d) {
     d->logtau_hi = -1.0;
     d->seed = 0;
     d->bisect_iters = 60;
+    d->n_langevin = 0;
+    d->langevin_h = 0.1;
+    d->langevin_adapt = 1;
     return AEM_OK;
 }
 
@@ -755,12 +991,19 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->m_logsig, P * st->LMS)) || (rc = dalloc(st, &st->m_logh, P * st->LMS)) ||
         (rc = dalloc(st, &st->m_m, P * st->LMS)) || (rc = dalloc(st, &st->m_logtau, P * st->LMS)) ||
         (rc = dalloc(st, &st->m_c, P * st->LMS)) || (rc = dalloc(st, &st->y, (size_t)st->S * G)) ||
-        (rc = dalloc(st, &st->eps_an, (size_t)G))) {
+        (rc = dalloc(st, &st->eps_an, (size_t)G)) || (rc = dalloc(st, &st->mgrad, P * st->LMS * 5)) ||
+        (rc = dalloc(st, &st->gcur, P * GD)) || (rc = dalloc(st, &st->gprop, P * GD)) ||
+        (rc = dalloc(st, &st->lq, P)) || (rc = dalloc(st, &st->lacc, (size_t)st->S)) ||
+        (rc = dalloc(st, &st->lprop, (size_t)st->S)) || (rc = dalloc(st, &st->lang_h, (size_t)st->S))) {
         smc_destroy(st);
         return rc;
     }
     cudaError_t e = cudaMemcpy(st->y, y_obs, sizeof(double) * st->S * G, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->eps_an, eps_an, sizeof(double) * G, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<double> h0(st->S, desc->langevin_h);
+        e = cudaMemcpy(st->lang_h, h0.data(), sizeof(double) * st->S, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         smc_destroy(st);
         return cuda_fail(e, "smc_create: upload data");
@@ -784,8 +1027,17 @@ extern "C" int smc_init(smc_state *st) {
     AEM_CUDA_TRY(cudaMemsetAsync(st->logz, 0, sizeof(double) * st->S * st->M, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->lacc, 0, sizeof(int) * st->S, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->lprop, 0, sizeof(int) * st->S, st->stream));
+    {
+        std::vector<double> h0(st->S, st->d.langevin_h);
+        AEM_CUDA_TRY(cudaMemcpyAsync(st->lang_h, h0.data(), sizeof(double) * st->S, cudaMemcpyHostToDevice,
+                                     st->stream));
+        AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    }
     st->stage = 0;
     st->have_prev = false;
+    st->gcur_valid = false;
     return run_loglik(st, st->cur);
 }
 
@@ -823,6 +1075,7 @@ extern "C" int smc_resample(smc_state *st) {
     PState t = st->cur;
     st->cur = st->alt;
     st->alt = t;
+    st->gcur_valid = false;
     return AEM_OK;
 }
 
@@ -831,6 +1084,28 @@ extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
     propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid, st->pr,
                                                                     stage, sweep);
     AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+static int langevin_sweeps(smc_state *st, int n) {
+    AEM_CUDA_TRY(cudaMemsetAsync(st->lacc, 0, sizeof(int) * st->S, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->lprop, 0, sizeof(int) * st->S, st->stream));
+    if (n <= 0) return AEM_OK;
+    int rc;
+    // the current particles' likelihood and gradient come from the adjoint
+    // kernel, so both sides of every Langevin test use the same evaluation
+    if ((rc = run_grad(st, st->cur, st->gcur))) return rc;
+    st->gcur_valid = true;
+    for (int l = 0; l < n; ++l) {
+        langevin_propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
+            st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, st->stage, l, st->valid, st->lq);
+        AEM_CUDA_TRY(cudaGetLastError());
+        if ((rc = run_grad(st, st->prop, st->gprop))) return rc;
+        langevin_accept_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
+            st->cur, st->prop, st->gcur, st->gprop, st->valid, st->lq, st->gamma, st->lang_h, st->pr, st->stage, l,
+            st->lacc, st->lprop);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
     return AEM_OK;
 }
 
@@ -874,6 +1149,13 @@ extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid,
                                                                       st->gamma, st->pr, st->stage, sw, st->acc,
                                                                       st->nprop);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
+    if (R > 0) st->gcur_valid = false;
+    if ((rc = langevin_sweeps(st, st->d.n_langevin))) return rc;
+    if (st->d.n_langevin > 0 && st->d.langevin_adapt) {
+        langevin_adapt_kernel<<<blocks_for(st->S, 128), 128, 0, st->stream>>>(st->lacc, st->lprop, st->S,
+                                                                              st->lang_h);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     st->acc_prev.assign(st->S * kMoves, 0);
@@ -992,12 +1274,54 @@ extern "C" int smc_set_particles(smc_state *st, const smc_particles_host *h, con
     if (gamma) AEM_CUDA_TRY(cudaMemcpy(st->gamma, gamma, sizeof(double) * st->S, cudaMemcpyHostToDevice));
     if (log_z) AEM_CUDA_TRY(cudaMemcpy(st->logz, log_z, sizeof(double) * st->S * st->M, cudaMemcpyHostToDevice));
     if (stage >= 0) st->stage = stage;
+    st->gcur_valid = false;
     return AEM_OK;
 }
 
 extern "C" int smc_loglik_current(smc_state *st) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_loglik_current: NULL state");
+    st->gcur_valid = false;
     return run_loglik(st, st->cur);
+}
+
+extern "C" int smc_grad_current(smc_state *st, float *grad_host) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_grad_current: NULL state");
+    int rc = run_grad(st, st->cur, st->gcur);
+    if (rc) return rc;
+    st->gcur_valid = true;
+    if (grad_host) {
+        AEM_CUDA_TRY(cudaMemcpyAsync(grad_host, st->gcur, sizeof(float) * (size_t)st->P * GD, cudaMemcpyDeviceToHost,
+                                     st->stream));
+        AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    }
+    return AEM_OK;
+}
+
+extern "C" int smc_langevin_propose(smc_state *st, int stage, int sweep) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_langevin_propose: NULL state");
+    if (!st->gcur_valid)
+        return fail(AEM_ERR_INVALID_ARG, "smc_langevin_propose: no gradient of the current particles (smc_grad_current)");
+    langevin_propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
+        st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, stage, sweep, st->valid, st->lq);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+extern "C" int smc_langevin(smc_state *st, int n_sweeps) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_langevin: NULL state");
+    if (n_sweeps < 0 || n_sweeps > 1000) return fail(AEM_ERR_INVALID_ARG, "smc_langevin: n_sweeps outside 0..1000");
+    int rc = langevin_sweeps(st, n_sweeps);
+    if (rc) return rc;
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return AEM_OK;
+}
+
+extern "C" int smc_langevin_stats(const smc_state *st, int *accepted, int *proposed, double *h) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_langevin_stats: NULL state");
+    if (h) AEM_CUDA_TRY(cudaMemcpy(h, st->lang_h, sizeof(double) * st->S, cudaMemcpyDeviceToHost));
+    if (accepted) AEM_CUDA_TRY(cudaMemcpy(accepted, st->lacc, sizeof(int) * st->S, cudaMemcpyDeviceToHost));
+    if (proposed) AEM_CUDA_TRY(cudaMemcpy(proposed, st->lprop, sizeof(int) * st->S, cudaMemcpyDeviceToHost));
+    return AEM_OK;
 }
 
 // ----------------------------------------------------- standalone entries

@@ -10,6 +10,7 @@ from . import _lib
 from ._lib import AEMError, check
 
 SLOTS = 10
+GRAD_DIM = 3 + 4 * SLOTS  # AEM_SMC_GRAD_DIM: phi_b, phi_c[10], z_c[10], z_m[10], m[10], tau coordinate, c
 MOVES = ("sigma_birth", "sigma_death", "m_birth", "m_death", "depth", "perturb")
 
 
@@ -92,6 +93,29 @@ class SMC:
 
     def loglik_current(self):
         check(_lib.load().smc_loglik_current(self._h), "smc_loglik_current")
+
+    def grad_current(self):
+        """smc_grad_current: [P, GRAD_DIM] float32 gradient of the log-likelihood
+        with respect to each current particle's parameters (slot layout of
+        AEM_SMC_GRAD_DIM); also refreshes the current particles' ll."""
+        g = np.zeros((self.P, GRAD_DIM), dtype=np.float32)
+        check(_lib.load().smc_grad_current(self._h, g.ctypes.data), "smc_grad_current")
+        return g
+
+    def langevin_propose(self, stage, sweep):
+        check(_lib.load().smc_langevin_propose(self._h, int(stage), int(sweep)), "smc_langevin_propose")
+
+    def langevin(self, n_sweeps):
+        check(_lib.load().smc_langevin(self._h, int(n_sweeps)), "smc_langevin")
+
+    def langevin_stats(self):
+        """(accepted [S], proposed [S], h [S]) of the last mutate / langevin call."""
+        acc = np.zeros(self.S, dtype=np.int32)
+        prop = np.zeros(self.S, dtype=np.int32)
+        h = np.zeros(self.S)
+        check(_lib.load().smc_langevin_stats(self._h, acc.ctypes.data, prop.ctypes.data, h.ctypes.data),
+              "smc_langevin_stats")
+        return acc, prop, h
 
     def run(self, max_stages=1000, n_sweeps=0):
         t = ctypes.c_int()

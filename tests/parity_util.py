@@ -70,11 +70,33 @@ def assert_within(e, bound, what):
     assert r.max() <= 1.0, f"{what}: error {e[i]:.3e} exceeds bound {bound[i]:.3e} at {i}"
 
 
+def dll_dy(y_model, y_obs, eps_an=EPS_AN, eps_mn=I.EPS_MN):
+    """d ll / d yhat_g of the Gaussian likelihood with v_g = eps_an^2 + (eps_mn yhat_g)^2:
+    r / v + (eps_mn^2 yhat / v) (r^2 / v - 1), r = y_obs - yhat."""
+    v = eps_an ** 2 + (eps_mn * y_model) ** 2
+    r = y_obs - y_model
+    return r / v + (eps_mn ** 2 * y_model / v) * (r ** 2 / v - 1.0)
+
+
 def loglik_bound(y_model, y_obs, gate_bound, eps_an=EPS_AN, eps_mn=I.EPS_MN):
     """First-order bound on |d ll| from per-gate relative errors gate_bound
     (relative to max(|y|, eps_an)): 2 sum_g |d ll / d yhat_g| |d yhat_g|."""
     dy = gate_bound * np.maximum(np.abs(y_model), eps_an)
-    v = eps_an ** 2 + (eps_mn * y_model) ** 2
-    r = y_obs - y_model
-    dll = np.abs(r / v + (eps_mn ** 2 * y_model / v) * (r ** 2 / v - 1.0))
-    return 2.0 * np.sum(dll * dy, axis=1)
+    return 2.0 * np.sum(np.abs(dll_dy(y_model, y_obs, eps_an, eps_mn)) * dy, axis=1)
+
+
+def gradient_bound(y_model, jac, y_obs, gate_bound, eps_an=EPS_AN, eps_mn=I.EPS_MN):
+    """First-order bound on the error of d ll / d theta [P, LMAX, 5] from
+    per-gate relative errors gate_bound of the predictions, assuming each
+    gate's Jacobian row carries the same relative error bound as the gate:
+      sum_g ( max_+- |l'_g(yhat_g +- dy_g) - l'_g(yhat_g)| + |l'_g| e_g ) |J_g|,
+    dy_g = e_g max(|yhat_g|, eps_an).  The first term is exact in the
+    perturbation (l' is far from linear where a model misses the data by
+    many standard deviations: there r / v and the variance term cancel to
+    leading order and l' is 1 / eps_mn^2 times more sensitive)."""
+    dy = gate_bound * np.maximum(np.abs(y_model), eps_an)
+    d0 = dll_dy(y_model, y_obs, eps_an, eps_mn)
+    dd = np.maximum(np.abs(dll_dy(y_model + dy, y_obs, eps_an, eps_mn) - d0),
+                    np.abs(dll_dy(y_model - dy, y_obs, eps_an, eps_mn) - d0))
+    w = dd + np.abs(d0) * gate_bound
+    return np.einsum("pg,pgnk->pnk", w, np.abs(jac))

@@ -220,3 +220,9 @@ def test_fd_gradient_is_step_consistent():
     _, g2 = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN, step=1e-5)
     scale = np.max(np.abs(g2), axis=(1, 2), keepdims=True)
     assert np.max(np.abs(g1 - g2) / scale) < 1e-5
+    # the gate Jacobian reproduces it through the chain rule with the
+    # closed-form d ll / d yhat (Section 2.3.2's Gaussian likelihood)
+    from parity_util import dll_dy
+    y, J = O.forward_jacobian_fd(models, s)
+    g3 = np.einsum("pg,pgnk->pnk", dll_dy(y, y_obs), J)
+    assert np.max(np.abs(g3 - g2) / scale) < 1e-6
