@@ -132,9 +132,42 @@ def cpu_baseline(target_seconds=15.0):
         elapsed += time.perf_counter() - t0
         done += n
         n = min(n * 2, 4096)
+    # the same discretisation as the GPU (the K-point Hankel rule) in FP64 on
+    # the same cores: the fair CPU form of the forward model
+    n, done_r, el_r = 256, 0, 0.0
+    while el_r < target_seconds / 3:
+        models = I.random_models(n, seed=5000 + done_r)
+        t0 = time.perf_counter()
+        y = O.forward(models, so, mode=O.HANKEL_RULE, nthreads=cores)
+        O.loglik(y, y_obs, I.EPS_AN, I.EPS_MN)
+        el_r += time.perf_counter() - t0
+        done_r += n
+        n = min(n * 2, 16384)
+    # the serial oracle RJSMC of the single-sounding configuration (N = 256,
+    # kappa <= 3, lambda <= 4, 10 sweeps per stage): prior draw plus one stage,
+    # extrapolated to the stage count the GPU sampler takes on it (30)
+    from oracle import rjsmc as R
+    ss = I.oracle_system("sounding-g20-f40-k120")
+    ss["T"] = O.tmatrix(ss["freqs"], ss["times"])
+    y1 = I.noisy(O.forward(I.truth_3layer(), ss, mode=O.HANKEL_RULE)[0], seed=0)
+    lik = R.ForwardLik(ss, y1, I.EPS_AN, I.EPS_MN, lmax=8)
+    st = R.SMCSettings(n_particles=256, kappa_max=3, lambda_max=4, n_sweeps=10, seed=0)
+    t0 = time.perf_counter()
+    parts = [R.sample_prior(st, i) for i in range(st.n_particles)]
+    lik(parts)
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R.run(st, lik, max_stages=1)
+    t_stage = time.perf_counter() - t0 - t_init
     return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} models of the {WORKLOAD} workload (adaptive-quadrature FP64 oracle, "
-                      f"{cores} threads), {elapsed:.1f} s"}
+                      f"{cores} threads), {elapsed:.1f} s",
+            "same_discretisation": {"value": done_r / el_r, "unit": UNIT, "cores": cores,
+                                    "sample": f"{done_r} models, FP64 oracle with the GPU's {WORKLOAD.split('-k')[-1]}"
+                                              f"-point Hankel rule, {el_r:.1f} s"},
+            "rjsmc": {"value": 1.0 / (t_init + 30 * t_stage), "unit": "soundings/s", "cores": cores,
+                      "sample": f"serial oracle RJSMC, 256 particles, kappa<=3, lambda<=4, 10 sweeps/stage: prior "
+                                f"draw {t_init:.2f} s + one stage {t_stage:.2f} s, extrapolated to 30 stages"}}
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,

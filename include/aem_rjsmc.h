@@ -137,6 +137,37 @@ int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *models, const do
 int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
                    const double *eps_an, double eps_mn, double *ll, double *gates, void *stream);
 
+/* Gate transform and likelihood from a batch of spectra (the a5 + a6 steps on
+ * their own; Section 2.3.2).  imh: [device] n_models x F Im Hz_s at the
+ * system's frequency nodes (as aem_forward_f32 writes it).  mode selects the
+ * arithmetic of y = T Im H:
+ *   AEM_GATES_FP32        FP32 dot products on the CUDA cores;
+ *   AEM_GATES_TF32_SPLIT  tensor cores (tcgen05, kind::tf32), each operand
+ *                         split into TF32 high + low parts, three products
+ *                         accumulated in FP32 (relative residual ~2^-22 per term);
+ *   AEM_GATES_BF16_SPLIT  the same with BF16 parts (kind::f16, ~2^-17 per term).
+ * gates: [device] n_models x G (may be NULL); ll: [device] n_models doubles
+ * (may be NULL; then y_obs and eps_an may be NULL too), with y_obs [device] G
+ * and eps_an [device] G as for aem_loglik_f32.  Asynchronous.  A bounded
+ * wait inside the tensor-core kernel that gives up records AEM_ERR_TIMEOUT in
+ * the system's status word (aem_system_status). */
+#define AEM_GATES_FP32 0
+#define AEM_GATES_TF32_SPLIT 1
+#define AEM_GATES_BF16_SPLIT 2
+int aem_gates_from_spectrum(const aem_system *sys, const float *imh, int n_models, int mode, const double *y_obs,
+                            const double *eps_an, double eps_mn, float *gates, double *ll, void *stream);
+
+/* aem_loglik_f32 with the gate transform of `mode` (above): the forward
+ * kernel writes the spectra into imh_work ([device] P x F floats, caller's
+ * scratch), then aem_gates_from_spectrum forms gates (may be NULL) and ll. */
+int aem_loglik_f32_tc(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                      const double *eps_an, double eps_mn, int mode, float *imh_work, double *ll, float *gates,
+                      void *stream);
+
+/* Synchronous.  Reads and clears the system's device status word: 0, or the
+ * AEM_ERR_TIMEOUT a kernel recorded since the last call. */
+int aem_system_status(const aem_system *sys, int *status);
+
 /* Gradient of the log-likelihood above (FP32 forward model) with respect to
  * every merged layer's parameters, by reverse-mode differentiation of the
  * forward model of Section 2 and the likelihood of Section 2.3.2.
@@ -306,6 +337,20 @@ int smc_get_particles(const smc_state *st, int which, smc_particles_host *h);
  * gamma [S], log_z [S x M] and the stage counter). */
 int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *gamma, const double *log_z,
                       int stage);
+
+/* Checkpoint / resume.  smc_checkpoint writes a self-describing image of the
+ * sampler's dynamic state (current particles with their log-likelihoods,
+ * gamma, log Z_k, stage counter, Langevin steps, the previous stage's
+ * acceptance counts that set R_t) into the caller's host buffer: with
+ * buf == NULL it only stores the image size in *size; otherwise *size is the
+ * buffer's capacity on entry (AEM_ERR_INVALID_ARG if too small) and the
+ * image's size on return.  Synchronous.  smc_restore loads such an image into
+ * a sampler created with the same n_soundings, n_particles, kappa_max and
+ * lambda_max (AEM_ERR_INVALID_ARG otherwise, or for a damaged or truncated
+ * image); the random streams are counter-based, so resuming reproduces the
+ * uninterrupted run exactly when the descriptors match. */
+int smc_checkpoint(const smc_state *st, void *buf, size_t *size);
+int smc_restore(smc_state *st, const void *buf, size_t size);
 
 /* Standalone single-sounding forms of a7 and a8 on caller buffers
  * ([device] pointers; `work` is a [device] scratch buffer of at least

@@ -15,11 +15,15 @@ import numpy as np
 from . import _lib
 from ._lib import AEMError, check
 
-__all__ = ["System", "forward_f32", "forward_f64", "loglik_f32", "loglik_f64", "loglik_grad_f32", "loglik",
-           "probe_peaks", "AEMError", "CC_PAPER", "CC_PELTON"]
+__all__ = ["System", "forward_f32", "forward_f64", "spectrum_f32", "loglik_f32", "loglik_f64", "loglik_f32_tc",
+           "gates_from_spectrum", "loglik_grad_f32", "loglik", "system_status", "probe_peaks", "AEMError",
+           "CC_PAPER", "CC_PELTON", "GATES_FP32", "GATES_TF32_SPLIT", "GATES_BF16_SPLIT"]
 
 CC_PAPER = 0
 CC_PELTON = 1
+GATES_FP32 = 0
+GATES_TF32_SPLIT = 1
+GATES_BF16_SPLIT = 2
 
 
 def _torch():
@@ -120,6 +124,61 @@ def forward_f64(system, models, want_imh=False, stream=None):
     """aem_forward_f64: the plain double-precision form of the same kernel."""
     g, i = _forward(_lib.load().aem_forward_f64, models, _torch().float64, True, want_imh, system, stream)
     return (g, i) if want_imh else g
+
+
+def spectrum_f32(system, models, stream=None):
+    """aem_forward_f32 with the spectrum only: Im Hz_s [P, F] (float32)."""
+    return _forward(_lib.load().aem_forward_f32, models, _torch().float32, False, True, system, stream)[1]
+
+
+def _obs(y_obs, eps_an, system, dev):
+    torch = _torch()
+    y = torch.as_tensor(y_obs, dtype=torch.float64, device=dev).contiguous()
+    e = torch.as_tensor(eps_an, dtype=torch.float64, device=dev).expand(system.G).contiguous()
+    return y, e
+
+
+def gates_from_spectrum(system, imh, mode=GATES_TF32_SPLIT, y_obs=None, eps_an=None, eps_mn=0.0, want_gates=True,
+                        stream=None):
+    """aem_gates_from_spectrum: gates [P, G] (float32, or None) and, when y_obs
+    is given, ll [P] (float64, else None) from spectra imh [P, F] (float32)."""
+    torch = _torch()
+    if imh.dtype != torch.float32 or not imh.is_cuda or not imh.is_contiguous() or imh.dim() != 2:
+        raise AEMError("imh must be a contiguous 2-D CUDA float32 tensor")
+    P = imh.shape[0]
+    gates = torch.empty((P, system.G), dtype=torch.float32, device=imh.device) if want_gates else None
+    ll = y = e = None
+    if y_obs is not None:
+        y, e = _obs(y_obs, eps_an, system, imh.device)
+        ll = torch.empty(P, dtype=torch.float64, device=imh.device)
+    check(_lib.load().aem_gates_from_spectrum(system.handle, _dptr(imh), P, int(mode), _dptr(y), _dptr(e),
+                                              float(eps_mn), _dptr(gates), _dptr(ll), _stream_ptr(stream)),
+          "aem_gates_from_spectrum")
+    return gates, ll
+
+
+def loglik_f32_tc(system, models, y_obs, eps_an, eps_mn, mode=GATES_TF32_SPLIT, want_gates=False, stream=None):
+    """aem_loglik_f32_tc: the FP32 forward model with the gate transform of
+    `mode` (tensor-core TF32 / BF16 split, or FP32); ll [P] (and gates)."""
+    torch = _torch()
+    ms = _models_struct(models, torch.float32)
+    P = ms.n_models
+    dev = models["logsig"].device
+    y, e = _obs(y_obs, eps_an, system, dev)
+    work = torch.empty((P, system.F), dtype=torch.float32, device=dev)
+    ll = torch.empty(P, dtype=torch.float64, device=dev)
+    gates = torch.empty((P, system.G), dtype=torch.float32, device=dev) if want_gates else None
+    check(_lib.load().aem_loglik_f32_tc(system.handle, ctypes.byref(ms), _dptr(y), _dptr(e), float(eps_mn),
+                                        int(mode), _dptr(work), _dptr(ll), _dptr(gates), _stream_ptr(stream)),
+          "aem_loglik_f32_tc")
+    return (ll, gates) if want_gates else ll
+
+
+def system_status(system):
+    """aem_system_status: 0, or the error a kernel recorded (cleared on read)."""
+    v = ctypes.c_int()
+    check(_lib.load().aem_system_status(system.handle, ctypes.byref(v)), "aem_system_status")
+    return v.value
 
 
 def _loglik(fn, models, dtype, y_obs, eps_an, eps_mn, system, want_gates, stream):

@@ -91,6 +91,11 @@ SIGNATURES = {
     "aem_loglik_f64": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                         c_void_p], c_int),
     "aem_probe_peaks": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "aem_gates_from_spectrum": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
+                                 c_void_p], c_int),
+    "aem_loglik_f32_tc": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
+                           c_void_p, c_void_p], c_int),
+    "aem_system_status": ([c_void_p, c_void_p], c_int),
     "aem_loglik_grad_f32": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                              c_void_p], c_int),
     "smc_desc_defaults": ([ctypes.POINTER(SMCDesc)], c_int),
@@ -106,6 +111,8 @@ SIGNATURES = {
     "smc_grad_current": ([c_void_p, c_void_p], c_int),
     "smc_langevin_propose": ([c_void_p, c_int, c_int], c_int),
     "smc_langevin": ([c_void_p, c_int], c_int),
+    "smc_checkpoint": ([c_void_p, c_void_p, ctypes.POINTER(ctypes.c_size_t)], c_int),
+    "smc_restore": ([c_void_p, c_void_p, ctypes.c_size_t], c_int),
     "smc_langevin_stats": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_run": ([c_void_p, c_int, c_int, c_void_p], c_int),
     "smc_model_odds": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "_build", "libaemrjsmc.so")
-SOURCES = ["system.cpp", "forward.cu", "adjoint.cu", "smc.cu", "peaks.cu"]
+SOURCES = ["system.cpp", "forward.cu", "adjoint.cu", "gates_tc.cu", "smc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

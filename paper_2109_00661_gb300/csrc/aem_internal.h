@@ -30,6 +30,11 @@ struct SystemTables {
     std::vector<double> freqs, omega, times, lam, hw, T;  // T is G x F
 };
 
+// Gates (and log-likelihood) from spectra [P][F] by the transform of the
+// given aem_gates_mode; y_obs rows advance every obs_per models (gates_tc.cu).
+int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode, const double *y_obs,
+                        int obs_per, const double *eps_an, double eps_mn, float *gates, double *ll,
+                        cudaStream_t stream);
 }  // namespace aem
 
 struct aem_system {
@@ -39,6 +44,9 @@ struct aem_system {
     float *d_omega_f = nullptr, *d_lam_f = nullptr, *d_hw_f = nullptr, *d_T_f = nullptr;
     double *d_omega_d = nullptr, *d_lam_d = nullptr, *d_hw_d = nullptr, *d_T_d = nullptr;
     int num_sms = 0;
+    // device status word: kernels record AEM_ERR_TIMEOUT here when a bounded
+    // wait gives up (read and cleared by aem_system_status)
+    int *d_status = nullptr;
 };
 
 namespace aem {
@@ -54,4 +62,9 @@ int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, co
 int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
                               cudaStream_t stream);
+// Gates (and log-likelihood) from spectra [P][F] by the transform of the
+// given aem_gates_mode; y_obs rows advance every obs_per models (gates_tc.cu).
+int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode, const double *y_obs,
+                        int obs_per, const double *eps_an, double eps_mn, float *gates, double *ll,
+                        cudaStream_t stream);
 }  // namespace aem

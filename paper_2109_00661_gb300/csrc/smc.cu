@@ -1324,6 +1324,125 @@ extern "C" int smc_langevin_stats(const smc_state *st, int *accepted, int *propo
     return AEM_OK;
 }
 
+// ------------------------------------------------------ checkpoint / restore
+// Image layout (little-endian host order, version 1): a fixed header, then the
+// current particles (kappa, lam int32 [P]; phib, tau, c float [P]; zc, phic,
+// zm, mv float [P][SLOTS]; ll double [P]), gamma [S], log Z [S][M], Langevin
+// step [S] (doubles), and the previous stage's acceptance counts [S][6] x 2
+// (int32, valid when have_prev).
+namespace {
+constexpr char kCkptMagic[8] = {'A', 'E', 'M', 'S', 'M', 'C', 'C', 'K'};
+struct CkptHeader {
+    char magic[8];
+    int32_t version, S, N, M, kappa_max, lambda_max, stage, have_prev;
+    uint64_t seed;
+    uint64_t payload_bytes;
+};
+
+size_t ckpt_payload(const smc_state *st) {
+    const size_t P = st->P, S = st->S;
+    return P * (2 * sizeof(int32_t) + 3 * sizeof(float) + 4 * KS * sizeof(float) + sizeof(double)) +
+           S * (2 + st->M) * sizeof(double) + 2 * S * kMoves * sizeof(int32_t);
+}
+
+template <class T>
+int d2h(unsigned char *&o, const T *src, size_t n, cudaStream_t s) {
+    AEM_CUDA_TRY(cudaMemcpyAsync(o, src, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    o += n * sizeof(T);
+    return AEM_OK;
+}
+
+template <class T>
+int h2d(T *dst, const unsigned char *&i, size_t n, cudaStream_t s) {
+    AEM_CUDA_TRY(cudaMemcpyAsync(dst, i, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    i += n * sizeof(T);
+    return AEM_OK;
+}
+}  // namespace
+
+extern "C" int smc_checkpoint(const smc_state *cst, void *buf, size_t *size) {
+    smc_state *st = const_cast<smc_state *>(cst);
+    if (!st || !size) return fail(AEM_ERR_INVALID_ARG, "smc_checkpoint: NULL state or size");
+    const size_t need = sizeof(CkptHeader) + ckpt_payload(st);
+    if (!buf) {
+        *size = need;
+        return AEM_OK;
+    }
+    if (*size < need) return fail(AEM_ERR_INVALID_ARG, "smc_checkpoint: buffer smaller than the image");
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.S = st->S;
+    h.N = st->N;
+    h.M = st->M;
+    h.kappa_max = st->d.kappa_max;
+    h.lambda_max = st->d.lambda_max;
+    h.stage = st->stage;
+    h.have_prev = st->have_prev ? 1 : 0;
+    h.seed = st->d.seed;
+    h.payload_bytes = ckpt_payload(st);
+    unsigned char *o = (unsigned char *)buf;
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t P = st->P, S = st->S;
+    const PState c = st->cur;
+    cudaStream_t sm = st->stream;
+    int rc;
+    if ((rc = d2h(o, c.kappa, P, sm)) || (rc = d2h(o, c.lam, P, sm)) || (rc = d2h(o, c.phib, P, sm)) ||
+        (rc = d2h(o, c.tau, P, sm)) || (rc = d2h(o, c.c, P, sm)) || (rc = d2h(o, c.zc, P * KS, sm)) ||
+        (rc = d2h(o, c.phic, P * KS, sm)) || (rc = d2h(o, c.zm, P * KS, sm)) || (rc = d2h(o, c.mv, P * KS, sm)) ||
+        (rc = d2h(o, c.ll, P, sm)) || (rc = d2h(o, st->gamma, S, sm)) || (rc = d2h(o, st->logz, S * st->M, sm)) ||
+        (rc = d2h(o, st->lang_h, S, sm)))
+        return rc;
+    AEM_CUDA_TRY(cudaStreamSynchronize(sm));
+    const size_t nc = S * kMoves;
+    for (size_t q = 0; q < nc; ++q) {
+        const int32_t a = st->have_prev ? st->acc_prev[q] : 0, b = st->have_prev ? st->nprop_prev[q] : 0;
+        std::memcpy(o + q * sizeof(int32_t), &a, sizeof a);
+        std::memcpy(o + (nc + q) * sizeof(int32_t), &b, sizeof b);
+    }
+    *size = need;
+    return AEM_OK;
+}
+
+extern "C" int smc_restore(smc_state *st, const void *buf, size_t size) {
+    if (!st || !buf) return fail(AEM_ERR_INVALID_ARG, "smc_restore: NULL state or buffer");
+    CkptHeader h{};
+    if (size < sizeof h) return fail(AEM_ERR_INVALID_ARG, "smc_restore: buffer shorter than the header");
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: not a version-1 sampler checkpoint");
+    if (h.S != st->S || h.N != st->N || h.M != st->M || h.kappa_max != st->d.kappa_max ||
+        h.lambda_max != st->d.lambda_max)
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: checkpoint sizes differ from this sampler's");
+    if (h.payload_bytes != ckpt_payload(st) || size < sizeof h + h.payload_bytes)
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: truncated checkpoint");
+    const unsigned char *i = (const unsigned char *)buf + sizeof h;
+    const size_t P = st->P, S = st->S;
+    const PState c = st->cur;
+    cudaStream_t sm = st->stream;
+    AEM_CUDA_TRY(cudaStreamSynchronize(sm));
+    int rc;
+    if ((rc = h2d(c.kappa, i, P, sm)) || (rc = h2d(c.lam, i, P, sm)) || (rc = h2d(c.phib, i, P, sm)) ||
+        (rc = h2d(c.tau, i, P, sm)) || (rc = h2d(c.c, i, P, sm)) || (rc = h2d(c.zc, i, P * KS, sm)) ||
+        (rc = h2d(c.phic, i, P * KS, sm)) || (rc = h2d(c.zm, i, P * KS, sm)) || (rc = h2d(c.mv, i, P * KS, sm)) ||
+        (rc = h2d(c.ll, i, P, sm)) || (rc = h2d(st->gamma, i, S, sm)) || (rc = h2d(st->logz, i, S * st->M, sm)) ||
+        (rc = h2d(st->lang_h, i, S, sm)))
+        return rc;
+    AEM_CUDA_TRY(cudaStreamSynchronize(sm));
+    const size_t nc = S * kMoves;
+    st->acc_prev.assign(nc, 0);
+    st->nprop_prev.assign(nc, 0);
+    for (size_t q = 0; q < nc; ++q) {
+        std::memcpy(&st->acc_prev[q], i + q * sizeof(int32_t), sizeof(int32_t));
+        std::memcpy(&st->nprop_prev[q], i + (nc + q) * sizeof(int32_t), sizeof(int32_t));
+    }
+    st->have_prev = h.have_prev != 0;
+    st->stage = h.stage;
+    st->gcur_valid = false;
+    return AEM_OK;
+}
+
 // ----------------------------------------------------- standalone entries
 extern "C" size_t aem_smc_workspace_bytes(int n, int n_models) {
     if (n < 0 || n_models < 1) return 0;

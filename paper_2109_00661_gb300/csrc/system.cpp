@@ -304,13 +304,20 @@ extern "C" int aem_system_create(const aem_system_desc *desc, aem_system **out) 
         aem_system_destroy(s);
         return rc;
     }
+    e = cudaMalloc((void **)&s->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        aem_system_destroy(s);
+        return cuda_fail(e, "aem_system_create: status word");
+    }
     *out = s;
     return AEM_OK;
 }
 
 extern "C" int aem_system_destroy(aem_system *s) {
     if (!s) return AEM_OK;
-    void *ptrs[] = {s->d_omega_f, s->d_lam_f, s->d_hw_f, s->d_T_f, s->d_omega_d, s->d_lam_d, s->d_hw_d, s->d_T_d};
+    void *ptrs[] = {s->d_omega_f, s->d_lam_f, s->d_hw_f, s->d_T_f,
+                    s->d_omega_d, s->d_lam_d, s->d_hw_d, s->d_T_d, s->d_status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete s;

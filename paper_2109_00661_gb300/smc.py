@@ -151,6 +151,20 @@ class SMC:
         check(_lib.load().smc_set_particles(self._h, ctypes.byref(s), None if g is None else g.ctypes.data,
                                             None if lz is None else lz.ctypes.data, int(stage)), "smc_set_particles")
 
+    def checkpoint(self) -> bytes:
+        """smc_checkpoint: the sampler's dynamic state as bytes."""
+        lib = _lib.load()
+        n = ctypes.c_size_t(0)
+        check(lib.smc_checkpoint(self._h, None, ctypes.byref(n)), "smc_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib.smc_checkpoint(self._h, buf, ctypes.byref(n)), "smc_checkpoint")
+        return buf.raw[:n.value]
+
+    def restore(self, image: bytes):
+        """smc_restore from bytes written by checkpoint()."""
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        check(_lib.load().smc_restore(self._h, buf, len(image)), "smc_restore")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().smc_destroy(self._h)
