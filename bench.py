@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rjsmc", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64 form, gate-transform variants, bucketed order and adjoint measurements")
     ap.add_argument("--rjsmc-only", action="store_true", help="run only the RJSMC measurement (profiling)")
     ap.add_argument("--flight-line", type=int, default=0, metavar="S",
                     help="run only the flight-line sampler: S soundings x 2048 particles in one sampler")
@@ -357,7 +359,7 @@ def main():
 
     # the plain double-precision form of the same kernel on a 65,536-model block
     fp64 = None
-    if rank == 0:
+    if rank == 0 and not args.no_variants:
         m64 = I.to_torch(I.subset(models_np, np.arange(1 << 16)), torch.float64)
         L.loglik_f64(sysg, m64, y_obs, eps_an, I.EPS_MN)
         torch.cuda.synchronize()
@@ -370,11 +372,63 @@ def main():
         fp64 = {"value": (1 << 16) / (g0.elapsed_time(g1) * 1e-3), "unit": UNIT, "models": 1 << 16,
                 "dtype": "f64"}
 
+    # the gate-transform variants of the same step on the same models: the
+    # forward kernel writes the spectra, then the transform + likelihood
+    # kernel runs on the tensor cores (TF32 / BF16 high-low splits) or the
+    # CUDA cores (FP32); both the whole step and the transform kernel alone
+    transforms = None
+    if rank == 0 and not args.no_variants:
+        transforms = {}
+        imh = L.spectrum_f32(sysg, models, stream=stream)
+        for name, mode in (("fp32", L.GATES_FP32), ("tf32_split", L.GATES_TF32_SPLIT),
+                           ("bf16_split", L.GATES_BF16_SPLIT)):
+            for _ in range(2):
+                L.loglik_f32_tc(sysg, models, y_obs, eps_an, I.EPS_MN, mode, stream=stream)
+            torch.cuda.synchronize()
+            t0_ = torch.cuda.Event(enable_timing=True)
+            t1_ = torch.cuda.Event(enable_timing=True)
+            t0_.record(stream)
+            for _ in range(args.steps):
+                L.loglik_f32_tc(sysg, models, y_obs, eps_an, I.EPS_MN, mode, stream=stream)
+            t1_.record(stream)
+            torch.cuda.synchronize()
+            step_ms = t0_.elapsed_time(t1_) / args.steps
+            for _ in range(2):
+                L.gates_from_spectrum(sysg, imh, mode, y_obs, eps_an, I.EPS_MN, want_gates=False, stream=stream)
+            torch.cuda.synchronize()
+            t0_.record(stream)
+            for _ in range(args.steps):
+                L.gates_from_spectrum(sysg, imh, mode, y_obs, eps_an, I.EPS_MN, want_gates=False, stream=stream)
+            t1_.record(stream)
+            torch.cuda.synchronize()
+            kms = t0_.elapsed_time(t1_) / args.steps
+            transforms[name] = {"evals_per_s": P / (step_ms * 1e-3), "ms_per_step": step_ms,
+                                "transform_kernel_ms": kms,
+                                "transform_tflops": 2.0 * P * F * G * (3 if "split" in name else 1) / (kms * 1e-3) / 1e12}
+        del imh
+        # the same step with the models reordered by layer count (one CTA per
+        # model already keeps every warp on one model, so this only changes
+        # the order in which CTAs meet short and long models)
+        order = torch.argsort(models["nlayers"].to(torch.int32), stable=True)
+        mb = {k: v[order].contiguous() for k, v in models.items()}
+        for _ in range(2):
+            L.loglik_f32(sysg, mb, y_obs, eps_an, I.EPS_MN, stream=stream)
+        torch.cuda.synchronize()
+        t0_.record(stream)
+        for _ in range(args.steps):
+            L.loglik_f32(sysg, mb, y_obs, eps_an, I.EPS_MN, stream=stream)
+        t1_.record(stream)
+        torch.cuda.synchronize()
+        transforms["fp32_epilogue_bucketed_by_L"] = {"evals_per_s": P / (t0_.elapsed_time(t1_) / args.steps * 1e-3)}
+        del mb
+        if L.system_status(sysg) != 0:
+            raise RuntimeError("a transform kernel reported a timeout")
+
     # the adjoint: log-likelihood and its gradient with respect to every
     # layer's (log10 sigma, log10 h, m, log10 tau, c) for 65,536 of the same
     # random models (1..10 layers), one aem_loglik_grad_f32 launch per step
     adjoint = None
-    if rank == 0 and not args.no_rjsmc:
+    if rank == 0 and not args.no_variants:
         na = 1 << 16
         ma = I.to_torch(I.subset(models_np, np.arange(na)), torch.float32)
         for _ in range(3):
@@ -443,6 +497,8 @@ def main():
             line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"] = rjsmc
         if adjoint is not None:
             line["adjoint"] = adjoint
+        if transforms is not None:
+            line["gate_transform_variants"] = transforms
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
