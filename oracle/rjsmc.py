@@ -131,6 +131,10 @@ class SMCSettings:
     n_langevin: int = 0         # Langevin sweeps per stage after the random-walk sweeps
     langevin_h: float = 0.1     # initial Langevin step, in units of the random-walk scales
     langevin_adapt: bool = True  # adapt the step between stages towards LANGEVIN_TARGET acceptance
+    adaptive: bool = False      # the paper's adaptive within-model proposal replaces the fixed-scale perturb move
+    pca_target: float = 0.44    # acceptance rate the scale bisection aims at (Section 3.2)
+    pca_bisect_iters: int = 6   # bisection steps on trial proposals per stage
+    pca_ridge: float = 0.01     # ridge on the fitted covariance, as a fraction of the random-walk scales
 
     @property
     def n_models(self):
@@ -590,6 +594,7 @@ class SMCResult:
     langevin_accept: int = 0
     langevin_proposed: int = 0
     langevin_h: list = field(default_factory=list)
+    pca_scales: list = field(default_factory=list)
 
 
 class ForwardLik:
@@ -630,6 +635,7 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
     prop = np.zeros(6)
     p_min = 0.0
     h_lang = s.langevin_h
+    pca_scale = {}
     for stage in range(1, max_stages + 1):
         model = np.array([p.model(s) for p in parts])
         dg, done, inc, W = reweight(ll, model, s.n_models, gamma, s.alpha, s.bisect_iters)
@@ -641,6 +647,11 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
         ll = ll[anc].copy()
         R = s.n_sweeps if s.n_sweeps > 0 else (s.r_max if stage == 1 else sweeps_needed(p_min, s.c_mut, s.r_max))
         res.sweeps.append(R)
+        if s.adaptive:
+            fits = fit_model_gaussians(parts, s)
+            pca_scale = pca_bisect_scales(parts, ll, fits, s, stage, gamma, loglik, pca_scale)
+            res.pca_scales.append(dict(pca_scale))
+            proposer = (lambda p_, s_, i_, st_, sw_: propose_adaptive(p_, s_, i_, st_, sw_, fits, pca_scale))
         acc_stage = np.zeros(6)
         prop_stage = np.zeros(6)
         for sweep in range(R):
@@ -697,3 +708,112 @@ def model_odds(counts, kappa_max, lambda_max):
     if n_ip == 0:
         return post, -math.inf
     return post, math.log(n_ip / (lambda_max * n_non))
+
+
+# ------------------------------------------- adaptive within-model proposal
+# Section 3.2 ("Transdimensional and within-model adaptive proposals"): a
+# Gaussian N(mu_k, Sigma_k) fitted to the particles of each model k, the
+# eigen-decomposition Sigma_k = U Lambda U^T, a component-wise random walk
+# along a uniformly chosen principal direction U_r with standard deviation
+# a_k sqrt(Lambda_r), and the scale a_k chosen per stage by bisection on trial
+# proposals so that their mean acceptance probability is pca_target.
+PURPOSE_PCA_TRIAL = 69
+PCA_LOG_SPAN = 3.0   # bisection bracket: log a within +-3 of the previous stage's
+
+
+def fit_model_gaussians(parts, s: SMCSettings):
+    """{model k: (mu, U, Lam)} over the (equally weighted) particles of each
+    model with at least two particles; Sigma is the biased sample covariance
+    plus (pca_ridge * step_j)^2 on the diagonal."""
+    out = {}
+    by_model = {}
+    for p in parts:
+        by_model.setdefault(p.model(s), []).append(theta_of(p, s))
+    for k, th in by_model.items():
+        if len(th) < 2:
+            continue
+        X = np.array(th)
+        mu = X.mean(axis=0)
+        C = (X - mu).T @ (X - mu) / len(th)
+        sc = theta_scales(parts[[q.model(s) for q in parts].index(k)], s)
+        C = C + np.diag((s.pca_ridge * sc) ** 2)
+        lam, U = np.linalg.eigh(C)
+        out[k] = (mu, U, np.maximum(lam, 0.0))
+    return out
+
+
+def pca_step(p: Particle, fit, a, s: SMCSettings, u_comp, xi):
+    """theta' = theta + a sqrt(Lambda_r) xi U_r with r = floor(u_comp d);
+    None outside the prior support or the interface order."""
+    _, U, lam = fit
+    d = len(lam)
+    r = min(int(u_comp * d), d - 1)
+    th = theta_of(p, s) + a * math.sqrt(lam[r]) * xi * U[:, r]
+    q = with_theta(p, s, th)
+    return q if theta_in_support(q, s) else None
+
+
+def pca_trial_draws(s: SMCSettings, i: int, stage: int):
+    w = draws(s.seed, s.sounding, i, PURPOSE_PCA_TRIAL, stage, 0)[0]
+    return float(u01_from(w[0])), float(gauss_pair(w[1], w[2]))
+
+
+def pca_bisect_scales(parts, ll, fits, s: SMCSettings, stage: int, gamma: float, loglik, a_prev):
+    """Per model: bisection on log a in [log a_prev - 3, log a_prev + 3] with
+    the same trial draws at every step; the mean over the model's particles of
+    min(1, (L'/L)^gamma) (0 outside the support) is compared with pca_target.
+    Returns {k: a}."""
+    lo = {k: math.log(a_prev.get(k, 1.0)) - PCA_LOG_SPAN for k in fits}
+    hi = {k: math.log(a_prev.get(k, 1.0)) + PCA_LOG_SPAN for k in fits}
+    trial = [pca_trial_draws(s, i, stage) for i in range(len(parts))]
+    for _ in range(s.pca_bisect_iters):
+        mid = {k: 0.5 * (lo[k] + hi[k]) for k in fits}
+        props = [pca_step(p, fits[p.model(s)], math.exp(mid[p.model(s)]), s, *trial[i])
+                 if p.model(s) in fits else None for i, p in enumerate(parts)]
+        live = [i for i in range(len(parts)) if props[i] is not None]
+        ll_new = np.full(len(parts), -np.inf)
+        if live:
+            ll_new[live] = loglik([props[i] for i in live])
+        acc = {k: [] for k in fits}
+        for i, p in enumerate(parts):
+            k = p.model(s)
+            if k in fits:
+                acc[k].append(0.0 if props[i] is None else min(1.0, math.exp(min(0.0, gamma * (ll_new[i] - ll[i])))))
+        for k in fits:
+            if np.mean(acc[k]) > s.pca_target:
+                lo[k] = mid[k]
+            else:
+                hi[k] = mid[k]
+    return {k: math.exp(0.5 * (lo[k] + hi[k])) for k in fits}
+
+
+def propose_adaptive(p: Particle, s: SMCSettings, i: int, stage: int, sweep: int, fits, scales):
+    """The move set of propose() with the perturb move replaced by the
+    adaptive principal-direction random walk (models without a fit keep the
+    fixed-scale one)."""
+    d0 = draws(s.seed, s.sounding, i, PURPOSE_MOVE, stage, sweep)[0]
+    move = min(int(u01_from(d0[0]) * 6), 5)
+    k = p.model(s)
+    if move != 5 or k not in fits:
+        return propose(p, s, i, stage, sweep)
+    d1 = draws(s.seed, s.sounding, i, PURPOSE_VALUE, stage, sweep)[0]
+    return move, pca_step(p, fits[k], scales[k], s, float(u01_from(d0[1])), float(gauss_pair(d1[1], d1[2])))
+
+
+# ------------------------------------------------ posterior predictive (PPD)
+def ppd_summary(y_model, y_obs, eps_an, eps_mn):
+    """Per-gate summaries of the posterior predictive distribution
+    p(y~ | y) = int p(y~ | theta) pi(theta | y) d theta (the goodness of fit
+    of Section 4.1) over equally weighted posterior particles with predictions
+    y_model [N, G] and Gaussian noise of variance v = eps_an^2 + (eps_mn yhat)^2:
+      mean_g = (1/N) sum_i yhat_ig,
+      var_g  = (1/N) sum_i [ v_ig + (yhat_ig - mean_g)^2 ]   (law of total variance),
+      z_g    = (y_g - mean_g) / sqrt(var_g)  (the data standardised to the PPD).
+    Returns (mean [G], var [G], z [G])."""
+    y_model = np.asarray(y_model, dtype=np.float64)
+    N = y_model.shape[0]
+    mean = y_model.sum(axis=0) / N
+    v = np.asarray(eps_an, dtype=np.float64) ** 2 + (eps_mn * y_model) ** 2
+    var = (v + (y_model - mean) ** 2).sum(axis=0) / N
+    z = (np.asarray(y_obs, dtype=np.float64) - mean) / np.sqrt(var)
+    return mean, var, z

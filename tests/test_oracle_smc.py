@@ -203,3 +203,83 @@ def test_rj_toy_model_probabilities():
         freq.append(res.counts / res.counts.sum())
     freq = np.mean(freq, axis=0)
     assert np.all(np.abs(freq - post) < 0.05), (freq, post)
+
+
+def test_ppd_summary_matches_sampling_the_predictive_mixture():
+    """Drawing y~ from the mixture (a particle uniformly, then its Gaussian
+    noise) reproduces the closed-form PPD mean and variance; one particle
+    reduces to its own prediction and noise variance."""
+    rng = np.random.default_rng(4)
+    N, G = 40, 6
+    y_model = np.exp(rng.normal(-25.0, 1.0, (N, G))) * rng.choice([-1.0, 1.0], (N, G))
+    y_obs = y_model[0] * 1.1
+    ea, em = 1e-13, 0.03
+    mean, var, z = R.ppd_summary(y_model, y_obs, ea, em)
+    M = 400000
+    pick = rng.integers(0, N, M)
+    mu = y_model[pick]
+    draws_ = mu + np.sqrt(ea ** 2 + (em * mu) ** 2) * rng.standard_normal((M, G))
+    se = np.sqrt(var / M)
+    assert np.all(np.abs(draws_.mean(axis=0) - mean) < 5 * se)
+    assert np.all(np.abs(draws_.var(axis=0) / var - 1.0) < 0.02)
+    m1, v1, z1 = R.ppd_summary(y_model[:1], y_obs, ea, em)
+    assert np.allclose(m1, y_model[0]) and np.allclose(v1, ea ** 2 + (em * y_model[0]) ** 2)
+    assert np.allclose(z1, (y_obs - y_model[0]) / np.sqrt(v1))
+
+
+# ----------------------------------------------- adaptive within-model proposal
+def test_pca_fit_and_scale_on_a_gaussian_target():
+    """On a Gaussian target the fitted eigenvalues are the target's variances
+    and the move along an eigenvector with standard deviation a sqrt(Lambda_r)
+    is a 1-D random walk on a Gaussian, accepted with probability
+    (2 / pi) arctan(2 / a): the bisection for 0.44 must land on
+    a = 2 / tan(0.22 pi) = 2.4175."""
+    mu = np.array([-2.0, -1.0, 100.0, 200.0, 0.4, 0.5, 0.5])
+    sd = np.array([0.1, 0.1, 5.0, 5.0, 0.05, 0.05, 0.05])
+    s = R.SMCSettings(n_particles=3000, kappa_max=1, lambda_max=1, step_phi=0.1, step_z=5.0, step_m=0.05,
+                      step_tau=0.05, step_c=0.05, pca_bisect_iters=12, seed=2)
+    rng = np.random.default_rng(1)
+    tmpl = R.Particle(1, 1, 0.0, [0.0], [0.0], [0.0], [0.0], 0.5, 0.5)
+    parts = [R.with_theta(tmpl, s, mu + sd * rng.standard_normal(7)) for _ in range(s.n_particles)]
+
+    def loglik(ps):
+        th = np.array([R.theta_of(p, s) for p in ps])
+        return -0.5 * np.sum(((th - mu) / sd) ** 2, axis=1)
+
+    fits = R.fit_model_gaussians(parts, s)
+    (k, (m_fit, U, lam)), = fits.items()
+    # sorted sample eigenvalues spread around repeated population values
+    assert np.allclose(np.sort(lam), np.sort(sd ** 2 * (1 + 1e-4)), rtol=0.15)
+    assert abs(lam.sum() / np.sum(sd ** 2) - 1.0) < 0.03
+    assert np.allclose(m_fit, mu, atol=4 * sd / math.sqrt(s.n_particles) * 1.5)
+    a = R.pca_bisect_scales(parts, loglik(parts), fits, s, stage=3, gamma=1.0, loglik=loglik, a_prev={})[k]
+    a_star = 2.0 / math.tan(0.22 * math.pi)
+    assert abs(a / a_star - 1.0) < 0.1, (a, a_star)
+
+
+@pytest.mark.slow
+def test_adaptive_smc_evidence_on_toy_with_closed_form():
+    """The adaptive within-model proposal keeps the static-SMC evidence of the
+    closed-form toy."""
+    est = []
+    for seed in range(10):
+        s = R.SMCSettings(n_particles=300, kappa_max=0, lambda_max=0, n_sweeps=6, adaptive=True, seed=seed)
+        res = R.run(s, toy_evidence_loglik)
+        assert res.gammas[-1] == 1.0
+        est.append(res.log_z[0])
+    est = np.array(est)
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - toy_log_z()) < 3 * se + 0.02
+    assert all(len(d) == 1 for d in res.pca_scales)
+
+
+@pytest.mark.slow
+def test_adaptive_rj_toy_model_probabilities():
+    post = toy_rj_posterior()
+    freq = []
+    for seed in range(4):
+        s = R.SMCSettings(n_particles=600, kappa_max=2, lambda_max=0, n_sweeps=10, adaptive=True, seed=seed)
+        res = R.run(s, toy_rj_loglik)
+        freq.append(res.counts / res.counts.sum())
+    freq = np.mean(freq, axis=0)
+    assert np.all(np.abs(freq - post) < 0.05), (freq, post)
