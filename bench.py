@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 form, gate-transform variants, bucketed order and adjoint measurements")
     ap.add_argument("--rjsmc-only", action="store_true", help="run only the RJSMC measurement (profiling)")
+    ap.add_argument("--convergence-study", action="store_true",
+                    help="fraction of soundings whose best particle reaches the truth's likelihood level, per "
+                         "sampler setting (8 soundings of the 3-layer data, 2 seeds)")
     ap.add_argument("--flight-line", type=int, default=0, metavar="S",
                     help="run only the flight-line sampler: S soundings x 2048 particles in one sampler")
     return ap.parse_args()
@@ -220,6 +223,43 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     return out
 
 
+def convergence_study(torch, L, I):
+    """8 noisy copies of the 3-layer sounding, N = 256, kappa <= 3, lambda <= 4:
+    for each sampler setting and seed, the fraction of soundings whose best
+    final particle is within 50 of the truth's log-likelihood (both from the
+    GPU's FP64 forward model) and the median |z| of the data against the
+    posterior predictive."""
+    from paper_2109_00661_gb300 import smc as S
+    sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
+    truth = I.truth_3layer()
+    y_true = L.forward_f64(sysg, I.to_torch(truth, torch.float64)).cpu().numpy()[0]
+    SN, N = 8, 256
+    data = np.stack([I.noisy(y_true, seed=k) for k in range(SN)])
+    ll_true = np.array([L.loglik_f64(sysg, I.to_torch(truth, torch.float64), data[k], I.EPS_AN,
+                                     I.EPS_MN).cpu().numpy()[0] for k in range(SN)])
+    rows = []
+    for label, kw, sweeps in (("walk, 10 sweeps", {}, 10), ("adaptive, 10 sweeps", {"adaptive": 1}, 10),
+                              ("walk, 20 sweeps", {}, 20), ("adaptive, 20 sweeps", {"adaptive": 1}, 20),
+                              ("walk, 40 sweeps", {}, 40), ("adaptive, 40 sweeps", {"adaptive": 1}, 40),
+                              ("walk, 10 sweeps, alpha 0.9", {"alpha": 0.9}, 10),
+                              ("adaptive, 10 sweeps, alpha 0.9", {"adaptive": 1, "alpha": 0.9}, 10),
+                              ("adaptive, 10 sweeps + 2 Langevin", {"adaptive": 1, "n_langevin": 2}, 10)):
+        for seed in (3, 4):
+            args = dict(n_particles=N, n_soundings=SN, kappa_max=3, lambda_max=4, seed=seed)
+            args.update(kw)
+            sm = S.SMC(sysg, data, I.EPS_AN, I.EPS_MN, **args)
+            sm.init()
+            stages = sm.run(max_stages=400, n_sweeps=sweeps)
+            _, _, z = sm.ppd()
+            ll = sm.get_particles(0).ll.reshape(SN, N)
+            rows.append({"setting": label, "seed": seed, "stages": stages,
+                         "converged": float(np.mean(ll.max(axis=1) > ll_true - 50)),
+                         "median_abs_z": float(np.median(np.abs(z)))})
+            sm.close()
+    sysg.close()
+    return rows
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -278,6 +318,9 @@ def main():
         truth, _ = I.flight_line(args.flight_line)
         out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth)
         print(json.dumps({"flight_line": out}), flush=True)
+        return
+    if args.convergence_study:
+        print(json.dumps({"convergence_study": convergence_study(torch, L, I)}), flush=True)
         return
     if args.rjsmc_only:
         print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())}), flush=True)

@@ -219,6 +219,10 @@ typedef struct {
     int n_langevin;                        /* Langevin sweeps per stage after the random walks (0..1000; 0: off) */
     double langevin_h;                     /* initial Langevin step h in units of the random-walk scales (> 0) */
     int langevin_adapt;                    /* 1: after each stage h <- h exp(2 (rate - 0.574)), in [1e-6, 10] */
+    int adaptive;                          /* 1: the adaptive within-model proposal of Section 3.2 (below) */
+    double pca_target;                     /* its target acceptance rate (0.44) */
+    int pca_bisect_iters;                  /* bisection steps on trial proposals per stage (1..60) */
+    double pca_ridge;                      /* covariance ridge, fraction of the random-walk steps (>= 0) */
 } smc_desc;
 
 typedef struct smc_state smc_state;
@@ -235,7 +239,8 @@ typedef struct {
 
 /* Fills *d with the defaults (N = 256, kappa_max = 3, lambda_max = 4,
  * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2),
- * no Langevin sweeps, langevin_h = 0.1, langevin_adapt = 1). */
+ * no Langevin sweeps, langevin_h = 0.1, langevin_adapt = 1, adaptive = 0,
+ * pca_target = 0.44, pca_bisect_iters = 6, pca_ridge = 0.01). */
 int smc_desc_defaults(smc_desc *d);
 
 /* Synchronous.  y_obs [host, S x G] observed gates per sounding; eps_an [host, G];
@@ -337,6 +342,38 @@ int smc_get_particles(const smc_state *st, int which, smc_particles_host *h);
  * gamma [S], log_z [S x M] and the stage counter). */
 int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *gamma, const double *log_z,
                       int stage);
+
+/* The adaptive within-model proposal of Section 3.2, for the current stage
+ * (smc_mutate calls it before its sweeps when desc.adaptive is set): per
+ * sounding and model k with at least two particles, the mean mu_k and
+ * covariance Sigma_k of the continuous vector theta (phi_b, phi_c, z_c, z_m,
+ * m, the tau coordinate, c) over the model's particles, plus (pca_ridge s_j)^2
+ * on the diagonal (s_j the random-walk step of component j), decomposed as
+ * U Lambda U^T by Jacobi rotations in FP64; then desc.pca_bisect_iters steps of
+ * bisection on log a_k within +-3 of the previous stage's value, each a forward
+ * pass over trial proposals theta + a sqrt(Lambda_r) xi U_r (r uniform, xi
+ * normal, the same draws at every step), comparing the model's mean
+ * min(1, (L'/L)^gamma) with desc.pca_target.  The perturb move of smc_mutate
+ * then steps along U_r with standard deviation a_k sqrt(Lambda_r); models
+ * without a fit keep the fixed-scale component-wise walk. */
+int smc_adapt(smc_state *st);
+/* Synchronous copies of the fitted proposal, D = 3 + 2 kappa_max + 2 lambda_max:
+ * mu [S][M][D], U [S][M][D][D] (row j, column r = direction r), lam [S][M][D],
+ * scale [S][M], ok [S][M] (entries past a model's own dimension are unused).
+ * Any pointer may be NULL. */
+int smc_get_adaptation(const smc_state *st, double *mu, double *U, double *lam, double *scale, int *ok);
+
+/* Posterior predictive summaries (the goodness of fit of Section 4.1) over
+ * each sounding's current particles, which after smc_run are equally weighted
+ * draws from the posterior (models mixed by their counts): the forward model
+ * of every particle, then per gate, in FP64,
+ *   mean = (1/N) sum_i yhat_i,  var = (1/N) sum_i [v(yhat_i) + (yhat_i - mean)^2],
+ *   z = (y - mean) / sqrt(var),  v(yhat) = eps_an^2 + (eps_mn yhat)^2,
+ * the moments of p(y~ | y) = int p(y~ | theta) pi(theta | y) d theta and the
+ * data standardised to it.  mean, var, z: [host] S x G (any may be NULL);
+ * gates_host: [host] P x G predictions (may be NULL).  The first call
+ * allocates P x G floats of device scratch held by the sampler.  Synchronous. */
+int smc_ppd(smc_state *st, double *mean, double *var, double *z, float *gates_host);
 
 /* Checkpoint / resume.  smc_checkpoint writes a self-describing image of the
  * sampler's dynamic state (current particles with their log-likelihoods,

@@ -70,6 +70,10 @@ class SMCDesc(ctypes.Structure):
         ("n_langevin", c_int),
         ("langevin_h", c_double),
         ("langevin_adapt", c_int),
+        ("adaptive", c_int),
+        ("pca_target", c_double),
+        ("pca_bisect_iters", c_int),
+        ("pca_ridge", c_double),
     ]
 
 
@@ -111,6 +115,9 @@ SIGNATURES = {
     "smc_grad_current": ([c_void_p, c_void_p], c_int),
     "smc_langevin_propose": ([c_void_p, c_int, c_int], c_int),
     "smc_langevin": ([c_void_p, c_int], c_int),
+    "smc_ppd": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "smc_adapt": ([c_void_p], c_int),
+    "smc_get_adaptation": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_checkpoint": ([c_void_p, c_void_p, ctypes.POINTER(ctypes.c_size_t)], c_int),
     "smc_restore": ([c_void_p, c_void_p, ctypes.c_size_t], c_int),
     "smc_langevin_stats": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),

@@ -36,6 +36,8 @@ constexpr int kPurposeMove = 64, kPurposeValue = 65, kPurposeAccept = 66, kPurpo
 // Langevin: acceptance uniform, and normal j of the proposal from words
 // 2 (j % 2), 2 (j % 2) + 1 of the block with purpose kPurposeLangevin0 + j / 2.
 constexpr int kPurposeLangevinAccept = 68, kPurposeLangevin0 = 72;
+// Adaptive within-model proposal: trial draws of the scale bisection.
+constexpr int kPurposePcaTrial = 69;
 // Particle-space gradient slots: phi_b, phi_c[KS], z_c[KS], z_m[KS], m[KS],
 // tau coordinate, c.
 constexpr int GD = AEM_SMC_GRAD_DIM;
@@ -104,7 +106,7 @@ struct PState {
 };
 
 struct Params {
-    int N, S, kappa_max, lambda_max, M, LMS, tau_log_prior;
+    int N, S, kappa_max, lambda_max, M, LMS, tau_log_prior, adaptive, DM;
     double zmax, phi_lo, phi_hi, logtau_lo, logtau_hi, step_phi, step_m, step_tau, step_c, step_z;
     unsigned long long seed;
 };
@@ -441,10 +443,17 @@ __global__ void gather_kernel(PState dst, PState src, const int *anc, int P) {
 }
 
 // ---------------------------------------------------------- RJ proposal (a9)
+// Adaptive principal-direction step (defined with the Langevin helpers below).
+struct PcaView {
+    const double *U, *lam, *a;
+    const int *ok;
+};
+__device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int lam, const Params &pr, PcaView pv,
+                         double a, double u_comp, double xi);
 __device__ inline bool in_bounds_open(double v, double lo, double hi) { return lo < v && v < hi; }
 
 __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage,
-                               int sweep) {
+                               int sweep, PcaView pv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
     const int s = i / pr.N, j = i - s * pr.N;
@@ -521,6 +530,11 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
             else
                 zz[i * KS + q] = (float)z;
         }
+    } else if (pr.adaptive && pv.ok[s * pr.M + kappa * (pr.lambda_max + 1) + lam]) {
+        // the paper's adaptive move: a random walk along a principal direction
+        // of the model's fitted Gaussian (Section 3.2)
+        const int k = s * pr.M + kappa * (pr.lambda_max + 1) + lam;
+        ok = pca_step(cur, prop, i, s, kappa, lam, pr, pv, pv.a[k], u1, gauss(d1[1], d1[2]));
     } else {  // component-wise Gaussian random walk
         const int ncomp = 1 + kappa + lam + 2;
         int at = (int)(u1 * ncomp);
@@ -768,6 +782,216 @@ __global__ void langevin_accept_kernel(PState cur, PState prop, float *gcur, con
     }
 }
 
+// ------------------------------------------- adaptive within-model proposal
+// Section 3.2: per (sounding, model) a Gaussian fitted to the model's
+// particles, its eigen-decomposition, and a random walk along a uniformly
+// chosen principal direction U_r with standard deviation a sqrt(Lambda_r).
+__device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int lam, const Params &pr, PcaView pv,
+                         double a, double u_comp, double xi) {
+    const int k = s * pr.M + kappa * (pr.lambda_max + 1) + lam;
+    const int d = 3 + 2 * kappa + 2 * lam, DM = pr.DM;
+    int r = (int)(u_comp * d);
+    r = r > d - 1 ? d - 1 : r;
+    const double *U = pv.U + (size_t)k * DM * DM;
+    const double step = a * sqrt(pv.lam[(size_t)k * DM + r]) * xi;
+    for (int j = 0; j < d; ++j) {
+        const ThetaRef rc = theta_ref(cur, i, j, kappa, lam, pr);
+        const ThetaRef rp = theta_ref(prop, i, j, kappa, lam, pr);
+        const double v = theta_value(rc, pr) + step * U[(size_t)j * DM + r];
+        *rp.x = (float)((rp.is_tau && pr.tau_log_prior) ? pow(10.0, v) : v);
+    }
+    bool ok = in_bounds_open(prop.phib[i], pr.phi_lo, pr.phi_hi) && in_bounds_open(prop.c[i], 0.0, 1.0);
+    for (int q = 0; q < kappa; ++q) ok = ok && in_bounds_open(prop.phic[i * KS + q], pr.phi_lo, pr.phi_hi);
+    for (int q = 0; q < lam; ++q) ok = ok && in_bounds_open(prop.mv[i * KS + q], 0.0, 1.0);
+    ok = ok && ordered_open(prop.zc + (size_t)i * KS, kappa, pr.zmax) &&
+         ordered_open(prop.zm + (size_t)i * KS, lam, pr.zmax);
+    if (pr.tau_log_prior)
+        ok = ok && prop.tau[i] > 0.f && in_bounds_open(log10((double)prop.tau[i]), pr.logtau_lo, pr.logtau_hi);
+    else
+        ok = ok && in_bounds_open(prop.tau[i], 0.0, 1.0);
+    return ok;
+}
+
+constexpr int kFitThreads = 128;
+constexpr int kJacobiSweeps = 30;
+
+// One CTA per (sounding, model): mean and (biased) covariance of theta over
+// the model's particles in FP64 with fixed-order sums, plus
+// (ridge * step_j)^2 on the diagonal, then cyclic Jacobi rotations (thread 0,
+// in shared memory) to Sigma = U Lambda U^T.  Models with fewer than two
+// particles get ok = 0 and their scale reset to 1.
+__global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const int *perm, const int *off,
+                                                              const int *counts, Params pr, double ridge,
+                                                              double *mu_out, double *U_out, double *lam_out,
+                                                              int *ok_out, double *a_out) {
+    extern __shared__ double sm_fit[];
+    const int DM = pr.DM;
+    double *A = sm_fit, *V = A + DM * DM, *mu = V + DM * DM;
+    const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
+    const int kappa = k / (pr.lambda_max + 1), lam = k - kappa * (pr.lambda_max + 1);
+    const int d = 3 + 2 * kappa + 2 * lam;
+    const int n = counts[b];
+    const int *idx = perm + (size_t)s * pr.N + off[s * (pr.M + 1) + k];
+    const int tid = threadIdx.x;
+    if (n < 2) {
+        if (tid == 0) {
+            ok_out[b] = 0;
+            a_out[b] = 1.0;
+        }
+        return;
+    }
+    for (int j = tid; j < d; j += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) acc += theta_value(theta_ref(st, idx[q], j, kappa, lam, pr), pr);
+        mu[j] = acc / n;
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        if (l < j) continue;
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const int i = idx[q];
+            acc += (theta_value(theta_ref(st, i, j, kappa, lam, pr), pr) - mu[j]) *
+                   (theta_value(theta_ref(st, i, l, kappa, lam, pr), pr) - mu[l]);
+        }
+        double c = acc / n;
+        if (j == l) {
+            const double sj = ridge * theta_ref(st, idx[0], j, kappa, lam, pr).scale;
+            c += sj * sj;
+        }
+        A[j * DM + l] = c;
+        A[l * DM + j] = c;
+    }
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        V[j * DM + l] = j == l ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double scale2 = 0.0;
+        for (int j = 0; j < d; ++j) scale2 += A[j * DM + j] * A[j * DM + j];
+        for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+            double offn = 0.0;
+            for (int p = 0; p < d; ++p)
+                for (int q = p + 1; q < d; ++q) offn += A[p * DM + q] * A[p * DM + q];
+            if (offn <= 1e-30 * scale2) break;
+            for (int p = 0; p < d; ++p) {
+                for (int q = p + 1; q < d; ++q) {
+                    const double apq = A[p * DM + q];
+                    if (apq == 0.0) continue;
+                    // rotation that zeroes A[p][q]: t = tan(phi) is the smaller root of
+                    // t^2 + 2 t th - 1 = 0 with th = (A_qq - A_pp) / (2 A_pq)
+                    const double th = (A[q * DM + q] - A[p * DM + p]) / (2.0 * apq);
+                    const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                    for (int r = 0; r < d; ++r) {
+                        if (r == p || r == q) continue;
+                        const double arp = A[r * DM + p], arq = A[r * DM + q];
+                        const double np_ = c * arp - sn * arq, nq_ = sn * arp + c * arq;
+                        A[r * DM + p] = np_;
+                        A[p * DM + r] = np_;
+                        A[r * DM + q] = nq_;
+                        A[q * DM + r] = nq_;
+                    }
+                    A[p * DM + p] -= t * apq;
+                    A[q * DM + q] += t * apq;
+                    A[p * DM + q] = 0.0;
+                    A[q * DM + p] = 0.0;
+                    for (int r = 0; r < d; ++r) {
+                        const double vrp = V[r * DM + p], vrq = V[r * DM + q];
+                        V[r * DM + p] = c * vrp - sn * vrq;
+                        V[r * DM + q] = sn * vrp + c * vrq;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        U_out[(size_t)b * DM * DM + (size_t)j * DM + l] = V[j * DM + l];
+    }
+    for (int j = tid; j < d; j += blockDim.x) {
+        mu_out[(size_t)b * DM + j] = mu[j];
+        const double lj = A[j * DM + j];
+        lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
+    }
+    if (tid == 0) ok_out[b] = 1;
+}
+
+// Trial proposals of the scale bisection: every particle of a fitted model
+// steps along its trial direction at scale exp((lo + hi) / 2) of its model;
+// the trial draws (purpose kPurposePcaTrial, sweep 0) are the same at every
+// bisection step.
+__global__ void pca_trial_kernel(PState cur, PState prop, int8_t *valid_out, Params pr, PcaView pv,
+                                 const double *lo, const double *hi, int stage) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pr.S * pr.N) return;
+    const int s = i / pr.N, j = i - s * pr.N;
+    const int kappa = cur.kappa[i], lam = cur.lam[i];
+    const int k = s * pr.M + kappa * (pr.lambda_max + 1) + lam;
+    copy_particle(prop, i, cur, i);
+    if (!pv.ok[k]) {
+        valid_out[i] = 0;
+        return;
+    }
+    uint32_t w[4];
+    block_draws(w, stream_key(pr.seed, s), (uint32_t)j, (uint32_t)kPurposePcaTrial, (uint32_t)stage, 0u);
+    const double a = exp(0.5 * (lo[k] + hi[k]));
+    const bool ok = pca_step(cur, prop, i, s, kappa, lam, pr, pv, a, u01(w[0]), gauss(w[1], w[2]));
+    if (!ok) copy_particle(prop, i, cur, i);
+    valid_out[i] = ok ? 1 : 0;
+}
+
+// One CTA per (sounding, model): mean over the model's particles of
+// min(1, (L'/L)^gamma) (0 for trials outside the support), in FP64 with a
+// fixed-order reduction; moves the bracket towards the target acceptance.
+__global__ void __launch_bounds__(128) pca_stat_kernel(const double *ll_cur, const double *ll_prop,
+                                                       const int8_t *valid, const int *perm, const int *off,
+                                                       const int *counts, const int *ok, const double *gamma,
+                                                       Params pr, double target, double *lo, double *hi) {
+    __shared__ double red[128];
+    const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
+    if (!ok[b]) return;
+    const int n = counts[b];
+    const int *idx = perm + (size_t)s * pr.N + off[s * (pr.M + 1) + k];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int i = idx[q];
+        if (valid[i]) {
+            const double dl = gamma[s] * (ll_prop[i] - ll_cur[i]);
+            acc += dl >= 0.0 ? 1.0 : exp(dl);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mid = 0.5 * (lo[b] + hi[b]);
+        if (red[0] / n > target)
+            lo[b] = mid;
+        else
+            hi[b] = mid;
+    }
+}
+
+__global__ void pca_bracket_kernel(const int *ok, const double *a, int n, double span, double *lo, double *hi) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const double la = log(a[b]);
+    lo[b] = la - span;
+    hi[b] = la + span;
+}
+
+__global__ void pca_finish_kernel(const int *ok, const double *lo, const double *hi, int n, double *a) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && ok[b]) a[b] = exp(0.5 * (lo[b] + hi[b]));
+}
+
 // Between stages: h <- h exp(2 (rate - 0.574)) per sounding, clamped to
 // [1e-6, 10] (0.574: the optimal MALA acceptance of Roberts & Rosenthal 1998).
 __global__ void langevin_adapt_kernel(const int *lacc, const int *lprop, int S, double *lang_h) {
@@ -776,6 +1000,47 @@ __global__ void langevin_adapt_kernel(const int *lacc, const int *lprop, int S, 
     const double rate = lprop[s] > 0 ? (double)lacc[s] / lprop[s] : 0.574;
     const double h = lang_h[s] * exp(2.0 * (rate - 0.574));
     lang_h[s] = h < 1e-6 ? 1e-6 : (h > 10.0 ? 10.0 : h);
+}
+
+// Posterior predictive summaries (Section 4.1): one CTA per (sounding, gate)
+// over the sounding's equally weighted particles, FP64 with fixed-order
+// reductions: mean, variance of the predictive mixture (noise variance plus
+// the spread of the predictions), and the data standardised to it.
+__global__ void __launch_bounds__(256) ppd_kernel(const float *gates, int N, int G, const double *y_obs,
+                                                  const double *eps_an, double eps_mn, double *mean, double *var,
+                                                  double *z) {
+    const int s = blockIdx.x / G, g = blockIdx.x - (blockIdx.x / G) * G;
+    __shared__ double red[256];
+    const float *col = gates + (size_t)s * N * G + g;
+    double a = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a += (double)col[(size_t)i * G];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double mu = red[0] / N;
+    __syncthreads();
+    const double ea = eps_an[g];
+    double b = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double yh = (double)col[(size_t)i * G];
+        const double d = yh - mu;
+        b += ea * ea + (eps_mn * yh) * (eps_mn * yh) + d * d;
+    }
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double v = red[0] / N;
+        mean[(size_t)s * G + g] = mu;
+        var[(size_t)s * G + g] = v;
+        z[(size_t)s * G + g] = (y_obs[(size_t)s * G + g] - mu) / sqrt(v);
+    }
 }
 
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n) {
@@ -836,6 +1101,13 @@ struct smc_state {
     // Langevin: merged-layer gradient, particle-space gradients of the current
     // and proposed particles, log q(theta' | theta), per-sounding counts.
     float *mgrad = nullptr, *gcur = nullptr, *gprop = nullptr;
+    float *ppd_gates = nullptr;  // [P][G], allocated on the first smc_ppd call
+    // adaptive within-model proposal, per (sounding, model): mean [DM], U
+    // [DM][DM] (column r = direction r), Lambda [DM], ok, scale a, bracket
+    double *pca_mu = nullptr, *pca_U = nullptr, *pca_lam = nullptr, *pca_a = nullptr, *pca_lo = nullptr,
+           *pca_hi = nullptr;
+    int *pca_ok = nullptr;
+    double *ppd_out = nullptr;   // [3][S][G]
     double *lq = nullptr, *lang_h = nullptr;
     int *lacc = nullptr, *lprop = nullptr;
     bool gcur_valid = false;
@@ -906,6 +1178,9 @@ int check_desc(const smc_desc *d) {
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid zmax / alpha / c_mut / r_max / prior bounds");
     if (d->tau_log_prior && !(d->logtau_hi > d->logtau_lo))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid log10 tau bounds");
+    if (d->adaptive && (!(d->pca_target > 0 && d->pca_target < 1) || d->pca_bisect_iters < 1 ||
+                        d->pca_bisect_iters > 60 || !(d->pca_ridge >= 0)))
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid pca_target / pca_bisect_iters / pca_ridge");
     if (d->n_langevin < 0 || d->n_langevin > 1000 || !(d->langevin_h > 0))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: n_langevin outside 0..1000 or langevin_h <= 0");
     return AEM_OK;
@@ -939,6 +1214,10 @@ extern "C" int smc_desc_defaults(smc_desc *d) {
     d->n_langevin = 0;
     d->langevin_h = 0.1;
     d->langevin_adapt = 1;
+    d->adaptive = 0;
+    d->pca_target = 0.44;
+    d->pca_bisect_iters = 6;
+    d->pca_ridge = 0.01;
     return AEM_OK;
 }
 
@@ -978,6 +1257,8 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
     p.step_c = desc->step_c;
     p.step_z = desc->step_z;
     p.seed = desc->seed;
+    p.adaptive = desc->adaptive;
+    p.DM = 3 + 2 * desc->kappa_max + 2 * desc->lambda_max;
     const int G = sys->host.G;
     const size_t P = st->P;
     if ((rc = alloc_pstate(st, &st->cur)) || (rc = alloc_pstate(st, &st->alt)) || (rc = alloc_pstate(st, &st->prop)) ||
@@ -994,7 +1275,12 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->eps_an, (size_t)G)) || (rc = dalloc(st, &st->mgrad, P * st->LMS * 5)) ||
         (rc = dalloc(st, &st->gcur, P * GD)) || (rc = dalloc(st, &st->gprop, P * GD)) ||
         (rc = dalloc(st, &st->lq, P)) || (rc = dalloc(st, &st->lacc, (size_t)st->S)) ||
-        (rc = dalloc(st, &st->lprop, (size_t)st->S)) || (rc = dalloc(st, &st->lang_h, (size_t)st->S))) {
+        (rc = dalloc(st, &st->lprop, (size_t)st->S)) || (rc = dalloc(st, &st->lang_h, (size_t)st->S)) ||
+        (rc = dalloc(st, &st->pca_mu, (size_t)st->S * st->M * p.DM)) ||
+        (rc = dalloc(st, &st->pca_U, (size_t)st->S * st->M * p.DM * p.DM)) ||
+        (rc = dalloc(st, &st->pca_lam, (size_t)st->S * st->M * p.DM)) ||
+        (rc = dalloc(st, &st->pca_a, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_lo, (size_t)st->S * st->M)) ||
+        (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M))) {
         smc_destroy(st);
         return rc;
     }
@@ -1004,6 +1290,11 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         std::vector<double> h0(st->S, desc->langevin_h);
         e = cudaMemcpy(st->lang_h, h0.data(), sizeof(double) * st->S, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess) {
+        std::vector<double> a0((size_t)st->S * st->M, 1.0);
+        e = cudaMemcpy(st->pca_a, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(st->pca_ok, 0, sizeof(int) * st->S * st->M);
     if (e != cudaSuccess) {
         smc_destroy(st);
         return cuda_fail(e, "smc_create: upload data");
@@ -1031,8 +1322,12 @@ extern "C" int smc_init(smc_state *st) {
     AEM_CUDA_TRY(cudaMemsetAsync(st->lprop, 0, sizeof(int) * st->S, st->stream));
     {
         std::vector<double> h0(st->S, st->d.langevin_h);
+        std::vector<double> a0((size_t)st->S * st->M, 1.0);
         AEM_CUDA_TRY(cudaMemcpyAsync(st->lang_h, h0.data(), sizeof(double) * st->S, cudaMemcpyHostToDevice,
                                      st->stream));
+        AEM_CUDA_TRY(cudaMemcpyAsync(st->pca_a, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice,
+                                     st->stream));
+        AEM_CUDA_TRY(cudaMemsetAsync(st->pca_ok, 0, sizeof(int) * st->S * st->M, st->stream));
         AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
     }
     st->stage = 0;
@@ -1079,10 +1374,46 @@ extern "C" int smc_resample(smc_state *st) {
     return AEM_OK;
 }
 
+static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, st->pca_a, st->pca_ok}; }
+
 extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_propose: NULL state");
     propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid, st->pr,
-                                                                    stage, sweep);
+                                                                    stage, sweep, pca_view(st));
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+// Section 3.2's adaptive within-model proposal for the current stage: fit
+// each (sounding, model)'s Gaussian, then bisect its scale on trial
+// proposals (desc.pca_bisect_iters forward passes) towards desc.pca_target.
+static int adapt_stage(smc_state *st) {
+    int rc = launch_group(st);
+    if (rc) return rc;
+    const int nb = st->S * st->M, DM = st->pr.DM;
+    const size_t smem = sizeof(double) * (2 * (size_t)DM * DM + DM);
+    if (smem > 48 * 1024)
+        AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    pca_fit_kernel<<<nb, kFitThreads, smem, st->stream>>>(st->cur, st->perm, st->off, st->counts, st->pr,
+                                                           st->d.pca_ridge, st->pca_mu, st->pca_U, st->pca_lam,
+                                                           st->pca_ok, st->pca_a);
+    AEM_CUDA_TRY(cudaGetLastError());
+    pca_bracket_kernel<<<blocks_for(nb, 128), 128, 0, st->stream>>>(st->pca_ok, st->pca_a, nb, 3.0, st->pca_lo,
+                                                                     st->pca_hi);
+    AEM_CUDA_TRY(cudaGetLastError());
+    for (int it = 0; it < st->d.pca_bisect_iters; ++it) {
+        pca_trial_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->valid, st->pr,
+                                                                          pca_view(st), st->pca_lo, st->pca_hi,
+                                                                          st->stage);
+        AEM_CUDA_TRY(cudaGetLastError());
+        if ((rc = run_loglik(st, st->prop))) return rc;
+        pca_stat_kernel<<<nb, 128, 0, st->stream>>>(st->cur.ll, st->prop.ll, st->valid, st->perm, st->off,
+                                                    st->counts, st->pca_ok, st->gamma, st->pr, st->d.pca_target,
+                                                    st->pca_lo, st->pca_hi);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
+    pca_finish_kernel<<<blocks_for(nb, 128), 128, 0, st->stream>>>(st->pca_ok, st->pca_lo, st->pca_hi, nb,
+                                                                    st->pca_a);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -1143,6 +1474,7 @@ extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
     if ((rc = sweeps_for_stage(st, n_sweeps, &R))) return rc;
     AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, st->stream));
+    if (st->d.adaptive && (rc = adapt_stage(st))) return rc;
     for (int sw = 0; sw < R; ++sw) {
         if ((rc = smc_propose(st, st->stage, sw))) return rc;
         if ((rc = run_loglik(st, st->prop))) return rc;
@@ -1313,6 +1645,51 @@ extern "C" int smc_langevin(smc_state *st, int n_sweeps) {
     int rc = langevin_sweeps(st, n_sweeps);
     if (rc) return rc;
     AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return AEM_OK;
+}
+
+extern "C" int smc_ppd(smc_state *st, double *mean, double *var, double *z, float *gates_host) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_ppd: NULL state");
+    const int G = st->sys->host.G;
+    const size_t P = st->P, S = st->S;
+    int rc;
+    if (!st->ppd_gates) {
+        if ((rc = dalloc(st, &st->ppd_gates, P * G)) || (rc = dalloc(st, &st->ppd_out, 3 * S * G))) return rc;
+    }
+    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->P, st->LMS, st->m_nl, st->m_logsig,
+                                                                st->m_logh, st->m_m, st->m_logtau, st->m_c);
+    AEM_CUDA_TRY(cudaGetLastError());
+    aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
+    if ((rc = aem_forward_f32(st->sys, &mm, st->ppd_gates, nullptr, st->stream))) return rc;
+    double *o = st->ppd_out;
+    ppd_kernel<<<(unsigned)(S * G), 256, 0, st->stream>>>(st->ppd_gates, st->N, G, st->y, st->eps_an, st->eps_mn, o,
+                                                          o + S * G, o + 2 * S * G);
+    AEM_CUDA_TRY(cudaGetLastError());
+    if (mean) AEM_CUDA_TRY(cudaMemcpyAsync(mean, o, sizeof(double) * S * G, cudaMemcpyDeviceToHost, st->stream));
+    if (var) AEM_CUDA_TRY(cudaMemcpyAsync(var, o + S * G, sizeof(double) * S * G, cudaMemcpyDeviceToHost, st->stream));
+    if (z) AEM_CUDA_TRY(cudaMemcpyAsync(z, o + 2 * S * G, sizeof(double) * S * G, cudaMemcpyDeviceToHost, st->stream));
+    if (gates_host)
+        AEM_CUDA_TRY(cudaMemcpyAsync(gates_host, st->ppd_gates, sizeof(float) * P * G, cudaMemcpyDeviceToHost,
+                                     st->stream));
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return AEM_OK;
+}
+
+extern "C" int smc_adapt(smc_state *st) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_adapt: NULL state");
+    return adapt_stage(st);
+}
+
+extern "C" int smc_get_adaptation(const smc_state *cst, double *mu, double *U, double *lam, double *scale, int *ok) {
+    smc_state *st = const_cast<smc_state *>(cst);
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_get_adaptation: NULL state");
+    const size_t nb = (size_t)st->S * st->M, DM = st->pr.DM;
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    if (mu) AEM_CUDA_TRY(cudaMemcpy(mu, st->pca_mu, sizeof(double) * nb * DM, cudaMemcpyDeviceToHost));
+    if (U) AEM_CUDA_TRY(cudaMemcpy(U, st->pca_U, sizeof(double) * nb * DM * DM, cudaMemcpyDeviceToHost));
+    if (lam) AEM_CUDA_TRY(cudaMemcpy(lam, st->pca_lam, sizeof(double) * nb * DM, cudaMemcpyDeviceToHost));
+    if (scale) AEM_CUDA_TRY(cudaMemcpy(scale, st->pca_a, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+    if (ok) AEM_CUDA_TRY(cudaMemcpy(ok, st->pca_ok, sizeof(int) * nb, cudaMemcpyDeviceToHost));
     return AEM_OK;
 }
 

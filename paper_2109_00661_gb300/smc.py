@@ -151,6 +151,32 @@ class SMC:
         check(_lib.load().smc_set_particles(self._h, ctypes.byref(s), None if g is None else g.ctypes.data,
                                             None if lz is None else lz.ctypes.data, int(stage)), "smc_set_particles")
 
+    def adapt(self):
+        check(_lib.load().smc_adapt(self._h), "smc_adapt")
+
+    def adaptation(self):
+        """smc_get_adaptation: dict of mu [S, M, D], U [S, M, D, D], lam [S, M, D],
+        scale [S, M], ok [S, M] with D = 3 + 2 kappa_max + 2 lambda_max."""
+        D = 3 + 2 * self.desc.kappa_max + 2 * self.desc.lambda_max
+        mu, lam = np.zeros((self.S, self.M, D)), np.zeros((self.S, self.M, D))
+        U = np.zeros((self.S, self.M, D, D))
+        scale = np.zeros((self.S, self.M))
+        ok = np.zeros((self.S, self.M), dtype=np.int32)
+        check(_lib.load().smc_get_adaptation(self._h, mu.ctypes.data, U.ctypes.data, lam.ctypes.data,
+                                             scale.ctypes.data, ok.ctypes.data), "smc_get_adaptation")
+        return dict(mu=mu, U=U, lam=lam, scale=scale, ok=ok)
+
+    def ppd(self, want_gates=False):
+        """smc_ppd: per-gate posterior predictive mean, variance and the data
+        standardised to it, each [S, G]; with want_gates also the particles'
+        predictions [P, G]."""
+        G = self.system.G
+        mean, var, z = (np.zeros((self.S, G)) for _ in range(3))
+        gates = np.zeros((self.P, G), dtype=np.float32) if want_gates else None
+        check(_lib.load().smc_ppd(self._h, mean.ctypes.data, var.ctypes.data, z.ctypes.data,
+                                  gates.ctypes.data if want_gates else None), "smc_ppd")
+        return (mean, var, z, gates) if want_gates else (mean, var, z)
+
     def checkpoint(self) -> bytes:
         """smc_checkpoint: the sampler's dynamic state as bytes."""
         lib = _lib.load()
