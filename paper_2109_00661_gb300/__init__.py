@@ -78,6 +78,22 @@ class System:
               "aem_system_tables")
         return f, lam, hw, T
 
+    def autotune(self, models, repeats=3, stream=None):
+        """aem_autotune_forward on a sample batch (float32 CUDA model tensors):
+        records the fastest launch shape of the FP32 forward kernel for the
+        batch's lmax; returns (shape, per-shape ms, -1 where a shape does not fit)."""
+        torch = _torch()
+        ms = _models_struct(models, torch.float32)
+        shape = ctypes.c_int()
+        times = (ctypes.c_float * 5)()
+        check(_lib.load().aem_autotune_forward(self._h, ctypes.byref(ms), int(repeats), _stream_ptr(stream),
+                                               ctypes.byref(shape), times), "aem_autotune_forward")
+        return shape.value, [float(t) for t in times]
+
+    def set_forward_shape(self, lmax, shape):
+        """aem_forward_shape: the FP32 forward kernel's launch shape for lmax."""
+        check(_lib.load().aem_forward_shape(self._h, int(lmax), int(shape)), "aem_forward_shape")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().aem_system_destroy(self._h)

@@ -47,6 +47,9 @@ struct aem_system {
     // device status word: kernels record AEM_ERR_TIMEOUT here when a bounded
     // wait gives up (read and cleared by aem_system_status)
     int *d_status = nullptr;
+    // launch shape of the FP32 forward kernel per lmax (index into its shape
+    // table, 0 = default), set by aem_autotune_forward / aem_forward_shape
+    int f32_shape[AEM_MAX_LAYERS + 1] = {};
 };
 
 namespace aem {

@@ -501,11 +501,11 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
 
 // Shared memory (dynamic), in order: RS[F*LS], RB[F*LS], RC[F*LS], RAB[F],
 // RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), stmp[F*LS], hwp[K2] (float2),
-// imh_w[kWarps*F], imh[F], T[G*F] (float).
-#ifndef AEM_F32_MIN_BLOCKS
-#define AEM_F32_MIN_BLOCKS 4  // resident CTAs per SM the register allocation must allow (<= 64 registers)
-#endif
-__global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kernel(ModelsView<FP32Ops> mv, int F, int G, int K,
+// imh_w[NW*F], imh[F], T[G*F] (float).
+// NT threads per CTA; MINB resident CTAs per SM the register allocation must
+// allow (the launch shapes the autotuner chooses between).
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Ops> mv, int F, int G, int K,
                                                                int cc_form, int LS,
                                                                const float *__restrict__ g_omega,
                                                                const float *__restrict__ g_lam,
@@ -516,6 +516,7 @@ __global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kern
                                                                const double *__restrict__ y_obs, int obs_per,
                                                                const double *__restrict__ eps_an, double eps_mn,
                                                                double *__restrict__ ll_out) {
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
     ulonglong2 *RS = reinterpret_cast<ulonglong2 *>(smem_raw);
@@ -528,11 +529,11 @@ __global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kern
     float2 *stmp = reinterpret_cast<float2 *>(RY + (size_t)F * LS);
     float2 *hwp = stmp + (size_t)F * LS;
     float *imh_w = reinterpret_cast<float *>(hwp + K2);
-    float *imh = imh_w + (size_t)kWarps * F;
+    float *imh = imh_w + (size_t)NW * F;
     float *Ts = imh + F;
     __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
     __shared__ float lsig[AEM_MAX_LAYERS], lm[AEM_MAX_LAYERS], ltau[AEM_MAX_LAYERS], lc[AEM_MAX_LAYERS];
-    __shared__ double ll_part[kWarps];
+    __shared__ double ll_part[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < G * F; i += blockDim.x) Ts[i] = g_T[i];
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kern
             ltau[tid] = exp10f(mv.logtau[o]);
             lc[tid] = mv.c[o];
         }
-        for (int i = tid; i < kWarps * F; i += blockDim.x) imh_w[i] = 0.f;
+        for (int i = tid; i < NW * F; i += blockDim.x) imh_w[i] = 0.f;
         __syncthreads();
         // Cole-Cole per (frequency, layer): x = (w tau)^c e^{i pi c / 2}, s = i w mu0 sigma
         for (int i = tid; i < F * L; i += blockDim.x) {
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kern
         for (int j = tid; j < F; j += blockDim.x) {
             float acc = 0.f;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) acc += imh_w[w * F + j];
+            for (int w = 0; w < NW; ++w) acc += imh_w[w * F + j];
             imh[j] = acc;
         }
         __syncthreads();
@@ -676,10 +677,54 @@ __global__ void __launch_bounds__(kThreads, AEM_F32_MIN_BLOCKS) forward_f32_kern
     }
 }
 
-size_t smem_bytes_f32(int F, int G, int K, int LS) {
+size_t smem_bytes_f32(int F, int G, int K, int LS, int NW) {
     const size_t K2 = (K + 1) / 2;
     return sizeof(ulonglong2) * ((size_t)3 * F * LS + 2 * (size_t)F + K2) + sizeof(u64) * (size_t)F * LS +
-           sizeof(float2) * ((size_t)F * LS + K2) + sizeof(float) * ((size_t)kWarps * F + F + (size_t)G * F);
+           sizeof(float2) * ((size_t)F * LS + K2) + sizeof(float) * ((size_t)NW * F + F + (size_t)G * F);
+}
+
+// Launch shapes of forward_f32_kernel: (threads per CTA, resident CTAs per SM
+// the register budget must allow).  Index 0 is the default.
+struct F32Shape {
+    int nt, minb;
+};
+constexpr F32Shape kF32Shapes[] = {{256, 4}, {128, 8}, {512, 2}, {256, 3}, {128, 6}};
+constexpr int kNumF32Shapes = sizeof(kF32Shapes) / sizeof(kF32Shapes[0]);
+
+template <int NT, int MINB>
+int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
+                 const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
+                 cudaStream_t stream) {
+    const SystemTables &h = sys->host;
+    const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS, NT / 32);
+    auto kern = forward_f32_kernel<NT, MINB>;
+    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the kernel reads its tables from shared memory only: give the SM's
+    // unified L1/shared storage to shared memory so more CTAs stay resident
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0;
+    AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    if (per_sm < 1) return fail(AEM_ERR_UNSUPPORTED, "forward kernel: launch shape does not fit on an SM");
+    long long grid = (long long)sys->num_sms * per_sm;
+    if (grid > mv.n) grid = mv.n;
+    kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
+                                               sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
+                                               ll);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
+                       float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
+                       cudaStream_t stream) {
+    switch (idx) {
+        case 1: return launch_shape<128, 8>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        case 2: return launch_shape<512, 2>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        case 3: return launch_shape<256, 3>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        case 4: return launch_shape<128, 6>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        default: return launch_shape<256, 4>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+    }
 }
 
 template <class Models>
@@ -693,27 +738,11 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
     if (!models->nlayers || !models->logsig || !models->logh || !models->m || !models->logtau || !models->c)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL model array");
     if (ll && (!y_obs || !eps_an)) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL y_obs or eps_an");
-    const SystemTables &h = sys->host;
     ModelsView<FP32Ops> mv{models->n_models, models->lmax, models->nlayers, models->logsig, models->logh,
                            models->m, models->logtau, models->c};
     const int LS = models->lmax;
-    const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
-    auto kern = forward_f32_kernel;
-    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // the kernel reads its tables from shared memory only: give the SM's
-    // unified L1/shared storage to shared memory so more CTAs stay resident
-    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-    int per_sm = 0;
-    AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    long long grid = (long long)sys->num_sms * per_sm;
-    if (grid > models->n_models) grid = models->n_models;
-    kern<<<(unsigned)grid, kThreads, smem, (cudaStream_t)stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f,
-                                                                   sys->d_lam_f, sys->d_hw_f, sys->d_T_f, gates, imh,
-                                                                   y_obs, obs_per, eps_an, eps_mn, ll);
-    AEM_CUDA_TRY(cudaGetLastError());
-    return AEM_OK;
+    return launch_shape_index(sys->f32_shape[LS], sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
+                              (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -754,4 +783,64 @@ extern "C" int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *model
     return launch_forward<FP64Ops>(sys, models, gates, nullptr, y_obs, 0, eps_an, eps_mn, ll, stream,
                                    sys ? sys->d_omega_d : nullptr, sys ? sys->d_lam_d : nullptr,
                                    sys ? sys->d_hw_d : nullptr, sys ? sys->d_T_d : nullptr, "aem_loglik_f64");
+}
+
+extern "C" int aem_autotune_forward(aem_system *sys, const aem_models_f32 *sample, int repeats, void *stream,
+                                    int *shape_out, float *ms_out) {
+    if (!sys || !sample) return fail(AEM_ERR_INVALID_ARG, "aem_autotune_forward: NULL system or sample");
+    if (sample->n_models < 1 || sample->lmax < 1 || sample->lmax > AEM_MAX_LAYERS || repeats < 1)
+        return fail(AEM_ERR_INVALID_ARG, "aem_autotune_forward: empty sample, lmax out of range or repeats < 1");
+    if (!sample->nlayers || !sample->logsig || !sample->logh || !sample->m || !sample->logtau || !sample->c)
+        return fail(AEM_ERR_INVALID_ARG, "aem_autotune_forward: NULL model array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int LS = sample->lmax;
+    ModelsView<FP32Ops> mv{sample->n_models, sample->lmax, sample->nlayers, sample->logsig, sample->logh,
+                           sample->m, sample->logtau, sample->c};
+    float *gates = nullptr;
+    AEM_CUDA_TRY(cudaMallocAsync((void **)&gates, sizeof(float) * (size_t)sample->n_models * sys->host.G, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = AEM_OK, best = -1;
+    float best_ms = 0.f;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = fail(AEM_ERR_CUDA, "aem_autotune_forward: cudaEventCreate");
+    for (int c = 0; c < kNumF32Shapes && rc == AEM_OK; ++c) {
+        float ms = 0.f;
+        // one untimed launch, then the timed repeats
+        rc = launch_shape_index(c, sys, mv, LS, gates, nullptr, nullptr, 0, nullptr, 0.0, nullptr, s);
+        if (rc == AEM_ERR_UNSUPPORTED) {  // this shape does not fit on an SM: skip it
+            rc = AEM_OK;
+            if (ms_out) ms_out[c] = -1.f;
+            continue;
+        }
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < repeats && rc == AEM_OK; ++r)
+            rc = launch_shape_index(c, sys, mv, LS, gates, nullptr, nullptr, 0, nullptr, 0.0, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail(AEM_ERR_CUDA, "aem_autotune_forward: timing");
+            break;
+        }
+        ms /= repeats;
+        if (ms_out) ms_out[c] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(gates, s);
+    if (rc) return rc;
+    if (best < 0) return fail(AEM_ERR_UNSUPPORTED, "aem_autotune_forward: no launch shape fits");
+    sys->f32_shape[LS] = best;
+    if (shape_out) *shape_out = best;
+    return AEM_OK;
+}
+
+extern "C" int aem_forward_shape(aem_system *sys, int lmax, int shape) {
+    if (!sys || lmax < 1 || lmax > AEM_MAX_LAYERS || shape < 0 || shape >= kNumF32Shapes)
+        return fail(AEM_ERR_INVALID_ARG, "aem_forward_shape: invalid lmax or shape");
+    sys->f32_shape[lmax] = shape;
+    return AEM_OK;
 }

@@ -17,7 +17,7 @@ import oracle as O
 from paper_2109_00661_gb300 import inputs as I
 
 EPS_AN = I.EPS_AN
-DELTA_S32 = 1e-5   # FP32 spectrum, relative to A_f
+DELTA_S32 = 3e-5   # FP32 spectrum, relative to A_f (worst of 20,000 models per system: 2.0e-5, at L = 1-2)
 DELTA_S64 = 1e-12  # FP64 spectrum, relative to A_f
 DELTA_T = 1e-8     # table agreement, relative to each row's largest entry
 

@@ -199,3 +199,32 @@ def test_full_size_sampled_parity(lib, torch_mod):
     e = rel_err(y[idx].cpu().numpy().astype(np.float64), y_ref)
     assert_within(e, bound32(kap, sysg.F), "FP32 gates at full size")
     assert torch_mod.isfinite(y).all()
+
+
+@pytest.mark.parametrize("shape", range(5))
+def test_every_launch_shape_matches_oracle(lib, torch_mod, shape):
+    """Each launch shape the autotuner can choose passes the FP32 parity bar
+    on a batch that spans several CTAs per SM and a ragged tail."""
+    name = "forward-g30-f60-k200"
+    sysg = lib.System(**I.system_kwargs(name))
+    models = as_f32_inputs(I.random_models(3001, seed=17))
+    sysg.set_forward_shape(models["logsig"].shape[1], shape)
+    y, imh = lib.forward_f32(sysg, I.to_torch(models, torch_mod.float32), want_imh=True)
+    y_ref, imh_ref, absh, kap = oracle_ref(models, name)
+    y, imh = y.cpu().numpy().astype(np.float64), imh.cpu().numpy().astype(np.float64)
+    assert spectrum_err(imh, imh_ref, absh).max() < DELTA_S32
+    assert_within(rel_err(y, y_ref), bound32(kap, imh.shape[1]), f"FP32 gates, launch shape {shape}")
+
+
+def test_autotune_records_the_fastest_shape(lib, torch_mod):
+    sysg = lib.System(**I.system_kwargs("forward-g30-f60-k200"))
+    models = I.to_torch(I.random_models(1 << 15, seed=3), torch_mod.float32)
+    shape, ms = sysg.autotune(models, repeats=2)
+    fits = [t for t in ms if t > 0]
+    print(f"\nautotune: shape {shape}, ms per launch {['%.2f' % t for t in ms]}")
+    assert 0 <= shape < 5 and ms[shape] == min(fits)
+    # the recorded shape is used: results equal a launch forced to that shape
+    a = lib.forward_f32(sysg, models)
+    sysg.set_forward_shape(models["logsig"].shape[1], shape)
+    b = lib.forward_f32(sysg, models)
+    assert torch_mod.equal(a, b)
