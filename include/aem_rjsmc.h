@@ -141,17 +141,19 @@ int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const do
  * aem_loglik_f32 and every sampler call that evaluates the forward model).
  * Shapes: 0 = 256 threads per CTA with 4 resident CTAs per SM (the default),
  * 1 = 128 x 8, 2 = 512 x 2, 3 = 256 x 3, 4 = 128 x 6 (the register budget per
- * thread follows from the pair).  aem_autotune_forward times every shape that
+ * thread follows from the pair), each with a fixed grid-stride order of
+ * models; 5..9 = the same five with dynamic scheduling (a CTA claims its
+ * next model from a counter in stream-ordered scratch when it finishes one).  aem_autotune_forward times every shape that
  * fits on an SM on the caller's sample batch (one untimed launch, then
  * `repeats` launches timed with CUDA events on `stream`; synchronous), and
  * records the fastest for the sample's lmax in the system: later launches
  * with that lmax use it.  shape_out (may be NULL) receives the choice; ms_out
- * (may be NULL, 5 floats) the mean time per launch of each shape, -1 for a
+ * (may be NULL, AEM_F32_SHAPES floats) the mean time per launch of each shape, -1 for a
  * shape that does not fit.  It takes P x G floats of stream-ordered scratch
  * (cudaMallocAsync) for the duration of the call.  aem_forward_shape sets the
  * shape for an lmax directly.  Not thread-safe against concurrent launches on
  * the same system. */
-#define AEM_F32_SHAPES 5
+#define AEM_F32_SHAPES 10
 int aem_autotune_forward(aem_system *sys, const aem_models_f32 *sample, int repeats, void *stream, int *shape_out,
                          float *ms_out);
 int aem_forward_shape(aem_system *sys, int lmax, int shape);

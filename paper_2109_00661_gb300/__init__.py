@@ -85,7 +85,7 @@ class System:
         torch = _torch()
         ms = _models_struct(models, torch.float32)
         shape = ctypes.c_int()
-        times = (ctypes.c_float * 5)()
+        times = (ctypes.c_float * 10)()
         check(_lib.load().aem_autotune_forward(self._h, ctypes.byref(ms), int(repeats), _stream_ptr(stream),
                                                ctypes.byref(shape), times), "aem_autotune_forward")
         return shape.value, [float(t) for t in times]

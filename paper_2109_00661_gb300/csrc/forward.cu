@@ -503,8 +503,11 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
 // RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), stmp[F*LS], hwp[K2] (float2),
 // imh_w[NW*F], imh[F], T[G*F] (float).
 // NT threads per CTA; MINB resident CTAs per SM the register allocation must
-// allow (the launch shapes the autotuner chooses between).
-template <int NT, int MINB>
+// allow; DYN: models are handed out by a global counter (each CTA takes the
+// next unclaimed model when it finishes one) instead of the fixed grid stride,
+// which evens out CTAs that draw many deep models (the launch shapes the
+// autotuner chooses between).
+template <int NT, int MINB, bool DYN>
 __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Ops> mv, int F, int G, int K,
                                                                int cc_form, int LS,
                                                                const float *__restrict__ g_omega,
@@ -515,7 +518,8 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                                                                float *__restrict__ imh_out,
                                                                const double *__restrict__ y_obs, int obs_per,
                                                                const double *__restrict__ eps_an, double eps_mn,
-                                                               double *__restrict__ ll_out) {
+                                                               double *__restrict__ ll_out,
+                                                               int *__restrict__ work_counter) {
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
@@ -548,9 +552,12 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     const float mu0 = (float)kMu0;
     const int FK2 = F * K2;
 
-    for (int p = blockIdx.x; p < mv.n; p += gridDim.x) {
+    __shared__ int next_model;
+    for (int p = blockIdx.x; p < mv.n; p = DYN ? next_model : p + gridDim.x) {
         const int L = mv.nlayers[p];
         __syncthreads();
+        // claimed now, read after this model's later barriers
+        if (DYN && tid == 0) next_model = (int)gridDim.x + atomicAdd(work_counter, 1);
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             lsig[tid] = exp10f(mv.logsig[o]);
@@ -689,15 +696,17 @@ struct F32Shape {
     int nt, minb;
 };
 constexpr F32Shape kF32Shapes[] = {{256, 4}, {128, 8}, {512, 2}, {256, 3}, {128, 6}};
-constexpr int kNumF32Shapes = sizeof(kF32Shapes) / sizeof(kF32Shapes[0]);
+// shapes kNumBase .. 2 kNumBase - 1 are the same with dynamic model scheduling
+constexpr int kNumBase = sizeof(kF32Shapes) / sizeof(kF32Shapes[0]);
+constexpr int kNumF32Shapes = 2 * kNumBase;
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool DYN>
 int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
                  cudaStream_t stream) {
     const SystemTables &h = sys->host;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS, NT / 32);
-    auto kern = forward_f32_kernel<NT, MINB>;
+    auto kern = forward_f32_kernel<NT, MINB, DYN>;
     if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the kernel reads its tables from shared memory only: give the SM's
     // unified L1/shared storage to shared memory so more CTAs stay resident
@@ -708,23 +717,40 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     if (per_sm < 1) return fail(AEM_ERR_UNSUPPORTED, "forward kernel: launch shape does not fit on an SM");
     long long grid = (long long)sys->num_sms * per_sm;
     if (grid > mv.n) grid = mv.n;
+    int *counter = nullptr;
+    if (DYN) {  // stream-ordered: one counter per launch, so launches on other streams never share it
+        AEM_CUDA_TRY(cudaMallocAsync((void **)&counter, sizeof(int), stream));
+        AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
+    }
     kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
                                                sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
-                                               ll);
-    AEM_CUDA_TRY(cudaGetLastError());
+                                               ll, counter);
+    const cudaError_t e = cudaGetLastError();
+    if (DYN) cudaFreeAsync(counter, stream);
+    AEM_CUDA_TRY(e);
     return AEM_OK;
 }
 
 int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
                        float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
                        cudaStream_t stream) {
+#define AEM_SHAPE(I, NT, MINB, DYN) \
+    case I:                         \
+        return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
     switch (idx) {
-        case 1: return launch_shape<128, 8>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
-        case 2: return launch_shape<512, 2>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
-        case 3: return launch_shape<256, 3>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
-        case 4: return launch_shape<128, 6>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
-        default: return launch_shape<256, 4>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        AEM_SHAPE(1, 128, 8, false)
+        AEM_SHAPE(2, 512, 2, false)
+        AEM_SHAPE(3, 256, 3, false)
+        AEM_SHAPE(4, 128, 6, false)
+        AEM_SHAPE(5, 256, 4, true)
+        AEM_SHAPE(6, 128, 8, true)
+        AEM_SHAPE(7, 512, 2, true)
+        AEM_SHAPE(8, 256, 3, true)
+        AEM_SHAPE(9, 128, 6, true)
+        default:
+            return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
     }
+#undef AEM_SHAPE
 }
 
 template <class Models>
