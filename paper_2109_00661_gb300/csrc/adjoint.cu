@@ -3,11 +3,11 @@
 // differentiation of the forward model (Section 2: Cole-Cole conductivity,
 // TE recursion, Hankel sum; Section 2.3.2: gate transform and likelihood).
 //
-// One CTA per model (grid-stride).  Pass 1 evaluates the spectrum Im H(w_f)
-// exactly as the forward model does; the epilogue forms the gates, the
-// log-likelihood and the adjoint seeds
-//   a_f = sum_g T[g,f] dl/dyhat_g,  dl/dyhat = r/v + (e_mn^2 yhat / v)(r^2/v - 1).
-// Pass 2 revisits every (frequency, abscissa) item with weight a_f w_k: the
+// The FP32 forward kernel (forward.cu) first writes every model's gates and
+// log-likelihood.  Then one CTA per model (models claimed from a counter)
+// forms the adjoint seeds from those gates,
+//   a_f = sum_g T[g,f] dl/dyhat_g,  dl/dyhat = r/v + (e_mn^2 yhat / v)(r^2/v - 1),
+// and visits every (frequency, abscissa) item with weight a_f w_k: the
 // recursion is run bottom-up storing the reflection coefficients Gamma_j, then
 // top-down propagating dGamma_0/dGamma_j through the Moebius steps
 //   Gamma_j = (rho_j + Gamma_{j+1} E_j) / (1 + rho_j Gamma_{j+1} E_j),
@@ -70,7 +70,7 @@ struct GradModels {
 
 // Shared memory (dynamic): S[F*LS] (float2 s), DS[F*LS*4] (float2 ds/dp for
 // log10 sigma, m, log10 tau, c), lamhw[K] (float2 {lambda, weight}),
-// imh_w[kGW*F], imh[F], af[F], T[G*F], part[kGW * LS * kNP] (float).
+// af[F], T[G*F], part[kGW * LS * kNP] (float).
 __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS,
                                                           const float *__restrict__ g_omega,
                                                           const float *__restrict__ g_lam,
@@ -78,20 +78,18 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                                                           const float *__restrict__ g_T,
                                                           const double *__restrict__ y_obs, int obs_per,
                                                           const double *__restrict__ eps_an, double eps_mn,
-                                                          double *__restrict__ ll_out, float *__restrict__ grad) {
+                                                          const float *__restrict__ g_gates, float *__restrict__ grad,
+                                                          int *__restrict__ work_counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *S = reinterpret_cast<float2 *>(smem_raw);
     float2 *DS = S + (size_t)F * LS;
     float2 *lamhw = DS + (size_t)F * LS * 4;
-    float *imh_w = reinterpret_cast<float *>(lamhw + K);
-    float *imh = imh_w + (size_t)kGW * F;
-    float *af = imh + F;
+    float *af = reinterpret_cast<float *>(lamhw + K);
     float *Ts = af + F;
     float *part = Ts + (size_t)G * F;
     __shared__ float thick[AEM_MAX_LAYERS];
     __shared__ float sig_s[AEM_MAX_LAYERS], m_s[AEM_MAX_LAYERS], tau_s[AEM_MAX_LAYERS], c_s[AEM_MAX_LAYERS];
     __shared__ double dldy[AEM_MAX_GATES];
-    __shared__ double ll_part[kGW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float mu0 = (float)kMu0, ln10 = 2.302585092994046f;
@@ -99,9 +97,13 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
     for (int k = tid; k < K; k += blockDim.x) lamhw[k] = make_float2(g_lam[k], g_hw[k]);
     const int FK = F * K;
 
-    for (int p = blockIdx.x; p < mv.n; p += gridDim.x) {
+    // models are claimed from a counter as CTAs finish them (model costs vary
+    // with the layer count, so a fixed stride would leave SMs idle at the end)
+    __shared__ int next_model;
+    for (int p = blockIdx.x; p < mv.n; p = next_model) {
         const int L = mv.nlayers[p];
         __syncthreads();
+        if (tid == 0) next_model = (int)gridDim.x + atomicAdd(work_counter, 1);
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             sig_s[tid] = exp10f(mv.logsig[o]);
@@ -110,7 +112,6 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
             tau_s[tid] = exp10f(mv.logtau[o]);
             c_s[tid] = mv.c[o];
         }
-        for (int i = tid; i < kGW * F; i += blockDim.x) imh_w[i] = 0.f;
         __syncthreads();
         // Cole-Cole (paper form) and its derivatives, per (frequency, layer):
         // sig = s_inf (1 - m / (1 + x)), x = (w tau)^c e^{i pi c / 2}, s = i w mu0 sig
@@ -140,79 +141,15 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         }
         __syncthreads();
 
-        // ---- pass 1: spectrum
-        int f = tid / K, k = tid - (tid / K) * K;
-        for (int base = 0; base < FK; base += blockDim.x) {
-            const int item = base + tid;
-            float val = 0.f;
-            int fl = -1;
-            if (item < FK) {
-                fl = f;
-                const float2 lh = lamhw[k];
-                const float lam = lh.x, lam2 = lam * lam;
-                const float2 *Sf = S + (size_t)f * LS;
-                float2 sb = Sf[L - 1];
-                float2 ub = csqrt_up(lam2 + sb.x, sb.y);
-                float2 G = make_float2(0.f, 0.f);
-                for (int j = L - 1; j >= 0; --j) {
-                    const float2 sa = j > 0 ? Sf[j - 1] : make_float2(0.f, 0.f);
-                    const float2 ua = j > 0 ? csqrt_up(lam2 + sa.x, sa.y) : make_float2(lam, 0.f);
-                    const float2 q = cadd(ua, ub);
-                    const float2 rho = cmul(csub(sa, Sf[j]), crcp(cmul(q, q)));
-                    if (j == L - 1) {
-                        G = rho;
-                    } else {
-                        const float2 E = cexpf2(cscale(ub, -2.f * thick[j]));
-                        const float2 b = cmul(G, E);
-                        G = cmul(cadd(rho, b), crcp(cadd(make_float2(1.f, 0.f), cmul(rho, b))));
-                    }
-                    ub = ua;
-                }
-                val = lh.y * G.y;
-            }
-            unsigned pending = __ballot_sync(kMask, fl >= 0);
-            while (pending) {
-                const int leader = __ffs(pending) - 1;
-                const int fsel = __shfl_sync(kMask, fl, leader);
-                const float s = wsum<float>(fl == fsel ? val : 0.f);
-                if (lane == leader) imh_w[warp * F + fsel] += s;
-                pending &= ~__ballot_sync(kMask, fl == fsel);
-            }
-            k += blockDim.x;
-            while (k >= K) {
-                k -= K;
-                ++f;
-            }
-        }
-        __syncthreads();
-        for (int j = tid; j < F; j += blockDim.x) {
-            float a = 0.f;
-            for (int w = 0; w < kGW; ++w) a += imh_w[w * F + j];
-            imh[j] = a;
-        }
-        __syncthreads();
-        // ---- gates, log-likelihood, dl/dyhat
-        double term = 0.0;
+        // ---- dl/dyhat from the forward kernel's gates of this model
         if (tid < G) {
-            float acc = 0.f;
-            for (int j = 0; j < F; ++j) acc = fmaf(Ts[tid * F + j], imh[j], acc);
-            const double yh = (double)acc;
+            const double yh = (double)g_gates[(size_t)p * G + tid];
             const double ea = eps_an[tid];
             const double v = ea * ea + (eps_mn * yh) * (eps_mn * yh);
             const double r = y_obs[(size_t)(p / obs_per) * G + tid] - yh;
-            term = r * r / v + log(2.0 * kPi * v);
             dldy[tid] = r / v + (eps_mn * eps_mn * yh / v) * (r * r / v - 1.0);
         }
-        if (warp * 32 < G) {
-            const double t = wsum<double>(term);
-            if (lane == 0) ll_part[warp] = t;
-        }
         __syncthreads();
-        if (tid == 0) {
-            double acc = 0.0;
-            for (int w = 0; w * 32 < G; ++w) acc += ll_part[w];
-            if (ll_out) ll_out[p] = -0.5 * acc;
-        }
         for (int j = tid; j < F; j += blockDim.x) {
             double a = 0.0;
             for (int g = 0; g < G; ++g) a += (double)Ts[g * F + j] * dldy[g];
@@ -224,8 +161,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         float acc[AEM_MAX_LAYERS * kNP];
         for (int v = 0; v < L * kNP; ++v) acc[v] = 0.f;
         float2 Gam[AEM_MAX_LAYERS];
-        f = tid / K;
-        k = tid - (tid / K) * K;
+        int f = tid / K, k = tid - (tid / K) * K;
         for (int item = tid; item < FK; item += blockDim.x) {
             const float2 lh = lamhw[k];
             const float wgt = af[f] * lh.y;
@@ -343,8 +279,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
         return fail(AEM_ERR_UNSUPPORTED, "aem_loglik_grad_f32: only the paper's Cole-Cole form is differentiated");
     const int LS = models->lmax;
     const size_t smem = sizeof(float2) * ((size_t)h.F * LS * 5 + h.K) +
-                        sizeof(float) * ((size_t)kGW * h.F + 2 * (size_t)h.F + (size_t)h.G * h.F +
-                                         (size_t)kGW * LS * kNP);
+                        sizeof(float) * ((size_t)h.F + (size_t)h.G * h.F + (size_t)kGW * LS * kNP);
     auto kern = loglik_grad_kernel;
     if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -354,9 +289,26 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     if (grid > models->n_models) grid = models->n_models;
     GradModels gm{models->n_models, models->lmax, models->nlayers, models->logsig, models->logh,
                   models->m, models->logtau, models->c};
-    kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, sys->d_omega_f, sys->d_lam_f, sys->d_hw_f,
-                                                sys->d_T_f, y_obs, models_per_sounding, eps_an, eps_mn, ll, grad);
-    AEM_CUDA_TRY(cudaGetLastError());
+    // stream-ordered scratch: the model count for the claim counter, then the gates
+    void *work = nullptr;
+    const size_t gate_off = 256;
+    AEM_CUDA_TRY(cudaMallocAsync(&work, gate_off + sizeof(float) * (size_t)models->n_models * h.G, stream));
+    int *counter = static_cast<int *>(work);
+    float *gates = reinterpret_cast<float *>(static_cast<char *>(work) + gate_off);
+    int rc = loglik_gates_f32_soundings(sys, models, y_obs, models_per_sounding, eps_an, eps_mn, ll, gates, stream);
+    cudaError_t e = cudaSuccess;
+    if (rc == AEM_OK) {
+        e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+        if (e == cudaSuccess) {
+            kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, sys->d_omega_f, sys->d_lam_f,
+                                                        sys->d_hw_f, sys->d_T_f, y_obs, models_per_sounding, eps_an,
+                                                        eps_mn, gates, grad, counter);
+            e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(work, stream);
+    if (rc) return rc;
+    AEM_CUDA_TRY(e);
     return AEM_OK;
 }
 

@@ -60,6 +60,11 @@ int build_tables(const aem_system_desc *desc, SystemTables *out);
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
                          cudaStream_t stream);
+// Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
+// with per-sounding rows of y_obs (forward.cu).
+int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *gates,
+                               cudaStream_t stream);
 // Log-likelihood and its merged-layer gradient [P][lmax][5] with the same
 // per-sounding rows of y_obs (adjoint.cu).
 int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,

@@ -811,6 +811,17 @@ extern "C" int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *model
                                    sys ? sys->d_hw_d : nullptr, sys ? sys->d_T_d : nullptr, "aem_loglik_f64");
 }
 
+namespace aem {
+// Gates and log-likelihood of the FP32 forward model for the adjoint, with the
+// per-sounding rows of y_obs (ll may be NULL).
+int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
+                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *gates,
+                               cudaStream_t stream) {
+    return launch_forward_f32(sys, models, gates, nullptr, y_obs, models_per_sounding, eps_an, eps_mn, ll, stream,
+                              "aem_loglik_grad_f32");
+}
+}  // namespace aem
+
 extern "C" int aem_autotune_forward(aem_system *sys, const aem_models_f32 *sample, int repeats, void *stream,
                                     int *shape_out, float *ms_out) {
     if (!sys || !sample) return fail(AEM_ERR_INVALID_ARG, "aem_autotune_forward: NULL system or sample");
