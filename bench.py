@@ -534,7 +534,13 @@ def main():
                        "forward_launch_shape": {"index": shape, "sample_ms_per_shape": shape_ms},
                        "l2": "inputs larger than L2 (210 MB of model parameters per step)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         # DRAM bytes of one launch from the ncu capture of the
+                         # dynamic-scheduled 256 x 4 shape (profiles/forward_f32_kernel_
+                         # forward-g30-f60-k200.md: 13,221,632 B for 65,536 models), scaled
+                         # by the model count; null when the autotuner picks another shape
+                         "traffic": (13221632.0 / 65536 * P) if shape == 5 else None,
+                         "traffic_unit": "bytes per launch",
                          "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
                          "mufu_frac": mufu_frac, "layer_steps_per_s": steps_work / (ms * 1e-3)},
             "gpu_launches": args.steps,
