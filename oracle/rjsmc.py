@@ -135,6 +135,7 @@ class SMCSettings:
     pca_target: float = 0.44    # acceptance rate the scale bisection aims at (Section 3.2)
     pca_bisect_iters: int = 6   # bisection steps on trial proposals per stage
     pca_ridge: float = 0.01     # ridge on the fitted covariance, as a fraction of the random-walk scales
+    recycle: int = 0            # > 0: fit the adaptive proposal on the last `recycle` stages' particles (Section 3.2)
 
     @property
     def n_models(self):
@@ -636,6 +637,9 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
     p_min = 0.0
     h_lang = s.langevin_h
     pca_scale = {}
+    history = [(0, [p.copy() for p in parts], ll.copy())] if s.recycle > 0 else []
+    gamma_hist = [0.0]
+    logz_hist = [np.zeros(s.n_models)]
     for stage in range(1, max_stages + 1):
         model = np.array([p.model(s) for p in parts])
         dg, done, inc, W = reweight(ll, model, s.n_models, gamma, s.alpha, s.bisect_iters)
@@ -645,10 +649,15 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
         anc = resample_systematic(W, model, s.n_models, resample_uniforms(s, stage))
         parts = [parts[a].copy() for a in anc]
         ll = ll[anc].copy()
+        gamma_hist.append(gamma)
+        logz_hist.append(log_z.copy())
+        if s.recycle > 0:
+            history = (history + [(stage, [p.copy() for p in parts], ll.copy())])[-s.recycle:]
         R = s.n_sweeps if s.n_sweeps > 0 else (s.r_max if stage == 1 else sweeps_needed(p_min, s.c_mut, s.r_max))
         res.sweeps.append(R)
         if s.adaptive:
-            fits = fit_model_gaussians(parts, s)
+            fits = (fit_model_gaussians_recycled(history, s, stage, gamma_hist, logz_hist) if s.recycle > 0
+                    else fit_model_gaussians(parts, s))
             pca_scale = pca_bisect_scales(parts, ll, fits, s, stage, gamma, loglik, pca_scale)
             res.pca_scales.append(dict(pca_scale))
             proposer = (lambda p_, s_, i_, st_, sw_: propose_adaptive(p_, s_, i_, st_, sw_, fits, pca_scale))
@@ -785,6 +794,54 @@ def pca_bisect_scales(parts, ll, fits, s: SMCSettings, stage: int, gamma: float,
             else:
                 hi[k] = mid[k]
     return {k: math.exp(0.5 * (lo[k] + hi[k])) for k in fits}
+
+
+def recycle_log_weights(ll, gammas, log_z_k, t):
+    """Deterministic-mixture weights of recycled particles for model k at
+    stage t (Section 3.2, "Overcoming particle impoverishment"):
+      log nu = gamma_t l - log( (1/(t+1)) sum_{l=0}^{t} exp(gamma_l l - log Z_{l,k}) ),
+    the prior cancelling between numerator and denominator.  The printed
+    normaliser 1/t over t + 1 terms is read as 1/(t+1).  ll: log-likelihoods
+    of the particles (from any stage s <= t); gammas[l], log_z_k[l] for l = 0..t."""
+    ll = np.asarray(ll, dtype=np.float64)[:, None]
+    g = np.asarray(gammas[:t + 1], dtype=np.float64)[None, :]
+    lz = np.asarray(log_z_k[:t + 1], dtype=np.float64)[None, :]
+    a = g * ll - lz
+    m = a.max(axis=1, keepdims=True)
+    lden = m[:, 0] + np.log(np.exp(a - m).sum(axis=1)) - math.log(t + 1)
+    return g[0, -1] * ll[:, 0] - lden
+
+
+def fit_model_gaussians_recycled(history, s: SMCSettings, t: int, gammas, log_z):
+    """As fit_model_gaussians, on the particles of every stored stage (history:
+    list of (stage, particles, ll), the last `recycle` stages up to t) with the
+    normalised recycling weights of recycle_log_weights per model; a model is
+    fitted when its current stage holds at least two particles."""
+    out = {}
+    cur = history[-1][1]
+    counts = {}
+    for p in cur:
+        counts[p.model(s)] = counts.get(p.model(s), 0) + 1
+    for k, n in counts.items():
+        if n < 2:
+            continue
+        th, ll = [], []
+        for _, parts, lls in history:
+            for p, l in zip(parts, lls):
+                if p.model(s) == k:
+                    th.append(theta_of(p, s))
+                    ll.append(l)
+        lw = recycle_log_weights(ll, gammas, [z[k] for z in log_z], t)
+        w = np.exp(lw - lw.max())
+        w /= w.sum()
+        X = np.array(th)
+        mu = w @ X
+        C = (X - mu).T @ ((X - mu) * w[:, None])
+        sc = theta_scales(next(p for p in cur if p.model(s) == k), s)
+        C = C + np.diag((s.pca_ridge * sc) ** 2)
+        lam, U = np.linalg.eigh(C)
+        out[k] = (mu, U, np.maximum(lam, 0.0))
+    return out
 
 
 def propose_adaptive(p: Particle, s: SMCSettings, i: int, stage: int, sweep: int, fits, scales):

@@ -283,3 +283,48 @@ def test_adaptive_rj_toy_model_probabilities():
         freq.append(res.counts / res.counts.sum())
     freq = np.mean(freq, axis=0)
     assert np.all(np.abs(freq - post) < 0.05), (freq, post)
+
+
+def test_recycling_weights_recover_the_current_target():
+    """Particles drawn exactly from every tempered target pi_l of a 1-D
+    Gaussian toy (uniform prior on (-50, 50), likelihood N(1; theta, 1)),
+    weighted by the deterministic-mixture recycling weights with the exact
+    normalising constants Z_l, reproduce the mean and variance of the current
+    target pi_t = N(1, 1); leaving Z_l out of the weights biases them.  (The
+    normaliser 1/t or 1/(t+1) is a common factor and cancels after
+    normalisation.)"""
+    rng = np.random.default_rng(11)
+    gammas = [0.0, 0.01, 0.05, 0.2, 1.0]
+    t = len(gammas) - 1
+    lo, hi = -50.0, 50.0
+    log_z = [0.0] + [-0.5 * g * math.log(2 * math.pi) + 0.5 * math.log(2 * math.pi / g) - math.log(hi - lo)
+                     for g in gammas[1:]]
+    th = [rng.uniform(lo, hi, 20000)] + [1.0 + rng.standard_normal(20000) / math.sqrt(g) for g in gammas[1:]]
+    th = np.concatenate(th)
+    ll = -0.5 * (th - 1.0) ** 2 - 0.5 * math.log(2 * math.pi)
+
+    def moments(lz):
+        lw = R.recycle_log_weights(ll, gammas, lz, t)
+        w = np.exp(lw - lw.max())
+        w /= w.sum()
+        mu = w @ th
+        return mu, w @ (th - mu) ** 2
+
+    mu, var = moments(log_z)
+    assert abs(mu - 1.0) < 0.02 and abs(var - 1.0) < 0.03, (mu, var)
+    mu0, var0 = moments([0.0] * len(gammas))
+    assert abs(var0 - 1.0) > 0.1, var0
+
+
+@pytest.mark.slow
+def test_recycling_smc_evidence_on_toy_with_closed_form():
+    est = []
+    for seed in range(8):
+        s = R.SMCSettings(n_particles=200, kappa_max=0, lambda_max=0, n_sweeps=5, adaptive=True, recycle=8,
+                          seed=seed)
+        res = R.run(s, toy_evidence_loglik)
+        assert res.gammas[-1] == 1.0
+        est.append(res.log_z[0])
+    est = np.array(est)
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - toy_log_z()) < 3 * se + 0.02
