@@ -244,6 +244,7 @@ typedef struct {
     double pca_target;                     /* its target acceptance rate (0.44) */
     int pca_bisect_iters;                  /* bisection steps on trial proposals per stage (1..60) */
     double pca_ridge;                      /* covariance ridge, fraction of the random-walk steps (>= 0) */
+    int recycle_stages;                    /* 0..32; > 0 (with adaptive): particle recycling over that many stages */
 } smc_desc;
 
 typedef struct smc_state smc_state;
@@ -261,7 +262,7 @@ typedef struct {
 /* Fills *d with the defaults (N = 256, kappa_max = 3, lambda_max = 4,
  * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2),
  * no Langevin sweeps, langevin_h = 0.1, langevin_adapt = 1, adaptive = 0,
- * pca_target = 0.44, pca_bisect_iters = 6, pca_ridge = 0.01). */
+ * pca_target = 0.44, pca_bisect_iters = 6, pca_ridge = 0.01, recycle_stages = 0). */
 int smc_desc_defaults(smc_desc *d);
 
 /* Synchronous.  y_obs [host, S x G] observed gates per sounding; eps_an [host, G];
@@ -376,7 +377,16 @@ int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *
  * normal, the same draws at every step), comparing the model's mean
  * min(1, (L'/L)^gamma) with desc.pca_target.  The perturb move of smc_mutate
  * then steps along U_r with standard deviation a_k sqrt(Lambda_r); models
- * without a fit keep the fixed-scale component-wise walk. */
+ * without a fit keep the fixed-scale component-wise walk.
+ * With desc.recycle_stages = H > 0 the fit recycles particles (Section 3.2,
+ * particle impoverishment): mu_k and Sigma_k are weighted over the model's
+ * particles of the last H post-resample populations (stage 0 = the prior
+ * draw), particle i from any stage carrying
+ *   log nu = gamma_t l_i - log( (1/(t+1)) sum_{l=0}^{t} exp(gamma_l l_i - log Z_{l,k}) )
+ * over every stage's gamma and log Z (at most 1024 stages); a model is
+ * fitted when its current population holds at least two particles.  The
+ * history takes H x P particle records of device memory and is not part of a
+ * checkpoint (smc_checkpoint returns AEM_ERR_UNSUPPORTED while recycling). */
 int smc_adapt(smc_state *st);
 /* Synchronous copies of the fitted proposal, D = 3 + 2 kappa_max + 2 lambda_max:
  * mu [S][M][D], U [S][M][D][D] (row j, column r = direction r), lam [S][M][D],

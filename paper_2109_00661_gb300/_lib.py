@@ -74,6 +74,7 @@ class SMCDesc(ctypes.Structure):
         ("pca_target", c_double),
         ("pca_bisect_iters", c_int),
         ("pca_ridge", c_double),
+        ("recycle_stages", c_int),
     ]
 
 

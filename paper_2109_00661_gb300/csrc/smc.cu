@@ -815,6 +815,50 @@ __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int l
 constexpr int kFitThreads = 128;
 constexpr int kJacobiSweeps = 30;
 
+// Cyclic Jacobi rotations on the symmetric d x d matrix A (row stride DM) in
+// place, accumulating the rotations in V: on return A's diagonal holds the
+// eigenvalues and V's columns the eigenvectors.  At most kJacobiSweeps sweeps;
+// stops when the off-diagonal mass falls below 1e-30 of the diagonal's.
+__device__ void jacobi_eigen(double *A, double *V, int d, int DM) {
+    double scale2 = 0.0;
+    for (int j = 0; j < d; ++j) scale2 += A[j * DM + j] * A[j * DM + j];
+    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+        double offn = 0.0;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) offn += A[p * DM + q] * A[p * DM + q];
+        if (offn <= 1e-30 * scale2) break;
+        for (int p = 0; p < d; ++p) {
+            for (int q = p + 1; q < d; ++q) {
+                const double apq = A[p * DM + q];
+                if (apq == 0.0) continue;
+                // rotation that zeroes A[p][q]: t = tan(phi) is the smaller root of
+                // t^2 + 2 t th - 1 = 0 with th = (A_qq - A_pp) / (2 A_pq)
+                const double th = (A[q * DM + q] - A[p * DM + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < d; ++r) {
+                    if (r == p || r == q) continue;
+                    const double arp = A[r * DM + p], arq = A[r * DM + q];
+                    const double np_ = c * arp - sn * arq, nq_ = sn * arp + c * arq;
+                    A[r * DM + p] = np_;
+                    A[p * DM + r] = np_;
+                    A[r * DM + q] = nq_;
+                    A[q * DM + r] = nq_;
+                }
+                A[p * DM + p] -= t * apq;
+                A[q * DM + q] += t * apq;
+                A[p * DM + q] = 0.0;
+                A[q * DM + p] = 0.0;
+                for (int r = 0; r < d; ++r) {
+                    const double vrp = V[r * DM + p], vrq = V[r * DM + q];
+                    V[r * DM + p] = c * vrp - sn * vrq;
+                    V[r * DM + q] = sn * vrp + c * vrq;
+                }
+            }
+        }
+    }
+}
+
 // One CTA per (sounding, model): mean and (biased) covariance of theta over
 // the model's particles in FP64 with fixed-order sums, plus
 // (ridge * step_j)^2 on the diagonal, then cyclic Jacobi rotations (thread 0,
@@ -868,45 +912,7 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const i
         V[j * DM + l] = j == l ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (tid == 0) {
-        double scale2 = 0.0;
-        for (int j = 0; j < d; ++j) scale2 += A[j * DM + j] * A[j * DM + j];
-        for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-            double offn = 0.0;
-            for (int p = 0; p < d; ++p)
-                for (int q = p + 1; q < d; ++q) offn += A[p * DM + q] * A[p * DM + q];
-            if (offn <= 1e-30 * scale2) break;
-            for (int p = 0; p < d; ++p) {
-                for (int q = p + 1; q < d; ++q) {
-                    const double apq = A[p * DM + q];
-                    if (apq == 0.0) continue;
-                    // rotation that zeroes A[p][q]: t = tan(phi) is the smaller root of
-                    // t^2 + 2 t th - 1 = 0 with th = (A_qq - A_pp) / (2 A_pq)
-                    const double th = (A[q * DM + q] - A[p * DM + p]) / (2.0 * apq);
-                    const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-                    for (int r = 0; r < d; ++r) {
-                        if (r == p || r == q) continue;
-                        const double arp = A[r * DM + p], arq = A[r * DM + q];
-                        const double np_ = c * arp - sn * arq, nq_ = sn * arp + c * arq;
-                        A[r * DM + p] = np_;
-                        A[p * DM + r] = np_;
-                        A[r * DM + q] = nq_;
-                        A[q * DM + r] = nq_;
-                    }
-                    A[p * DM + p] -= t * apq;
-                    A[q * DM + q] += t * apq;
-                    A[p * DM + q] = 0.0;
-                    A[q * DM + p] = 0.0;
-                    for (int r = 0; r < d; ++r) {
-                        const double vrp = V[r * DM + p], vrq = V[r * DM + q];
-                        V[r * DM + p] = c * vrp - sn * vrq;
-                        V[r * DM + q] = sn * vrp + c * vrq;
-                    }
-                }
-            }
-        }
-    }
+    if (tid == 0) jacobi_eigen(A, V, d, DM);
     __syncthreads();
     for (int e = tid; e < d * d; e += blockDim.x) {
         const int j = e / d, l = e - (e / d) * d;
@@ -918,6 +924,148 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const i
         lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
     }
     if (tid == 0) ok_out[b] = 1;
+}
+
+// ----------------------------------------------------- particle recycling
+// Section 3.2 ("Overcoming particle impoverishment"): the fit of each model's
+// proposal uses the particles of the last H stages, each weighted by the
+// deterministic-mixture weight
+//   log nu = gamma_t l - log( (1/(t+1)) sum_{l=0}^{t} exp(gamma_l l - log Z_{l,k}) )
+// (the prior cancels; the printed 1/t over t + 1 terms read as 1/(t+1)).
+constexpr int kMaxRecycleStages = 1024;  // stages whose gamma and log Z are kept
+
+__global__ void recycle_weight_kernel(PState hist, int P, int n_used, int N, int M, int lp1, int t,
+                                      const double *gamma_hist, const double *logz_hist, double *lognu) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n_used * P) return;
+    const int i = (int)(idx % (size_t)P), s = i / N;
+    const int k = hist.kappa[idx] * lp1 + hist.lam[idx];
+    const double l = hist.ll[idx];
+    const double *g = gamma_hist + (size_t)s * kMaxRecycleStages;
+    const double *lz = logz_hist + (size_t)s * kMaxRecycleStages * M + k;
+    double m = -INFINITY;
+    for (int q = 0; q <= t; ++q) m = fmax(m, g[q] * l - lz[(size_t)q * M]);
+    double acc = 0.0;
+    for (int q = 0; q <= t; ++q) acc += exp(g[q] * l - lz[(size_t)q * M] - m);
+    lognu[idx] = g[t] * l - (m + log(acc) - log((double)(t + 1)));
+}
+
+__device__ inline double block_reduce_128(double v, double *red, bool take_max) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            red[threadIdx.x] = take_max ? fmax(red[threadIdx.x], red[threadIdx.x + w]) : red[threadIdx.x] + red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// One CTA (128 threads) per (sounding, model) with at least two current
+// particles: normalised recycling weights over the model's stored particles
+// (written to wbuf), the weighted mean and covariance of theta in FP64 with
+// fixed-order sums, the ridge, then the same Jacobi decomposition as the
+// plain fit.
+__global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState hist, const double *lognu, double *wbuf,
+                                                                      int n_used, int P, const int *counts, Params pr,
+                                                                      double ridge, double *mu_out, double *U_out,
+                                                                      double *lam_out, int *ok_out, double *a_out) {
+    extern __shared__ double sm_fit[];
+    __shared__ double red[kFitThreads];
+    const int DM = pr.DM;
+    double *A = sm_fit, *V = A + DM * DM, *mu = V + DM * DM;
+    const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
+    const int lp1 = pr.lambda_max + 1, kappa = k / lp1, lam = k - kappa * lp1;
+    const int d = 3 + 2 * kappa + 2 * lam;
+    const int tid = threadIdx.x;
+    if (counts[b] < 2) {
+        if (tid == 0) {
+            ok_out[b] = 0;
+            a_out[b] = 1.0;
+        }
+        return;
+    }
+    const int C = n_used * pr.N;  // candidates: every stored particle of this sounding
+    auto cand = [&](int c) -> size_t { return (size_t)(c / pr.N) * P + (size_t)s * pr.N + (c % pr.N); };
+    auto member = [&](size_t idx) { return hist.kappa[idx] == kappa && hist.lam[idx] == lam; };
+    double m = -INFINITY;
+    for (int c = tid; c < C; c += blockDim.x) {
+        const size_t idx = cand(c);
+        if (member(idx)) m = fmax(m, lognu[idx]);
+    }
+    m = block_reduce_128(m, red, true);
+    double sw = 0.0;
+    for (int c = tid; c < C; c += blockDim.x) {
+        const size_t idx = cand(c);
+        if (member(idx)) {
+            const double w = exp(lognu[idx] - m);
+            wbuf[idx] = w;
+            sw += w;
+        }
+    }
+    sw = block_reduce_128(sw, red, false);  // also orders the wbuf writes before the reads below
+    for (int j = tid; j < d; j += blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < C; ++c) {
+            const size_t idx = cand(c);
+            if (member(idx)) acc += wbuf[idx] * theta_value(theta_ref(hist, (int)idx, j, kappa, lam, pr), pr);
+        }
+        mu[j] = acc / sw;
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        if (l < j) continue;
+        double acc = 0.0;
+        for (int c = 0; c < C; ++c) {
+            const size_t idx = cand(c);
+            if (!member(idx)) continue;
+            acc += wbuf[idx] * (theta_value(theta_ref(hist, (int)idx, j, kappa, lam, pr), pr) - mu[j]) *
+                   (theta_value(theta_ref(hist, (int)idx, l, kappa, lam, pr), pr) - mu[l]);
+        }
+        double cv = acc / sw;
+        if (j == l) {
+            const double sj = ridge * theta_ref(hist, 0, j, kappa, lam, pr).scale;
+            cv += sj * sj;
+        }
+        A[j * DM + l] = cv;
+        A[l * DM + j] = cv;
+    }
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        V[j * DM + l] = j == l ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) jacobi_eigen(A, V, d, DM);
+    __syncthreads();
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int j = e / d, l = e - (e / d) * d;
+        U_out[(size_t)b * DM * DM + (size_t)j * DM + l] = V[j * DM + l];
+    }
+    for (int j = tid; j < d; j += blockDim.x) {
+        mu_out[(size_t)b * DM + j] = mu[j];
+        const double lj = A[j * DM + j];
+        lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
+    }
+    if (tid == 0) ok_out[b] = 1;
+}
+
+// Stores the current particles as history slot `slot` and this stage's gamma
+// and log Z (per sounding) at row t.
+__global__ void record_slot_kernel(PState hist, PState cur, int P, int slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) copy_particle(hist, slot * P + i, cur, i);
+}
+
+__global__ void record_stage_kernel(const double *gamma, const double *logz, int S, int M, int t, double *gamma_hist,
+                                    double *logz_hist) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    gamma_hist[(size_t)s * kMaxRecycleStages + t] = gamma[s];
+    for (int k = 0; k < M; ++k)
+        logz_hist[((size_t)s * kMaxRecycleStages + t) * M + k] = logz[(size_t)s * M + k];
 }
 
 // Trial proposals of the scale bisection: every particle of a fitted model
@@ -1107,6 +1255,11 @@ struct smc_state {
     double *pca_mu = nullptr, *pca_U = nullptr, *pca_lam = nullptr, *pca_a = nullptr, *pca_lo = nullptr,
            *pca_hi = nullptr;
     int *pca_ok = nullptr;
+    // particle recycling: the last H post-resample populations ([H * P] in
+    // every particle array, slot = stage mod H), their log nu and weights, and
+    // every stage's gamma [S][1024] and log Z [S][1024][M]
+    PState hist{};
+    double *hist_lognu = nullptr, *hist_w = nullptr, *gamma_hist = nullptr, *logz_hist = nullptr;
     double *ppd_out = nullptr;   // [3][S][G]
     double *lq = nullptr, *lang_h = nullptr;
     int *lacc = nullptr, *lprop = nullptr;
@@ -1127,8 +1280,8 @@ int dalloc(smc_state *st, T **p, size_t n) {
     return AEM_OK;
 }
 
-int alloc_pstate(smc_state *st, PState *ps) {
-    const size_t P = st->P;
+int alloc_pstate(smc_state *st, PState *ps, size_t count = 0) {
+    const size_t P = count ? count : (size_t)st->P;
     int rc;
     if ((rc = dalloc(st, &ps->kappa, P)) || (rc = dalloc(st, &ps->lam, P)) || (rc = dalloc(st, &ps->phib, P)) ||
         (rc = dalloc(st, &ps->tau, P)) || (rc = dalloc(st, &ps->c, P)) || (rc = dalloc(st, &ps->zc, P * KS)) ||
@@ -1181,6 +1334,8 @@ int check_desc(const smc_desc *d) {
     if (d->adaptive && (!(d->pca_target > 0 && d->pca_target < 1) || d->pca_bisect_iters < 1 ||
                         d->pca_bisect_iters > 60 || !(d->pca_ridge >= 0)))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid pca_target / pca_bisect_iters / pca_ridge");
+    if (d->recycle_stages < 0 || d->recycle_stages > 32 || (d->recycle_stages > 0 && !d->adaptive))
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: recycle_stages outside 0..32, or set without adaptive");
     if (d->n_langevin < 0 || d->n_langevin > 1000 || !(d->langevin_h > 0))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: n_langevin outside 0..1000 or langevin_h <= 0");
     return AEM_OK;
@@ -1218,6 +1373,7 @@ extern "C" int smc_desc_defaults(smc_desc *d) {
     d->pca_target = 0.44;
     d->pca_bisect_iters = 6;
     d->pca_ridge = 0.01;
+    d->recycle_stages = 0;
     return AEM_OK;
 }
 
@@ -1295,6 +1451,20 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         e = cudaMemcpy(st->pca_a, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemset(st->pca_ok, 0, sizeof(int) * st->S * st->M);
+    if (e == cudaSuccess && desc->recycle_stages > 0) {
+        const size_t HP = (size_t)desc->recycle_stages * st->P;
+        if (HP * KS >= ((size_t)1 << 31)) {
+            smc_destroy(st);
+            return fail(AEM_ERR_INVALID_ARG, "smc_create: recycle_stages x particles too large for the history");
+        }
+        if ((rc = alloc_pstate(st, &st->hist, HP)) || (rc = dalloc(st, &st->hist_lognu, HP)) ||
+            (rc = dalloc(st, &st->hist_w, HP)) ||
+            (rc = dalloc(st, &st->gamma_hist, (size_t)st->S * kMaxRecycleStages)) ||
+            (rc = dalloc(st, &st->logz_hist, (size_t)st->S * kMaxRecycleStages * st->M))) {
+            smc_destroy(st);
+            return rc;
+        }
+    }
     if (e != cudaSuccess) {
         smc_destroy(st);
         return cuda_fail(e, "smc_create: upload data");
@@ -1309,6 +1479,8 @@ extern "C" int smc_destroy(smc_state *st) {
     delete st;
     return AEM_OK;
 }
+
+static int record_history(smc_state *st);
 
 extern "C" int smc_init(smc_state *st) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_init: NULL state");
@@ -1333,7 +1505,9 @@ extern "C" int smc_init(smc_state *st) {
     st->stage = 0;
     st->have_prev = false;
     st->gcur_valid = false;
-    return run_loglik(st, st->cur);
+    int rc = run_loglik(st, st->cur);
+    if (rc) return rc;
+    return record_history(st);
 }
 
 static int launch_group(smc_state *st) {
@@ -1371,7 +1545,7 @@ extern "C" int smc_resample(smc_state *st) {
     st->cur = st->alt;
     st->alt = t;
     st->gcur_valid = false;
-    return AEM_OK;
+    return record_history(st);
 }
 
 static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, st->pca_a, st->pca_ok}; }
@@ -1387,6 +1561,21 @@ extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
 // Section 3.2's adaptive within-model proposal for the current stage: fit
 // each (sounding, model)'s Gaussian, then bisect its scale on trial
 // proposals (desc.pca_bisect_iters forward passes) towards desc.pca_target.
+// Particle recycling: the current (post-resample) particles become history
+// slot stage mod H; this stage's gamma and log Z are kept for the weights.
+static int record_history(smc_state *st) {
+    if (st->d.recycle_stages <= 0) return AEM_OK;
+    const int t = st->stage;
+    if (t >= kMaxRecycleStages) return fail(AEM_ERR_INVALID_ARG, "particle recycling keeps at most 1024 stages");
+    record_slot_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->hist, st->cur, st->P,
+                                                                       t % st->d.recycle_stages);
+    AEM_CUDA_TRY(cudaGetLastError());
+    record_stage_kernel<<<blocks_for(st->S, 128), 128, 0, st->stream>>>(st->gamma, st->logz, st->S, st->M, t,
+                                                                        st->gamma_hist, st->logz_hist);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
 static int adapt_stage(smc_state *st) {
     int rc = launch_group(st);
     if (rc) return rc;
@@ -1394,9 +1583,24 @@ static int adapt_stage(smc_state *st) {
     const size_t smem = sizeof(double) * (2 * (size_t)DM * DM + DM);
     if (smem > 48 * 1024)
         AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    pca_fit_kernel<<<nb, kFitThreads, smem, st->stream>>>(st->cur, st->perm, st->off, st->counts, st->pr,
-                                                           st->d.pca_ridge, st->pca_mu, st->pca_U, st->pca_lam,
-                                                           st->pca_ok, st->pca_a);
+    if (st->d.recycle_stages > 0) {
+        const int t = st->stage, H = st->d.recycle_stages;
+        const int n_used = t + 1 < H ? t + 1 : H;
+        if (smem > 48 * 1024)
+            AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_recycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        recycle_weight_kernel<<<blocks_for((long long)n_used * st->P, 128), 128, 0, st->stream>>>(
+            st->hist, st->P, n_used, st->N, st->M, st->d.lambda_max + 1, t, st->gamma_hist, st->logz_hist,
+            st->hist_lognu);
+        AEM_CUDA_TRY(cudaGetLastError());
+        pca_fit_recycle_kernel<<<nb, kFitThreads, smem, st->stream>>>(
+            st->hist, st->hist_lognu, st->hist_w, n_used, st->P, st->counts, st->pr, st->d.pca_ridge, st->pca_mu,
+            st->pca_U, st->pca_lam, st->pca_ok, st->pca_a);
+    } else {
+        pca_fit_kernel<<<nb, kFitThreads, smem, st->stream>>>(st->cur, st->perm, st->off, st->counts, st->pr,
+                                                               st->d.pca_ridge, st->pca_mu, st->pca_U, st->pca_lam,
+                                                               st->pca_ok, st->pca_a);
+    }
     AEM_CUDA_TRY(cudaGetLastError());
     pca_bracket_kernel<<<blocks_for(nb, 128), 128, 0, st->stream>>>(st->pca_ok, st->pca_a, nb, 3.0, st->pca_lo,
                                                                      st->pca_hi);
@@ -1740,6 +1944,8 @@ int h2d(T *dst, const unsigned char *&i, size_t n, cudaStream_t s) {
 extern "C" int smc_checkpoint(const smc_state *cst, void *buf, size_t *size) {
     smc_state *st = const_cast<smc_state *>(cst);
     if (!st || !size) return fail(AEM_ERR_INVALID_ARG, "smc_checkpoint: NULL state or size");
+    if (st->d.recycle_stages > 0)
+        return fail(AEM_ERR_UNSUPPORTED, "smc_checkpoint: the recycling history is not part of the image");
     const size_t need = sizeof(CkptHeader) + ckpt_payload(st);
     if (!buf) {
         *size = need;

@@ -167,3 +167,50 @@ def test_adaptive_perturb_acceptance_near_target(env):
         print(f"\nadaptive={adaptive}: {stages} stages, final-stage perturb acceptance {rate[adaptive]:.3f}, "
               f"{np.mean(llmax > ll_true - 50):.2f} of soundings within 50 of the truth's log-likelihood")
     assert abs(rate[1] - 0.44) < 0.12
+
+
+def test_recycled_fit_matches_oracle(env):
+    """Particle recycling (Section 3.2): at each of four stages the GPU's fit
+    over the last three post-resample populations equals the oracle's
+    weighted fit on the same populations, log-likelihoods, gammas and
+    evidence estimates."""
+    torch, L, S, gsys, s, y_true = env
+    st = settings(n_particles=384, recycle=3)
+    sm = S.SMC(gsys, I.noisy(y_true, seed=0), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles,
+               kappa_max=st.kappa_max, lambda_max=st.lambda_max, seed=st.seed, adaptive=1, recycle_stages=3)
+    sm.init()
+
+    def population():
+        p = sm.get_particles(0)
+        return [to_oracle(p, i) for i in range(st.n_particles)], p.ll.copy()
+
+    parts, ll = population()
+    history, gammas, log_z = [(0, parts, ll)], [0.0], [np.zeros(st.n_models)]
+    n_checked = 0
+    for t in range(1, 5):
+        g = sm.reweight()
+        sm.resample()
+        parts, ll = population()
+        _, _, lz = sm.model_odds()
+        gammas.append(g[0])
+        log_z.append(lz[0].copy())
+        history = (history + [(t, parts, ll)])[-3:]
+        sm.adapt()
+        ad = sm.adaptation()
+        ref = R.fit_model_gaussians_recycled(history, st, t, gammas, log_z)
+        for k in range(st.n_models):
+            assert bool(ad["ok"][0, k]) == (k in ref), (t, k)
+            if k not in ref:
+                continue
+            mu, U, lam = ref[k]
+            d = len(mu)
+            C_ref = U @ np.diag(lam) @ U.T
+            Ug, lg = ad["U"][0, k, :d, :d], ad["lam"][0, k, :d]
+            scale = np.abs(C_ref).max()
+            assert np.allclose(ad["mu"][0, k, :d], mu, rtol=1e-10, atol=1e-10 * np.abs(mu).max()), (t, k)
+            assert np.allclose(Ug @ np.diag(lg) @ Ug.T, C_ref, atol=1e-9 * scale), (t, k)
+            n_checked += 1
+        sm.mutate(3)
+    assert n_checked >= 20
+    with pytest.raises(Exception):
+        sm.checkpoint()
