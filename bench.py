@@ -176,7 +176,7 @@ def cpu_baseline(target_seconds=15.0):
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
-                  reduce=None, n_langevin=0):
+                  reduce=None, n_langevin=0, graph=False):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
     (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s.  With
@@ -199,7 +199,7 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sm.init()
-    stages = sm.run(max_stages=500, n_sweeps=sweeps)
+    stages = sm.run_graph(max_stages=500, n_sweeps=sweeps) if graph else sm.run(max_stages=500, n_sweeps=sweeps)
     e1.record(stream)
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) * 1e-3
@@ -217,6 +217,7 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
            "forward_evals_per_s": evals / sec,
            "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
                      f"{sweeps} sweeps/stage" + (f" + {n_langevin} Langevin sweeps/stage" if n_langevin else "") +
+                     (", stages in one CUDA graph with a device-side loop condition" if graph else "") +
                      ", alpha=0.5, sounding system G=20 F=40 K=120",
            "median_log_bfipd": float(np.median(np.clip(lb, -50, 50))),
            "forward_launch_shape": shape,
@@ -517,7 +518,9 @@ def main():
         rjsmc = (rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
                  rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce),
                  rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce,
-                               n_langevin=2))
+                               n_langevin=2),
+                 rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
+                               graph=True))
 
     if rank == 0:
         flops = steps_work * FLOPS_PER_LAYER_STEP
@@ -553,7 +556,7 @@ def main():
         if fp64 is not None:
             line["fp64_plain"] = fp64
         if rjsmc is not None:
-            line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"] = rjsmc
+            line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"], line["rjsmc_graph"] = rjsmc
         if adjoint is not None:
             line["adjoint"] = adjoint
         if transforms is not None:

@@ -348,6 +348,18 @@ int smc_langevin_stats(const smc_state *st, int *accepted, int *proposed, double
  * max_stages stages (Alg. 1).  stages_out may be NULL. */
 int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 
+/* smc_run with the stage loop on the device: one stage (reweight,
+ * resample, n_sweeps >= 1 sweeps of the fixed-scale moves) is captured once
+ * into a CUDA graph as the body of a conditional WHILE node.  A kernel at the
+ * end of the body advances nothing on the host; it sets the loop condition
+ * from the new gammas (another stage while any sounding's gamma < 1 and fewer
+ * than max_stages stages have run), and the stage number lives in device
+ * memory.  No host synchronisation happens between stages.  Same results as
+ * smc_run(st, max_stages, n_sweeps) bit for bit.  Samplers with the adaptive
+ * proposal, Langevin sweeps or recycling return AEM_ERR_UNSUPPORTED.
+ * Synchronous; stages_out may be NULL. */
+int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
+
 /* Synchronous (a10).  post_k [S x M]: N_k / N; log_bfipd [S]: log of the
  * BFIPD statistic of Section 2.3.3 with uniform p(k), i.e.
  * log(N_IP / (lambda_max N_nonIP)), +inf when no particle is non-chargeable;

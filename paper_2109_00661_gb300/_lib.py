@@ -120,6 +120,7 @@ SIGNATURES = {
     "smc_langevin": ([c_void_p, c_int], c_int),
     "smc_ppd": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_adapt": ([c_void_p], c_int),
+    "smc_run_graph": ([c_void_p, c_int, c_int, c_void_p], c_int),
     "smc_get_adaptation": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_checkpoint": ([c_void_p, c_void_p, ctypes.POINTER(ctypes.c_size_t)], c_int),
     "smc_restore": ([c_void_p, c_void_p, ctypes.c_size_t], c_int),

@@ -57,9 +57,11 @@ namespace aem {
 int build_tables(const aem_system_desc *desc, SystemTables *out);
 // FP32 forward + log-likelihood where consecutive blocks of
 // models_per_sounding models use consecutive rows of y_obs (forward.cu).
+// counter: optional device int the dynamic-scheduled shapes use for model
+// claiming instead of a per-launch stream-ordered allocation.
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream);
+                         cudaStream_t stream, int *counter = nullptr);
 // Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
 // with per-sounding rows of y_obs (forward.cu).
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,

@@ -703,7 +703,7 @@ constexpr int kNumF32Shapes = 2 * kNumBase;
 template <int NT, int MINB, bool DYN>
 int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, int *counter_ext) {
     const SystemTables &h = sys->host;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS, NT / 32);
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
@@ -717,26 +717,27 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     if (per_sm < 1) return fail(AEM_ERR_UNSUPPORTED, "forward kernel: launch shape does not fit on an SM");
     long long grid = (long long)sys->num_sms * per_sm;
     if (grid > mv.n) grid = mv.n;
-    int *counter = nullptr;
-    if (DYN) {  // stream-ordered: one counter per launch, so launches on other streams never share it
+    int *counter = counter_ext;
+    const bool own = DYN && !counter_ext;
+    if (own)  // stream-ordered: one counter per launch, so launches on other streams never share it
         AEM_CUDA_TRY(cudaMallocAsync((void **)&counter, sizeof(int), stream));
-        AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
-    }
+    if (DYN) AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
                                                sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
                                                ll, counter);
     const cudaError_t e = cudaGetLastError();
-    if (DYN) cudaFreeAsync(counter, stream);
+    if (own) cudaFreeAsync(counter, stream);
     AEM_CUDA_TRY(e);
     return AEM_OK;
 }
 
 int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
                        float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int *counter_ext = nullptr) {
 #define AEM_SHAPE(I, NT, MINB, DYN) \
     case I:                         \
-        return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+        return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream, \
+                                           counter_ext);
     switch (idx) {
         AEM_SHAPE(1, 128, 8, false)
         AEM_SHAPE(2, 512, 2, false)
@@ -748,14 +749,16 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
         AEM_SHAPE(8, 256, 3, true)
         AEM_SHAPE(9, 128, 6, true)
         default:
-            return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream);
+            return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream,
+                                               counter_ext);
     }
 #undef AEM_SHAPE
 }
 
 template <class Models>
 int launch_forward_f32(const aem_system *sys, const Models *models, float *gates, float *imh, const double *y_obs,
-                       int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name) {
+                       int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name,
+                       int *counter_ext = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -768,7 +771,7 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
                            models->m, models->logtau, models->c};
     const int LS = models->lmax;
     return launch_shape_index(sys->f32_shape[LS], sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
-                              (cudaStream_t)stream);
+                              (cudaStream_t)stream, counter_ext);
 }
 
 }  // namespace
@@ -777,9 +780,9 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
 namespace aem {
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, int *counter) {
     return launch_forward_f32(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding, eps_an,
-                              eps_mn, ll, (void *)stream, "loglik (SMC)");
+                              eps_mn, ll, (void *)stream, "loglik (SMC)", counter);
 }
 }  // namespace aem
 

@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(kGroupThreads)
 // with C_r > floor((j 2^40 + u40_k) / N_k).
 __global__ void __launch_bounds__(kGroupThreads)
     resample_kernel(const double *Wg, const int *perm, const int *off, const int *counts, int N, int M,
-                    const unsigned long long *u40_in, unsigned long long seed, int stage, unsigned long long *C,
+                    const unsigned long long *u40_in, unsigned long long seed, int stage, const int *stage_dev,
+                    unsigned long long *C,
                     int *anc) {
     const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int *o = off + s * (M + 1);
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(kGroupThreads)
             u40 = u40_in[s * M + k];
         } else {
             uint32_t w[4];
-            block_draws(w, stream_key(seed, s), (uint32_t)k, (uint32_t)kPurposeResample, (uint32_t)stage, 0u);
+            block_draws(w, stream_key(seed, s), (uint32_t)k, (uint32_t)kPurposeResample,
+                        (uint32_t)(stage_dev ? *stage_dev : stage), 0u);
             u40 = (((unsigned long long)w[0] << 8) | (unsigned long long)(w[1] >> 24)) & (one - 1ull);
         }
         unsigned long long carry = 0;
@@ -452,8 +454,9 @@ __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int l
                          double a, double u_comp, double xi);
 __device__ inline bool in_bounds_open(double v, double lo, double hi) { return lo < v && v < hi; }
 
-__global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage,
-                               int sweep, PcaView pv) {
+__global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage_arg,
+                               int sweep, PcaView pv, const int *stage_dev) {
+    const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
     const int s = i / pr.N, j = i - s * pr.N;
@@ -579,7 +582,8 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
 // proposal ratios cancel (App. E), and the random walks are symmetric inside
 // the uniform prior support.
 __global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const int8_t *valid, const double *gamma,
-                              Params pr, int stage, int sweep, int *acc, int *nprop) {
+                              Params pr, int stage_arg, int sweep, int *acc, int *nprop, const int *stage_dev) {
+    const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
     const int s = i / pr.N, j = i - s * pr.N;
@@ -1191,6 +1195,25 @@ __global__ void __launch_bounds__(256) ppd_kernel(const float *gates, int N, int
     }
 }
 
+// Graph-captured stages: the stage counter advances on the device; the loop
+// condition (another stage needed) is set on the device from the new gammas.
+__global__ void stage_inc_kernel(int *d_stage) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_stage += 1;
+}
+
+__global__ void stage_cond_kernel(const double *gamma, int S, const int *d_stage, int stop_stage,
+                                  cudaGraphConditionalHandle h) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    bool all = true;
+    for (int s = 0; s < S; ++s) all = all && gamma[s] >= 1.0;
+    cudaGraphSetConditional(h, (!all && *d_stage < stop_stage) ? 1u : 0u);
+}
+
+__global__ void copy_state_kernel(PState dst, PState src, int P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) copy_particle(dst, i, src, i);
+}
+
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1265,6 +1288,9 @@ struct smc_state {
     int *lacc = nullptr, *lprop = nullptr;
     bool gcur_valid = false;
     int stage = 0;
+    // device-side stage counter (graph-captured runs) and the forward kernel's
+    // model-claim counter, owned by the sampler so its launches allocate nothing
+    int *d_stage = nullptr, *fwd_counter = nullptr;
     std::vector<int> acc_prev, nprop_prev;
     bool have_prev = false;
 };
@@ -1296,7 +1322,8 @@ int run_loglik(smc_state *st, PState ps) {
                                                                 st->m_logh, st->m_m, st->m_logtau, st->m_c);
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
-    return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream);
+    return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream,
+                                st->fwd_counter);
 }
 
 // Log-likelihood and particle-space gradient of a particle set: merge, the
@@ -1436,7 +1463,8 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->pca_U, (size_t)st->S * st->M * p.DM * p.DM)) ||
         (rc = dalloc(st, &st->pca_lam, (size_t)st->S * st->M * p.DM)) ||
         (rc = dalloc(st, &st->pca_a, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_lo, (size_t)st->S * st->M)) ||
-        (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M))) {
+        (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M)) ||
+        (rc = dalloc(st, &st->d_stage, 1)) || (rc = dalloc(st, &st->fwd_counter, 1))) {
         smc_destroy(st);
         return rc;
     }
@@ -1537,7 +1565,8 @@ extern "C" int smc_reweight(smc_state *st, double *gamma_out) {
 extern "C" int smc_resample(smc_state *st) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_resample: NULL state");
     resample_kernel<<<st->S, kGroupThreads, 0, st->stream>>>(st->Wg, st->perm, st->off, st->counts, st->N, st->M,
-                                                             nullptr, st->d.seed, st->stage, st->C, st->anc);
+                                                             nullptr, st->d.seed, st->stage, nullptr, st->C,
+                                                             st->anc);
     AEM_CUDA_TRY(cudaGetLastError());
     gather_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->alt, st->cur, st->anc, st->P);
     AEM_CUDA_TRY(cudaGetLastError());
@@ -1553,7 +1582,7 @@ static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, 
 extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_propose: NULL state");
     propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid, st->pr,
-                                                                    stage, sweep, pca_view(st));
+                                                                    stage, sweep, pca_view(st), nullptr);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -1684,7 +1713,7 @@ extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
         if ((rc = run_loglik(st, st->prop))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid,
                                                                       st->gamma, st->pr, st->stage, sw, st->acc,
-                                                                      st->nprop);
+                                                                      st->nprop, nullptr);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     if (R > 0) st->gcur_valid = false;
@@ -1721,6 +1750,101 @@ extern "C" int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_
         }
     }
     if (stages_out) *stages_out = t;
+    return AEM_OK;
+}
+
+// One stage of Algorithm 1 (reweight, resample, R sweeps of the fixed-scale
+// moves) enqueued on st->stream without host synchronisation, reading the
+// stage number from st->d_stage; ends with the loop condition.
+static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphConditionalHandle h) {
+    cudaStream_t s = st->stream;
+    stage_inc_kernel<<<1, 32, 0, s>>>(st->d_stage);
+    AEM_CUDA_TRY(cudaGetLastError());
+    int rc = launch_group(st);
+    if (rc) return rc;
+    reweight_kernel<<<st->S, kGroupThreads, 0, s>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
+                                                    st->d.alpha, st->d.bisect_iters, st->gamma, st->logz, st->Wg,
+                                                    st->dgamma, st->done);
+    AEM_CUDA_TRY(cudaGetLastError());
+    resample_kernel<<<st->S, kGroupThreads, 0, s>>>(st->Wg, st->perm, st->off, st->counts, st->N, st->M, nullptr,
+                                                    st->d.seed, 0, st->d_stage, st->C, st->anc);
+    AEM_CUDA_TRY(cudaGetLastError());
+    gather_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->alt, st->cur, st->anc, st->P);
+    AEM_CUDA_TRY(cudaGetLastError());
+    copy_state_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->alt, st->P);
+    AEM_CUDA_TRY(cudaGetLastError());
+    AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, s));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, s));
+    for (int sw = 0; sw < R; ++sw) {
+        propose_kernel<<<blocks_for(st->P, 128), 128, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->pr, 0, sw,
+                                                               pca_view(st), st->d_stage);
+        AEM_CUDA_TRY(cudaGetLastError());
+        if ((rc = run_loglik(st, st->prop))) return rc;
+        accept_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->gamma,
+                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
+    stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, h);
+    AEM_CUDA_TRY(cudaGetLastError());
+    return AEM_OK;
+}
+
+extern "C" int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: NULL state");
+    if (n_sweeps < 1 || max_stages < 1) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: n_sweeps and max_stages must be >= 1");
+    if (st->d.adaptive || st->d.n_langevin > 0 || st->d.recycle_stages > 0)
+        return fail(AEM_ERR_UNSUPPORTED,
+                    "smc_run_graph: only the fixed-scale moves (no adaptive proposal, Langevin sweeps or recycling)");
+    const int s0 = st->stage;
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    AEM_CUDA_TRY(cudaMemcpy(st->d_stage, &s0, sizeof(int), cudaMemcpyHostToDevice));
+    cudaStream_t user = st->stream, cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = AEM_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle handle{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t loop = nullptr;
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handle;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&loop, graph, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            st->stream = cap;
+            rc = enqueue_graph_stage(st, n_sweeps, s0 + max_stages, handle);
+            st->stream = user;
+            cudaGraph_t captured = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
+            if (rc == AEM_OK) e = e2;
+        }
+    }
+    if (rc == AEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (rc == AEM_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, user);
+    if (rc == AEM_OK && e == cudaSuccess) e = cudaStreamSynchronize(user);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "smc_run_graph");
+    int s1 = s0;
+    AEM_CUDA_TRY(cudaMemcpy(&s1, st->d_stage, sizeof(int), cudaMemcpyDeviceToHost));
+    st->stage = s1;
+    st->gcur_valid = false;
+    st->acc_prev.assign(st->S * kMoves, 0);
+    st->nprop_prev.assign(st->S * kMoves, 0);
+    AEM_CUDA_TRY(cudaMemcpy(st->acc_prev.data(), st->acc, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost));
+    AEM_CUDA_TRY(cudaMemcpy(st->nprop_prev.data(), st->nprop, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost));
+    st->have_prev = true;
+    if (stages_out) *stages_out = s1 - s0;
     return AEM_OK;
 }
 
@@ -2112,8 +2236,8 @@ extern "C" int aem_resample_systematic(const double *W, const int *model, int n,
     split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, 1, w.kappa, w.lam);
     group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
     gather_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(W, w.perm, n, w.Wg);
-    resample_kernel<<<1, kGroupThreads, 0, s>>>(w.Wg, w.perm, w.off, w.counts, n, n_models, u40, 0ull, 0, w.C,
-                                                ancestor);
+    resample_kernel<<<1, kGroupThreads, 0, s>>>(w.Wg, w.perm, w.off, w.counts, n, n_models, u40, 0ull, 0, nullptr,
+                                                w.C, ancestor);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }

@@ -122,6 +122,13 @@ class SMC:
         check(_lib.load().smc_run(self._h, int(max_stages), int(n_sweeps), ctypes.byref(t)), "smc_run")
         return t.value
 
+    def run_graph(self, max_stages=1000, n_sweeps=10):
+        """smc_run_graph: the stage loop captured as a CUDA graph with a device-side
+        loop condition (fixed-scale moves, n_sweeps >= 1)."""
+        t = ctypes.c_int()
+        check(_lib.load().smc_run_graph(self._h, int(max_stages), int(n_sweeps), ctypes.byref(t)), "smc_run_graph")
+        return t.value
+
     def model_odds(self):
         post = np.zeros((self.S, self.M))
         lb = np.zeros(self.S)

@@ -267,3 +267,31 @@ def test_flight_line_ip_probability_follows_chargeability(torch, L, S):
     assert p_ip[4] > 0.9
     assert lb[4] > max(lb[0], lb[8])
     assert np.all(np.isfinite(post))
+
+
+def test_graph_captured_run_equals_host_loop(S, gsys, data):
+    """smc_run_graph (one captured stage repeated by a device-side WHILE
+    condition) reproduces smc_run bit for bit: particles, log-likelihoods,
+    gammas, evidence estimates and the stage count, on three soundings."""
+    import time
+    runs = []
+    for graph in (False, True):
+        st = settings(n_particles=256, seed=21)
+        sm = gpu_smc(S, gsys, data, st, soundings=3)
+        sm.init()
+        t0 = time.perf_counter()
+        stages = sm.run_graph(max_stages=200, n_sweeps=10) if graph else sm.run(max_stages=200, n_sweeps=10)
+        dt = time.perf_counter() - t0
+        p = sm.get_particles(0)
+        post, lb, lz = sm.model_odds()
+        runs.append((stages, p, sm.stats()["gamma"], lz, dt))
+    (s0, p0, g0, z0, t0_), (s1, p1, g1, z1, t1_) = runs
+    print(f"\nhost loop {t0_ * 1e3:.1f} ms, graph {t1_ * 1e3:.1f} ms, {s0} stages")
+    assert s0 == s1 and np.all(g1 == 1.0)
+    assert np.array_equal(g0, g1) and np.array_equal(z0, z1)
+    for name in ("kappa", "lam", "phib", "tau", "c", "zc", "phic", "zm", "mv", "ll"):
+        assert np.array_equal(getattr(p0, name), getattr(p1, name)), name
+    # a capped run stops after max_stages
+    sm = gpu_smc(S, gsys, data, settings(n_particles=256, seed=21), soundings=3)
+    sm.init()
+    assert sm.run_graph(max_stages=3, n_sweeps=2) == 3
