@@ -136,6 +136,7 @@ class SMCSettings:
     pca_bisect_iters: int = 6   # bisection steps on trial proposals per stage
     pca_ridge: float = 0.01     # ridge on the fitted covariance, as a fraction of the random-walk scales
     recycle: int = 0            # > 0: fit the adaptive proposal on the last `recycle` stages' particles (Section 3.2)
+    zca: float = 0.0            # with adaptive: probability that a birth/death is the ZCA-coloured one of App. F
 
     @property
     def n_models(self):
@@ -670,12 +671,13 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
             if live:
                 ll_new[live] = loglik([props[i][1] for i in live])
             for i in range(N):
-                mv, q = props[i]
+                mv, q = props[i][:2]
+                log_f = props[i][2] if len(props[i]) > 2 else 0.0
                 prop_stage[mv] += 1
                 if q is None:
                     continue
                 u = accept_uniform(s, i, stage, sweep)
-                if math.log(u) < gamma * (ll_new[i] - ll[i]):
+                if math.log(u) < gamma * (ll_new[i] - ll[i]) + log_f:
                     parts[i] = q
                     ll[i] = ll_new[i]
                     acc_stage[mv] += 1
@@ -844,6 +846,96 @@ def fit_model_gaussians_recycled(history, s: SMCSettings, t: int, gammas, log_z)
     return out
 
 
+# ----------------------------------------- ZCA-coloured birth/death (App. F)
+# Birth k -> k+1 at depth u_d ~ U(0, zmax): the new layer's value starts as a
+# copy of the value of the layer it splits (0 for a chargeable layer inserted
+# above every chargeable interface, whose background m = 0 is fixed); then
+# every component but the new depth moves by u Sigma^(1/2)[i, j], u ~ N(0, 1),
+# with Sigma^(1/2) = U Lambda^(1/2) U^T the ZCA root of model k+1's fitted
+# covariance and i the new value's component.  The Jacobian of
+# (theta_k, u_d, u) -> theta_{k+1} is Sigma^(1/2)[i, j_new] - Sigma^(1/2)[i, h]
+# (h the copied value; 0 without one).  With uniform priors, the uniform
+# depth draw, uniform move selection and a uniformly chosen death interface,
+# the prior and proposal densities leave the birth acceptance
+#   min(1, (L'/L)^gamma |J| / (width phi(u))),
+# width the prior width of the new value (phi_hi - phi_lo, or 1 for m), and
+# the death the reciprocal with u solved from the two values.
+def zca_root(fit):
+    _, U, lam = fit
+    return (U * np.sqrt(np.maximum(lam, 0.0))) @ U.T
+
+
+def _profile_offsets(k, l):
+    """Component offsets in theta of (phi_c, z_c, z_m, m) for kappa = k, lambda = l."""
+    return 1, 1 + k, 1 + 2 * k, 1 + 2 * k + l
+
+
+def zca_birth(p: Particle, s: SMCSettings, fit_next, cond: bool, u_depth: float, u: float):
+    """Returns (proposal or None outside the support, log of the factor that
+    multiplies (L'/L)^gamma)."""
+    z = s.zmax * u_depth
+    q = p.copy()
+    if cond:
+        j = sum(1 for v in p.zc if v < z)
+        src = p.phib if j == 0 else p.phic[j - 1]
+        q.zc.insert(j, z)
+        q.phic.insert(j, src)
+        q.kappa += 1
+        o_val, o_dep, _, _ = _profile_offsets(q.kappa, q.lam)
+        width = s.phi_hi - s.phi_lo
+        j_new, h = o_val + j, (0 if j == 0 else o_val + j - 1)
+    else:
+        j = sum(1 for v in p.zm if v < z)
+        src = 0.0 if j == 0 else p.mv[j - 1]
+        q.zm.insert(j, z)
+        q.mv.insert(j, src)
+        q.lam += 1
+        _, _, o_dep, o_val = _profile_offsets(q.kappa, q.lam)
+        width = 1.0
+        j_new, h = o_val + j, (None if j == 0 else o_val + j - 1)
+    j_z = o_dep + j
+    Z = zca_root(fit_next)
+    th = theta_of(q, s)
+    for jj in range(len(th)):
+        if jj != j_z:
+            th[jj] += Z[j_new, jj] * u
+    jac = Z[j_new, j_new] - (Z[j_new, h] if h is not None else 0.0)
+    log_f = math.log(abs(jac)) - math.log(width) - (-0.5 * u * u - 0.5 * math.log(2 * math.pi))
+    q = with_theta(q, s, th)
+    return (q if theta_in_support(q, s) else None), log_f
+
+
+def zca_death(p: Particle, s: SMCSettings, fit_own, cond: bool, u_choice: float):
+    n = p.kappa if cond else p.lam
+    j = min(int(u_choice * n), n - 1)
+    o_phic, o_zc, o_zm, o_mv = _profile_offsets(p.kappa, p.lam)
+    if cond:
+        j_new, j_z, h, width = o_phic + j, o_zc + j, (0 if j == 0 else o_phic + j - 1), s.phi_hi - s.phi_lo
+    else:
+        j_new, j_z, h, width = o_mv + j, o_zm + j, (None if j == 0 else o_mv + j - 1), 1.0
+    Z = zca_root(fit_own)
+    th = theta_of(p, s)
+    jac = Z[j_new, j_new] - (Z[j_new, h] if h is not None else 0.0)
+    u = (th[j_new] - (th[h] if h is not None else 0.0)) / jac
+    back = th.copy()
+    for jj in range(len(th)):
+        if jj not in (j_z, j_new):
+            back[jj] -= Z[j_new, jj] * u
+    keep = [jj for jj in range(len(th)) if jj not in (j_z, j_new)]
+    q = p.copy()
+    if cond:
+        del q.zc[j]
+        del q.phic[j]
+        q.kappa -= 1
+    else:
+        del q.zm[j]
+        del q.mv[j]
+        q.lam -= 1
+    q = with_theta(q, s, back[keep])
+    log_f = math.log(width) + (-0.5 * u * u - 0.5 * math.log(2 * math.pi)) - math.log(abs(jac))
+    return (q if theta_in_support(q, s) else None), log_f
+
+
 def propose_adaptive(p: Particle, s: SMCSettings, i: int, stage: int, sweep: int, fits, scales):
     """The move set of propose() with the perturb move replaced by the
     adaptive principal-direction random walk (models without a fit keep the
@@ -851,6 +943,24 @@ def propose_adaptive(p: Particle, s: SMCSettings, i: int, stage: int, sweep: int
     d0 = draws(s.seed, s.sounding, i, PURPOSE_MOVE, stage, sweep)[0]
     move = min(int(u01_from(d0[0]) * 6), 5)
     k = p.model(s)
+    if s.zca > 0 and move <= 3:
+        # a state-independent choice between the ZCA-coloured and the
+        # prior-drawn pair keeps the mixture reversible
+        d1 = draws(s.seed, s.sounding, i, PURPOSE_VALUE, stage, sweep)[0]
+        use = float(u01_from(d1[3])) < s.zca
+        cond = move in (0, 1)
+        L1 = s.lambda_max + 1
+        if use and move in (0, 2):
+            n, nmax = (p.kappa, s.kappa_max) if cond else (p.lam, s.lambda_max)
+            k_next = k + (L1 if cond else 1)
+            if n < nmax and k_next in fits:
+                q, lf = zca_birth(p, s, fits[k_next], cond, float(u01_from(d0[1])), float(gauss_pair(d1[1], d1[2])))
+                return move, q, lf
+        elif use:
+            n = p.kappa if cond else p.lam
+            if n > 0 and k in fits:
+                q, lf = zca_death(p, s, fits[k], cond, float(u01_from(d0[1])))
+                return move, q, lf
     if move != 5 or k not in fits:
         return propose(p, s, i, stage, sweep)
     d1 = draws(s.seed, s.sounding, i, PURPOSE_VALUE, stage, sweep)[0]
