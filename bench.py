@@ -250,7 +250,8 @@ def convergence_study(torch, L, I):
                               ("adaptive, 10 sweeps, alpha 0.9", {"adaptive": 1, "alpha": 0.9}, 10),
                               ("adaptive, 10 sweeps + 2 Langevin", {"adaptive": 1, "n_langevin": 2}, 10),
                               ("adaptive + recycling (8 stages), 10 sweeps", {"adaptive": 1, "recycle_stages": 8}, 10),
-                              ("adaptive + recycling (8 stages), 20 sweeps", {"adaptive": 1, "recycle_stages": 8}, 20)):
+                              ("adaptive + recycling (8 stages), 20 sweeps", {"adaptive": 1, "recycle_stages": 8}, 20),
+                              ("adaptive + ZCA birth/death (p 0.5), 20 sweeps", {"adaptive": 1, "zca": 0.5}, 20)):
         for seed in (3, 4):
             args = dict(n_particles=N, n_soundings=SN, kappa_max=3, lambda_max=4, seed=seed)
             args.update(kw)

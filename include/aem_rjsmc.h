@@ -245,6 +245,7 @@ typedef struct {
     int pca_bisect_iters;                  /* bisection steps on trial proposals per stage (1..60) */
     double pca_ridge;                      /* covariance ridge, fraction of the random-walk steps (>= 0) */
     int recycle_stages;                    /* 0..32; > 0 (with adaptive): particle recycling over that many stages */
+    double zca;                            /* 0..1 (with adaptive): probability of the ZCA-coloured birth / death */
 } smc_desc;
 
 typedef struct smc_state smc_state;
@@ -262,7 +263,8 @@ typedef struct {
 /* Fills *d with the defaults (N = 256, kappa_max = 3, lambda_max = 4,
  * zmax = 500 m, alpha = 0.5, c_mut = 0.01, r_max = 10, log10 sigma in (-4, 2),
  * no Langevin sweeps, langevin_h = 0.1, langevin_adapt = 1, adaptive = 0,
- * pca_target = 0.44, pca_bisect_iters = 6, pca_ridge = 0.01, recycle_stages = 0). */
+ * pca_target = 0.44, pca_bisect_iters = 6, pca_ridge = 0.01, recycle_stages = 0,
+ * zca = 0). */
 int smc_desc_defaults(smc_desc *d);
 
 /* Synchronous.  y_obs [host, S x G] observed gates per sounding; eps_an [host, G];
@@ -398,8 +400,23 @@ int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *
  * over every stage's gamma and log Z (at most 1024 stages); a model is
  * fitted when its current population holds at least two particles.  The
  * history takes H x P particle records of device memory and is not part of a
- * checkpoint (smc_checkpoint returns AEM_ERR_UNSUPPORTED while recycling). */
+ * checkpoint (smc_checkpoint returns AEM_ERR_UNSUPPORTED while recycling).
+ * With desc.zca = p > 0 a birth or death uses, with probability p (a draw
+ * independent of the state) and when the target model (birth) or the current
+ * model (death) has a fit, Appendix F's ZCA-coloured move: the new layer's
+ * value starts as the split layer's (0 for a chargeable layer above every
+ * chargeable interface), then every component but the new depth moves by
+ * u Z[i, j], u ~ N(0, 1), Z = U Lambda^(1/2) U^T of model k+1's fit, i the new
+ * value's component; the Metropolis-Hastings test adds log(|J| / (width phi(u)))
+ * with J = Z[i, i] - Z[i, h] (the reciprocal for a death, u solved from the two
+ * values).  p = 1 is the paper's form. */
 int smc_adapt(smc_state *st);
+/* Synchronous.  lf [host, P]: the log factor each particle's last proposal
+ * (smc_propose or a sweep of smc_mutate) adds to gamma_t (l' - l) in its
+ * Metropolis-Hastings test: log(|J| / (width phi(u))) for a ZCA-coloured birth,
+ * its reciprocal for a death, 0 for every other move. */
+int smc_get_log_factors(const smc_state *st, double *lf);
+
 /* Synchronous copies of the fitted proposal, D = 3 + 2 kappa_max + 2 lambda_max:
  * mu [S][M][D], U [S][M][D][D] (row j, column r = direction r), lam [S][M][D],
  * scale [S][M], ok [S][M] (entries past a model's own dimension are unused).

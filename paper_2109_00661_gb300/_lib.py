@@ -75,6 +75,7 @@ class SMCDesc(ctypes.Structure):
         ("pca_bisect_iters", c_int),
         ("pca_ridge", c_double),
         ("recycle_stages", c_int),
+        ("zca", c_double),
     ]
 
 
@@ -120,6 +121,7 @@ SIGNATURES = {
     "smc_langevin": ([c_void_p, c_int], c_int),
     "smc_ppd": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_adapt": ([c_void_p], c_int),
+    "smc_get_log_factors": ([c_void_p, c_void_p], c_int),
     "smc_run_graph": ([c_void_p, c_int, c_int, c_void_p], c_int),
     "smc_get_adaptation": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_checkpoint": ([c_void_p, c_void_p, ctypes.POINTER(ctypes.c_size_t)], c_int),

@@ -107,6 +107,7 @@ struct PState {
 
 struct Params {
     int N, S, kappa_max, lambda_max, M, LMS, tau_log_prior, adaptive, DM;
+    double zca_prob;
     double zmax, phi_lo, phi_hi, logtau_lo, logtau_hi, step_phi, step_m, step_tau, step_c, step_z;
     unsigned long long seed;
 };
@@ -452,10 +453,15 @@ struct PcaView {
 };
 __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int lam, const Params &pr, PcaView pv,
                          double a, double u_comp, double xi);
+// Appendix F's ZCA-coloured birth / death (defined below): returns false when
+// the move does not apply (no fit of the target model, or a full / empty
+// profile), otherwise writes the proposal and sets ok and the log factor.
+__device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool cond, const Params &pr, PcaView pv,
+                         double u1, double xi, bool &ok, double &lf);
 __device__ inline bool in_bounds_open(double v, double lo, double hi) { return lo < v && v < hi; }
 
 __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage_arg,
-                               int sweep, PcaView pv, const int *stage_dev) {
+                               int sweep, PcaView pv, const int *stage_dev, double *lf_out) {
     const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
@@ -470,7 +476,15 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
     copy_particle(prop, i, cur, i);
     int kappa = cur.kappa[i], lam = cur.lam[i];
     bool ok = true;
-    if (move == 0 || move == 2) {  // birth: depth U(0, zmax), property from the prior
+    double lf = 0.0;
+    // a state-independent choice between the ZCA-coloured pair and the
+    // prior-drawn one keeps the mixture reversible
+    const bool zca = pr.adaptive && pr.zca_prob > 0.0 && move <= 3 && u01(d1[3]) < pr.zca_prob &&
+                     zca_move(cur, prop, i, s, move == 0 || move == 2, move <= 1, pr, pv, u1, gauss(d1[1], d1[2]),
+                              ok, lf);
+    if (zca) {
+        // proposal written by zca_move
+    } else if (move == 0 || move == 2) {  // birth: depth U(0, zmax), property from the prior
         const bool cond = move == 0;
         const int n = cond ? kappa : lam;
         if (n >= (cond ? pr.kappa_max : pr.lambda_max)) {
@@ -575,6 +589,7 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
     if (!ok) copy_particle(prop, i, cur, i);
     move_out[i] = (int8_t)move;
     valid_out[i] = ok ? 1 : 0;
+    if (lf_out) lf_out[i] = lf;
 }
 
 // Tempered Metropolis-Hastings test: accept when ln u < gamma_t (l' - l).
@@ -582,7 +597,8 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
 // proposal ratios cancel (App. E), and the random walks are symmetric inside
 // the uniform prior support.
 __global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const int8_t *valid, const double *gamma,
-                              Params pr, int stage_arg, int sweep, int *acc, int *nprop, const int *stage_dev) {
+                              Params pr, int stage_arg, int sweep, int *acc, int *nprop, const int *stage_dev,
+                              const double *lf) {
     const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
@@ -594,7 +610,7 @@ __global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const
     block_draws(w, stream_key(pr.seed, s), (uint32_t)j, (uint32_t)kPurposeAccept, (uint32_t)stage, (uint32_t)sweep);
     const double u = u01_53(w[0], w[1]);
     const double dl = prop.ll[i] - cur.ll[i];
-    if (log(u) < gamma[s] * dl) {
+    if (log(u) < gamma[s] * dl + (lf ? lf[i] : 0.0)) {
         copy_particle(cur, i, prop, i);
         atomicAdd(&acc[s * kMoves + mv], 1);
     }
@@ -814,6 +830,115 @@ __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int l
     else
         ok = ok && in_bounds_open(prop.tau[i], 0.0, 1.0);
     return ok;
+}
+
+// ZCA-coloured birth / death (Appendix F).  Birth k -> k+1 at depth
+// u_d = zmax u1: the new value starts as a copy of the value of the layer it
+// splits (0 for a chargeable layer above every chargeable interface), then
+// every component but the new depth moves by u Z[i, j], u ~ N(0, 1), with
+// Z = U Lambda^(1/2) U^T the ZCA root of model k+1's fit and i the new value's
+// component; the factor multiplying (L'/L)^gamma is |J| / (width phi(u)),
+// J = Z[i, i] - Z[i, h] (h the copied value's component, absent for the m = 0
+// background).  Death: the interface floor(u1 n) of model k, u solved from
+// the two values, the reciprocal factor.
+__device__ inline double zca_entry(const double *U, const double *lam, int DM, int d, int i, int jj) {
+    double z = 0.0;
+    for (int r = 0; r < d; ++r) z += U[(size_t)i * DM + r] * sqrt(lam[r] > 0.0 ? lam[r] : 0.0) * U[(size_t)jj * DM + r];
+    return z;
+}
+
+__device__ inline void theta_store(const ThetaRef &r, const Params &pr, double v) {
+    *r.x = (float)((r.is_tau && pr.tau_log_prior) ? pow(10.0, v) : v);
+}
+
+__device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool cond, const Params &pr, PcaView pv,
+                         double u1, double xi, bool &ok, double &lf) {
+    const int kappa = cur.kappa[i], lam = cur.lam[i];
+    const int lp1 = pr.lambda_max + 1, DM = pr.DM;
+    const double width = cond ? pr.phi_hi - pr.phi_lo : 1.0;
+    const double log_phi0 = -0.91893853320467274;  // log(1 / sqrt(2 pi))
+    if (birth) {
+        const int n = cond ? kappa : lam;
+        if (n >= (cond ? pr.kappa_max : pr.lambda_max)) return false;
+        const int kk = s * pr.M + (cond ? (kappa + 1) * lp1 + lam : kappa * lp1 + lam + 1);
+        if (!pv.ok[kk]) return false;
+        float *zz = cond ? prop.zc : prop.zm;
+        float *vv = cond ? prop.phic : prop.mv;
+        const double z = __dmul_rn(pr.zmax, u1);
+        int at = 0;
+        while (at < n && (double)zz[i * KS + at] < z) ++at;
+        const float src = cond ? (at == 0 ? cur.phib[i] : cur.phic[i * KS + at - 1]) : (at == 0 ? 0.f : cur.mv[i * KS + at - 1]);
+        for (int q = n; q > at; --q) {
+            zz[i * KS + q] = zz[i * KS + q - 1];
+            vv[i * KS + q] = vv[i * KS + q - 1];
+        }
+        zz[i * KS + at] = (float)z;
+        vv[i * KS + at] = src;
+        const int k2 = cond ? kappa + 1 : kappa, l2 = cond ? lam : lam + 1;
+        if (cond)
+            prop.kappa[i] = k2;
+        else
+            prop.lam[i] = l2;
+        const int d = 3 + 2 * k2 + 2 * l2;
+        const int o_val = cond ? 1 : 1 + 2 * k2 + l2, o_dep = cond ? 1 + k2 : 1 + 2 * k2;
+        const int j_new = o_val + at, j_z = o_dep + at, h = cond ? (at == 0 ? 0 : o_val + at - 1) : (at == 0 ? -1 : o_val + at - 1);
+        const double *U = pv.U + (size_t)kk * DM * DM, *L = pv.lam + (size_t)kk * DM;
+        double th[3 + 4 * AEM_SMC_SLOTS];
+        // the new value's base is the copied value (exact in float), then the shift
+        for (int jj = 0; jj < d; ++jj) th[jj] = theta_value(theta_ref(prop, i, jj, k2, l2, pr), pr);
+        for (int jj = 0; jj < d; ++jj)
+            if (jj != j_z) th[jj] += zca_entry(U, L, DM, d, j_new, jj) * xi;
+        for (int jj = 0; jj < d; ++jj) theta_store(theta_ref(prop, i, jj, k2, l2, pr), pr, th[jj]);
+        const double jac = zca_entry(U, L, DM, d, j_new, j_new) - (h >= 0 ? zca_entry(U, L, DM, d, j_new, h) : 0.0);
+        lf = log(fabs(jac)) - log(width) - (log_phi0 - 0.5 * xi * xi);
+    } else {
+        const int n = cond ? kappa : lam;
+        if (n == 0) return false;
+        const int kk = s * pr.M + kappa * lp1 + lam;
+        if (!pv.ok[kk]) return false;
+        int at = (int)(u1 * n);
+        at = at > n - 1 ? n - 1 : at;
+        const int d = 3 + 2 * kappa + 2 * lam;
+        const int o_val = cond ? 1 : 1 + 2 * kappa + lam, o_dep = cond ? 1 + kappa : 1 + 2 * kappa;
+        const int j_new = o_val + at, j_z = o_dep + at, h = cond ? (at == 0 ? 0 : o_val + at - 1) : (at == 0 ? -1 : o_val + at - 1);
+        const double *U = pv.U + (size_t)kk * DM * DM, *L = pv.lam + (size_t)kk * DM;
+        double th[3 + 4 * AEM_SMC_SLOTS];
+        for (int jj = 0; jj < d; ++jj) th[jj] = theta_value(theta_ref(cur, i, jj, kappa, lam, pr), pr);
+        const double jac = zca_entry(U, L, DM, d, j_new, j_new) - (h >= 0 ? zca_entry(U, L, DM, d, j_new, h) : 0.0);
+        const double u = (th[j_new] - (h >= 0 ? th[h] : 0.0)) / jac;
+        for (int jj = 0; jj < d; ++jj)
+            if (jj != j_z && jj != j_new) th[jj] -= zca_entry(U, L, DM, d, j_new, jj) * u;
+        // drop the two components, then the interface from the profile
+        int w = 0;
+        for (int jj = 0; jj < d; ++jj)
+            if (jj != j_z && jj != j_new) th[w++] = th[jj];
+        float *zz = cond ? prop.zc : prop.zm;
+        float *vv = cond ? prop.phic : prop.mv;
+        for (int q = at; q < n - 1; ++q) {
+            zz[i * KS + q] = zz[i * KS + q + 1];
+            vv[i * KS + q] = vv[i * KS + q + 1];
+        }
+        zz[i * KS + n - 1] = 0.f;
+        vv[i * KS + n - 1] = 0.f;
+        const int k2 = cond ? kappa - 1 : kappa, l2 = cond ? lam : lam - 1;
+        if (cond)
+            prop.kappa[i] = k2;
+        else
+            prop.lam[i] = l2;
+        for (int jj = 0; jj < w; ++jj) theta_store(theta_ref(prop, i, jj, k2, l2, pr), pr, th[jj]);
+        lf = log(width) + (log_phi0 - 0.5 * u * u) - log(fabs(jac));
+    }
+    const int k2 = prop.kappa[i], l2 = prop.lam[i];
+    ok = in_bounds_open(prop.phib[i], pr.phi_lo, pr.phi_hi) && in_bounds_open(prop.c[i], 0.0, 1.0);
+    for (int q = 0; q < k2; ++q) ok = ok && in_bounds_open(prop.phic[i * KS + q], pr.phi_lo, pr.phi_hi);
+    for (int q = 0; q < l2; ++q) ok = ok && in_bounds_open(prop.mv[i * KS + q], 0.0, 1.0);
+    ok = ok && ordered_open(prop.zc + (size_t)i * KS, k2, pr.zmax) && ordered_open(prop.zm + (size_t)i * KS, l2, pr.zmax);
+    if (pr.tau_log_prior)
+        ok = ok && prop.tau[i] > 0.f && in_bounds_open(log10((double)prop.tau[i]), pr.logtau_lo, pr.logtau_hi);
+    else
+        ok = ok && in_bounds_open(prop.tau[i], 0.0, 1.0);
+    ok = ok && isfinite(lf);
+    return true;
 }
 
 constexpr int kFitThreads = 128;
@@ -1261,6 +1386,7 @@ struct smc_state {
     PState cur{}, alt{}, prop{};
     std::vector<void *> allocs;
     int8_t *move = nullptr, *valid = nullptr;
+    double *lf = nullptr;  // per-proposal log factor of the ZCA-coloured birth / death (0 otherwise)
     int *anc = nullptr, *perm = nullptr, *off = nullptr, *counts = nullptr, *acc = nullptr, *nprop = nullptr,
         *done = nullptr;
     double *Wg = nullptr, *gamma = nullptr, *logz = nullptr, *dgamma = nullptr;
@@ -1361,6 +1487,8 @@ int check_desc(const smc_desc *d) {
     if (d->adaptive && (!(d->pca_target > 0 && d->pca_target < 1) || d->pca_bisect_iters < 1 ||
                         d->pca_bisect_iters > 60 || !(d->pca_ridge >= 0)))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: invalid pca_target / pca_bisect_iters / pca_ridge");
+    if (!(d->zca >= 0.0 && d->zca <= 1.0) || (d->zca > 0.0 && !d->adaptive))
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: zca outside [0, 1], or set without adaptive");
     if (d->recycle_stages < 0 || d->recycle_stages > 32 || (d->recycle_stages > 0 && !d->adaptive))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: recycle_stages outside 0..32, or set without adaptive");
     if (d->n_langevin < 0 || d->n_langevin > 1000 || !(d->langevin_h > 0))
@@ -1401,6 +1529,7 @@ extern "C" int smc_desc_defaults(smc_desc *d) {
     d->pca_bisect_iters = 6;
     d->pca_ridge = 0.01;
     d->recycle_stages = 0;
+    d->zca = 0.0;
     return AEM_OK;
 }
 
@@ -1441,6 +1570,7 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
     p.step_z = desc->step_z;
     p.seed = desc->seed;
     p.adaptive = desc->adaptive;
+    p.zca_prob = desc->zca;
     p.DM = 3 + 2 * desc->kappa_max + 2 * desc->lambda_max;
     const int G = sys->host.G;
     const size_t P = st->P;
@@ -1464,7 +1594,8 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->pca_lam, (size_t)st->S * st->M * p.DM)) ||
         (rc = dalloc(st, &st->pca_a, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_lo, (size_t)st->S * st->M)) ||
         (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M)) ||
-        (rc = dalloc(st, &st->d_stage, 1)) || (rc = dalloc(st, &st->fwd_counter, 1))) {
+        (rc = dalloc(st, &st->d_stage, 1)) || (rc = dalloc(st, &st->fwd_counter, 1)) ||
+        (rc = dalloc(st, &st->lf, P))) {
         smc_destroy(st);
         return rc;
     }
@@ -1582,7 +1713,7 @@ static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, 
 extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_propose: NULL state");
     propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid, st->pr,
-                                                                    stage, sweep, pca_view(st), nullptr);
+                                                                    stage, sweep, pca_view(st), nullptr, st->lf);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -1713,7 +1844,7 @@ extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
         if ((rc = run_loglik(st, st->prop))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid,
                                                                       st->gamma, st->pr, st->stage, sw, st->acc,
-                                                                      st->nprop, nullptr);
+                                                                      st->nprop, nullptr, st->lf);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     if (R > 0) st->gcur_valid = false;
@@ -1777,11 +1908,11 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, s));
     for (int sw = 0; sw < R; ++sw) {
         propose_kernel<<<blocks_for(st->P, 128), 128, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->pr, 0, sw,
-                                                               pca_view(st), st->d_stage);
+                                                               pca_view(st), st->d_stage, nullptr);
         AEM_CUDA_TRY(cudaGetLastError());
         if ((rc = run_loglik(st, st->prop))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->gamma,
-                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage);
+                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage, nullptr);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, h);
@@ -2000,6 +2131,14 @@ extern "C" int smc_ppd(smc_state *st, double *mean, double *var, double *z, floa
         AEM_CUDA_TRY(cudaMemcpyAsync(gates_host, st->ppd_gates, sizeof(float) * P * G, cudaMemcpyDeviceToHost,
                                      st->stream));
     AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return AEM_OK;
+}
+
+extern "C" int smc_get_log_factors(const smc_state *cst, double *lf) {
+    smc_state *st = const_cast<smc_state *>(cst);
+    if (!st || !lf) return fail(AEM_ERR_INVALID_ARG, "smc_get_log_factors: NULL argument");
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    AEM_CUDA_TRY(cudaMemcpy(lf, st->lf, sizeof(double) * st->P, cudaMemcpyDeviceToHost));
     return AEM_OK;
 }
 

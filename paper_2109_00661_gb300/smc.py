@@ -158,6 +158,12 @@ class SMC:
         check(_lib.load().smc_set_particles(self._h, ctypes.byref(s), None if g is None else g.ctypes.data,
                                             None if lz is None else lz.ctypes.data, int(stage)), "smc_set_particles")
 
+    def log_factors(self):
+        """smc_get_log_factors: [P] log factor of each particle's last proposal."""
+        lf = np.zeros(self.P)
+        check(_lib.load().smc_get_log_factors(self._h, lf.ctypes.data), "smc_get_log_factors")
+        return lf
+
     def adapt(self):
         check(_lib.load().smc_adapt(self._h), "smc_adapt")
 

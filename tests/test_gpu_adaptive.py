@@ -45,7 +45,7 @@ def gpu_smc(S, gsys, data, st, soundings=1):
     return S.SMC(gsys, np.tile(data, (soundings, 1)), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles,
                  n_soundings=soundings, kappa_max=st.kappa_max, lambda_max=st.lambda_max, seed=st.seed,
                  adaptive=int(st.adaptive), pca_target=st.pca_target, pca_bisect_iters=st.pca_bisect_iters,
-                 pca_ridge=st.pca_ridge)
+                 pca_ridge=st.pca_ridge, zca=float(st.zca))
 
 
 def to_oracle(h, i):
@@ -214,3 +214,38 @@ def test_recycled_fit_matches_oracle(env):
     assert n_checked >= 20
     with pytest.raises(Exception):
         sm.checkpoint()
+
+
+@pytest.mark.parametrize("zca", [1.0, 0.5])
+def test_zca_moves_match_oracle(env, zca):
+    """Appendix F's ZCA-coloured birth / death on the GPU: given the GPU's fit,
+    every proposal of a sweep and its log factor equal the oracle's
+    propose_adaptive (moves, support decisions, parameters to float32
+    rounding, log factors to 1e-9)."""
+    torch, L, S, gsys, s, y_true = env
+    st = settings(zca=zca)
+    sm, _ = staged(S, gsys, I.noisy(y_true, seed=0), st)
+    fits, scales = gpu_fits(sm.adaptation(), st)
+    n_zca = 0
+    for sweep in (0, 3):
+        sm.propose(1, sweep)
+        cur, prop = sm.get_particles(0), sm.get_particles(1)
+        lf = sm.log_factors()
+        for i in range(st.n_particles):
+            p = to_oracle(cur, i)
+            res = R.propose_adaptive(p, st, i, 1, sweep, fits, scales)
+            mv, q = res[:2]
+            lf_ref = res[2] if len(res) > 2 else 0.0
+            assert prop.move[i] == mv and bool(prop.valid[i]) == (q is not None), (i, mv)
+            if len(res) > 2:
+                n_zca += 1
+                assert abs(lf[i] - lf_ref) <= 1e-9 * max(1.0, abs(lf_ref)), (i, lf[i], lf_ref)
+            else:
+                assert lf[i] == 0.0
+            if q is None:
+                continue
+            assert (q.kappa, q.lam) == (int(prop.kappa[i]), int(prop.lam[i]))
+            got = R.theta_of(to_oracle(prop, i), st)
+            ref = R.theta_of(q, st).astype(np.float32).astype(np.float64)
+            assert np.allclose(got, ref, rtol=4e-7, atol=1e-30), (i, mv, got, ref)
+    assert n_zca > 50
