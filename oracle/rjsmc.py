@@ -93,8 +93,23 @@ def stream_key(seed, sounding):
     return (seed & _MASK, ((seed >> 32) ^ sounding) & _MASK)
 
 
+def philox4x32_one(c0, c1, c2, c3, k0, k1):
+    """philox4x32 of one counter in plain Python integers (the same rounds)."""
+    for _ in range(10):
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0) & _MASK, p1 & _MASK, ((p0 >> 32) ^ c3 ^ k1) & _MASK, p0 & _MASK
+        k0 = (k0 + _W0) & _MASK
+        k1 = (k1 + _W1) & _MASK
+    return c0, c1, c2, c3
+
+
 def draws(seed, sounding, particle, purpose, stage, sweep):
     """Four 32-bit words for each particle index in `particle`."""
+    if np.ndim(particle) == 0:
+        k0, k1 = stream_key(seed, sounding)
+        w = philox4x32_one(int(particle) & _MASK, purpose & _MASK, stage & _MASK, sweep & _MASK, k0, k1)
+        return np.array([w], dtype=np.uint64)
     particle = np.atleast_1d(np.asarray(particle, dtype=np.uint64))
     ctr = np.zeros((len(particle), 4), dtype=np.uint64)
     ctr[:, 0] = particle

@@ -113,6 +113,28 @@ def test_sweeps_formula_is_the_smallest_r(p):
 
 
 # ------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Both Philox paths reproduce the generator's published known-answer
+    vectors (tests/golden/philox4x32_10_kat.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert R.philox4x32_one(*v[:4], *v[4:6]) == tuple(v[6:])
+        assert [int(x) for x in R.philox4x32([v[:4]], tuple(v[4:6]))[0]] == v[6:]
+
+
+def test_philox_scalar_path_equals_array_path():
+    rng = np.random.default_rng(9)
+    ctr = rng.integers(0, 2 ** 32, (64, 4), dtype=np.uint64)
+    key = (int(rng.integers(0, 2 ** 32)), int(rng.integers(0, 2 ** 32)))
+    ref = R.philox4x32(ctr, key)
+    for row, r in zip(ctr, ref):
+        assert R.philox4x32_one(*[int(v) for v in row], *key) == tuple(int(v) for v in r)
+
+
 def test_philox_uniform_statistics():
     d = R.draws(7, 0, np.arange(1 << 14), R.PURPOSE_MOVE, 1, 0).ravel()
     u = R.u01_from(d)
