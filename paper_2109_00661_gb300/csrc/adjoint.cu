@@ -71,6 +71,9 @@ struct GradModels {
 // Shared memory (dynamic): S[F*LS] (float2 s), DS[F*LS*4] (float2 ds/dp for
 // log10 sigma, m, log10 tau, c), lamhw[K] (float2 {lambda, weight}),
 // af[F], T[G*F], part[kGW * LS * kNP] (float).
+// MAXL: the largest layer count the per-thread arrays hold (10 or
+// AEM_MAX_LAYERS), so the common lmax <= 10 keeps them half as large.
+template <int MAXL>
 __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS,
                                                           const float *__restrict__ g_omega,
                                                           const float *__restrict__ g_lam,
@@ -158,9 +161,15 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         __syncthreads();
 
         // ---- pass 2: reverse sweep per item, per-thread accumulators
-        float acc[AEM_MAX_LAYERS * kNP];
+        float acc[MAXL * kNP];
         for (int v = 0; v < L * kNP; ++v) acc[v] = 0.f;
-        float2 Gam[AEM_MAX_LAYERS];
+        // reflection coefficients of the bottom-up pass; with MAXL <= 10 also
+        // its vertical wavenumbers and propagation factors, which the top-down
+        // pass then reuses (for 20 layers the larger stack costs more than the
+        // recomputation saves)
+        constexpr bool kKeep = MAXL <= 10;
+        constexpr int MK = kKeep ? MAXL : 1;
+        float2 Gam[MAXL], Us[MK], Es[MK];
         int f = tid / K, k = tid - (tid / K) * K;
         for (int item = tid; item < FK; item += blockDim.x) {
             const float2 lh = lamhw[k];
@@ -173,6 +182,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                 float2 sb = Sf[L - 1];
                 float2 ub = csqrt_up(lam2 + sb.x, sb.y);
                 for (int j = L - 1; j >= 0; --j) {
+                    if constexpr (kKeep) Us[j] = ub;
                     const float2 sa = j > 0 ? Sf[j - 1] : make_float2(0.f, 0.f);
                     const float2 ua = j > 0 ? csqrt_up(lam2 + sa.x, sa.y) : make_float2(lam, 0.f);
                     const float2 q = cadd(ua, ub);
@@ -181,6 +191,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                         Gam[j] = rho;
                     } else {
                         const float2 E = cexpf2(cscale(ub, -2.f * thick[j]));
+                        if constexpr (kKeep) Es[j] = E;
                         const float2 b = cmul(Gam[j + 1], E);
                         Gam[j] = cmul(cadd(rho, b), crcp(cadd(make_float2(1.f, 0.f), cmul(rho, b))));
                     }
@@ -193,7 +204,11 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
             float2 ubar_p = make_float2(0.f, 0.f), sbar_p = make_float2(0.f, 0.f);
             for (int j = 0; j < L; ++j) {
                 const float2 sj = Sf[j];
-                const float2 uj = csqrt_up(lam2 + sj.x, sj.y);
+                float2 uj;
+                if constexpr (kKeep)
+                    uj = Us[j];
+                else
+                    uj = csqrt_up(lam2 + sj.x, sj.y);
                 const float2 q = cadd(up, uj);
                 const float2 iq = crcp(q);
                 const float2 iq2 = cmul(iq, iq);
@@ -201,7 +216,11 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                 float2 rbar, ubar_j = make_float2(0.f, 0.f), gnext = make_float2(0.f, 0.f);
                 if (j < L - 1) {
                     const float h = thick[j];
-                    const float2 E = cexpf2(cscale(uj, -2.f * h));
+                    float2 E;
+                    if constexpr (kKeep)
+                        E = Es[j];
+                    else
+                        E = cexpf2(cscale(uj, -2.f * h));
                     const float2 Gn = Gam[j + 1];
                     const float2 b = cmul(Gn, E);
                     const float2 iden = crcp(cadd(make_float2(1.f, 0.f), cmul(rho, b)));
@@ -280,7 +299,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     const int LS = models->lmax;
     const size_t smem = sizeof(float2) * ((size_t)h.F * LS * 5 + h.K) +
                         sizeof(float) * ((size_t)h.F + (size_t)h.G * h.F + (size_t)kGW * LS * kNP);
-    auto kern = loglik_grad_kernel;
+    auto kern = LS <= 10 ? loglik_grad_kernel<10> : loglik_grad_kernel<AEM_MAX_LAYERS>;
     if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGT, smem));
