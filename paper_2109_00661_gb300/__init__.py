@@ -24,6 +24,7 @@ CC_PELTON = 1
 GATES_FP32 = 0
 GATES_TF32_SPLIT = 1
 GATES_BF16_SPLIT = 2
+F32_SHAPES = 10  # AEM_F32_SHAPES: launch shapes of the FP32 forward kernel
 
 
 def _torch():
@@ -85,7 +86,7 @@ class System:
         torch = _torch()
         ms = _models_struct(models, torch.float32)
         shape = ctypes.c_int()
-        times = (ctypes.c_float * 10)()
+        times = (ctypes.c_float * F32_SHAPES)()
         check(_lib.load().aem_autotune_forward(self._h, ctypes.byref(ms), int(repeats), _stream_ptr(stream),
                                                ctypes.byref(shape), times), "aem_autotune_forward")
         return shape.value, [float(t) for t in times]

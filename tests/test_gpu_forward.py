@@ -15,13 +15,14 @@ delta one of the component accuracies asserted separately (the spectrum
 relative to the Hankel sum's magnitude A_f, the two transform tables relative
 to each row's largest entry):
   FP64:  e_g <= 1e-7 + kappa_H,g 1e-12 + kappa_g 2^-46 + kappa_T,g 1e-8
-  FP32:  e_g <= 1e-4 + kappa_H,g 1e-5 + kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8
+  FP32:  e_g <= 1e-4 + kappa_H,g 3e-5 + kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8
 and the fraction of gates inside the plain 1e-4 FP32 bound is reported.
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from paper_2109_00661_gb300 import F32_SHAPES
 from paper_2109_00661_gb300 import inputs as I
 from parity_util import (DELTA_S32, DELTA_S64, DELTA_T, assert_within, bound32, bound64, kappa, loglik_bound,
                          oracle_ref, oracle_system, rel_err, spectrum_err)
@@ -201,7 +202,7 @@ def test_full_size_sampled_parity(lib, torch_mod):
     assert torch_mod.isfinite(y).all()
 
 
-@pytest.mark.parametrize("shape", range(10))
+@pytest.mark.parametrize("shape", range(F32_SHAPES))
 def test_every_launch_shape_matches_oracle(lib, torch_mod, shape):
     """Each launch shape the autotuner can choose passes the FP32 parity bar
     on a batch that spans several CTAs per SM and a ragged tail."""
@@ -222,7 +223,7 @@ def test_autotune_records_the_fastest_shape(lib, torch_mod):
     shape, ms = sysg.autotune(models, repeats=2)
     fits = [t for t in ms if t > 0]
     print(f"\nautotune: shape {shape}, ms per launch {['%.2f' % t for t in ms]}")
-    assert 0 <= shape < 10 and ms[shape] == min(fits)
+    assert len(ms) == F32_SHAPES and 0 <= shape < F32_SHAPES and ms[shape] == min(fits)
     # the recorded shape is used: results equal a launch forced to that shape
     a = lib.forward_f32(sysg, models)
     sysg.set_forward_shape(models["logsig"].shape[1], shape)
