@@ -41,17 +41,38 @@ __device__ __forceinline__ float2 crcp(float2 a) {
     const float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
     return make_float2(a.x * d, -a.y * d);
 }
-// principal square root of (x, y) with y > 0
-__device__ __forceinline__ float2 csqrt_up(float x, float y) {
-    const float mod = sqrtf(fmaf(x, x, y * y));
-    const float q = sqrtf(0.5f * (mod + fabsf(x)));
-    const float o = 0.5f * y / q;
-    return x >= 0.f ? make_float2(q, o) : make_float2(o, q);
+// The per-item passes use the hardware approximations of rcp, rsqrt, ex2,
+// sin and cos (relative error about 2^-22; the FP32 forward kernel uses the
+// same ones), the per-(frequency, layer) Cole-Cole setup the rounded library
+// functions.
+__device__ __forceinline__ float rcp_a(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
 }
-__device__ __forceinline__ float2 cexpf2(float2 z) {
-    float s, c;
-    sincosf(z.y, &s, &c);
-    const float e = expf(z.x);
+__device__ __forceinline__ float rsqrt_a(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float2 crcp_a(float2 a) {
+    const float d = rcp_a(fmaf(a.x, a.x, a.y * a.y));
+    return make_float2(a.x * d, -a.y * d);
+}
+// principal root of x + i y, y > 0: with t = (|z| + |x|) / 2 the pair
+// (sqrt t, y / (2 sqrt t)) is (Re, Im) for x >= 0 and (Im, Re) otherwise
+__device__ __forceinline__ float2 csqrt_a(float x, float y) {
+    const float v = fmaf(x, x, y * y);
+    const float t = 0.5f * fmaf(v, rsqrt_a(v), fabsf(x));
+    const float rr = rsqrt_a(t);
+    const float p = t * rr, o = 0.5f * y * rr;
+    return x >= 0.f ? make_float2(p, o) : make_float2(o, p);
+}
+__device__ __forceinline__ float2 cexp_a(float2 z) {
+    float s, c, e;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(z.y));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(z.y));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z.x * 1.44269504088896341f));
     return make_float2(e * c, e * s);
 }
 
@@ -180,20 +201,20 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
             // bottom-up: Gamma_j for every interface j
             {
                 float2 sb = Sf[L - 1];
-                float2 ub = csqrt_up(lam2 + sb.x, sb.y);
+                float2 ub = csqrt_a(lam2 + sb.x, sb.y);
                 for (int j = L - 1; j >= 0; --j) {
                     if constexpr (kKeep) Us[j] = ub;
                     const float2 sa = j > 0 ? Sf[j - 1] : make_float2(0.f, 0.f);
-                    const float2 ua = j > 0 ? csqrt_up(lam2 + sa.x, sa.y) : make_float2(lam, 0.f);
+                    const float2 ua = j > 0 ? csqrt_a(lam2 + sa.x, sa.y) : make_float2(lam, 0.f);
                     const float2 q = cadd(ua, ub);
-                    const float2 rho = cmul(csub(sa, Sf[j]), crcp(cmul(q, q)));
+                    const float2 rho = cmul(csub(sa, Sf[j]), crcp_a(cmul(q, q)));
                     if (j == L - 1) {
                         Gam[j] = rho;
                     } else {
-                        const float2 E = cexpf2(cscale(ub, -2.f * thick[j]));
+                        const float2 E = cexp_a(cscale(ub, -2.f * thick[j]));
                         if constexpr (kKeep) Es[j] = E;
                         const float2 b = cmul(Gam[j + 1], E);
-                        Gam[j] = cmul(cadd(rho, b), crcp(cadd(make_float2(1.f, 0.f), cmul(rho, b))));
+                        Gam[j] = cmul(cadd(rho, b), crcp_a(cadd(make_float2(1.f, 0.f), cmul(rho, b))));
                     }
                     ub = ua;
                 }
@@ -208,9 +229,9 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                 if constexpr (kKeep)
                     uj = Us[j];
                 else
-                    uj = csqrt_up(lam2 + sj.x, sj.y);
+                    uj = csqrt_a(lam2 + sj.x, sj.y);
                 const float2 q = cadd(up, uj);
-                const float2 iq = crcp(q);
+                const float2 iq = crcp_a(q);
                 const float2 iq2 = cmul(iq, iq);
                 const float2 rho = cmul(csub(sp, sj), iq2);
                 float2 rbar, ubar_j = make_float2(0.f, 0.f), gnext = make_float2(0.f, 0.f);
@@ -220,10 +241,10 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                     if constexpr (kKeep)
                         E = Es[j];
                     else
-                        E = cexpf2(cscale(uj, -2.f * h));
+                        E = cexp_a(cscale(uj, -2.f * h));
                     const float2 Gn = Gam[j + 1];
                     const float2 b = cmul(Gn, E);
-                    const float2 iden = crcp(cadd(make_float2(1.f, 0.f), cmul(rho, b)));
+                    const float2 iden = crcp_a(cadd(make_float2(1.f, 0.f), cmul(rho, b)));
                     const float2 iden2 = cmul(iden, iden);
                     rbar = cmul(gbar, cmul(csub(make_float2(1.f, 0.f), cmul(b, b)), iden2));
                     const float2 tbar = cmul(gbar, cmul(csub(make_float2(1.f, 0.f), cmul(rho, rho)), iden2));
@@ -241,7 +262,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                     sbar_p = cadd(sbar_p, cmul(rbar, iq2));
                     ubar_p = cadd(ubar_p, dq);
                     // layer j-1 complete: s enters through u as well (du/ds = 1 / (2 u))
-                    sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp(up), 0.5f)));
+                    sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp_a(up), 0.5f)));
                     const float2 *d = Df + (size_t)(j - 1) * 4;
                     acc[(j - 1) * kNP + 0] += wgt * cmul(sbar_p, d[0]).y;
                     acc[(j - 1) * kNP + 2] += wgt * cmul(sbar_p, d[1]).y;
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                 sp = sj;
                 gbar = gnext;
             }
-            sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp(up), 0.5f)));
+            sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp_a(up), 0.5f)));
             {
                 const float2 *d = Df + (size_t)(L - 1) * 4;
                 acc[(L - 1) * kNP + 0] += wgt * cmul(sbar_p, d[0]).y;
