@@ -214,7 +214,7 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     if reduce is not None:  # ranks run disjoint soundings: sum the work, take the slowest time
         sec, world_soundings, evals = reduce(sec, n_soundings, evals)
     out = {"value": world_soundings / sec, "unit": "soundings/s", "seconds": sec, "stages": stages,
-           "forward_evals_per_s": evals / sec,
+           "ms_per_stage": sec / stages * 1e3, "forward_evals_per_s": evals / sec,
            "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
                      f"{sweeps} sweeps/stage" + (f" + {n_langevin} Langevin sweeps/stage" if n_langevin else "") +
                      (", stages in one CUDA graph with a device-side loop condition" if graph else "") +
@@ -225,6 +225,25 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
            "mean_p_ip": float(np.mean(post.reshape(n_soundings, kappa_max + 1, lambda_max + 1)[:, :, 1:].sum(axis=(1, 2))))}
     sm.close()
     sysg.close()
+    return out
+
+
+def combine_runs(runs):
+    """Runs of one RJSMC configuration with different seeds: soundings/s over
+    the summed time, with each run's stage count (the number of tempering
+    stages follows the path the sampler takes: 23 to 43 over five seeds of the
+    4 x 4096 Langevin configuration)."""
+    sec = sum(r["seconds"] for r in runs)
+    stages = [r["stages"] for r in runs]
+    out = dict(runs[0])
+    out.update(value=sum(r["value"] * r["seconds"] for r in runs) / sec, seconds=sec, stages=stages,
+               ms_per_stage=sec / sum(stages) * 1e3, seeds=len(runs),
+               forward_evals_per_s=sum(r["forward_evals_per_s"] * r["seconds"] for r in runs) / sec,
+               median_log_bfipd=float(np.median([r["median_log_bfipd"] for r in runs])),
+               mean_p_ip=float(np.mean([r["mean_p_ip"] for r in runs])))
+    if runs[0]["langevin"]:
+        out["langevin"] = dict(runs[-1]["langevin"],
+                               gradient_evals=sum(r["langevin"]["gradient_evals"] for r in runs))
     return out
 
 
@@ -516,10 +535,14 @@ def main():
 
     rjsmc = None
     if not args.no_rjsmc:
+        # the 4-sounding configurations run three seeds each: their stage
+        # counts vary more from one sampler path to another
+        seeds = [rank + world * i for i in range(3)]
         rjsmc = (rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
-                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce),
-                 rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=rank, reduce=reduce,
-                               n_langevin=2),
+                 combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
+                                             reduce=reduce) for sd in seeds]),
+                 combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
+                                             reduce=reduce, n_langevin=2) for sd in seeds]),
                  rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
                                graph=True))
 

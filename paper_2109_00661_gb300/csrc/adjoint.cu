@@ -17,22 +17,30 @@
 // into per-thread accumulators, reduced over the CTA at the end of the model.
 // R_0 is holomorphic in every s_n, so d Im R_0 / dp = Im(dR_0/ds_n ds_n/dp)
 // for the real parameters p.
+//
+// Like the forward kernel, each thread carries two abscissae of one frequency
+// (k and k + K/2) through both passes in 64-bit register pairs on the paired
+// FP32 instructions (f32x2.h); the two abscissae's weighted adjoints are added
+// before they meet the per-(frequency, layer) derivatives ds_n/dp, which do
+// not depend on the abscissa.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "aem_internal.h"
+#include "f32x2.h"
 
 namespace aem {
 namespace {
+
+using namespace f32x2;
 
 constexpr int kGT = 256;
 constexpr int kGW = kGT / 32;
 constexpr int kNP = 5;  // parameters per layer: log10 sigma, log10 h, m, log10 tau, c
 constexpr unsigned kMask = 0xffffffffu;
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// scalar complex helpers of the per-(frequency, layer) Cole-Cole setup
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -41,39 +49,67 @@ __device__ __forceinline__ float2 crcp(float2 a) {
     const float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
     return make_float2(a.x * d, -a.y * d);
 }
-// The per-item passes use the hardware approximations of rcp, rsqrt, ex2,
-// sin and cos (relative error about 2^-22; the FP32 forward kernel uses the
-// same ones), the per-(frequency, layer) Cole-Cole setup the rounded library
-// functions.
-__device__ __forceinline__ float rcp_a(float v) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+
+// paired complex helpers: two abscissae per operation
+__device__ __forceinline__ C2x2 c2(u64 re, u64 im) {
+    C2x2 r;
+    r.re = re;
+    r.im = im;
     return r;
 }
-__device__ __forceinline__ float rsqrt_a(float v) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
+__device__ __forceinline__ C2x2 c2add(C2x2 a, C2x2 b) { return c2(add2(a.re, b.re), add2(a.im, b.im)); }
+__device__ __forceinline__ C2x2 c2neg(C2x2 a) { return c2(sub2(kZero2, a.re), sub2(kZero2, a.im)); }
+__device__ __forceinline__ C2x2 c2add1(C2x2 a) { return c2(add2(kOne2, a.re), a.im); }         // 1 + a
+__device__ __forceinline__ C2x2 c2sub1(C2x2 a) { return c2(sub2(kOne2, a.re), sub2(kZero2, a.im)); }  // 1 - a
+__device__ __forceinline__ C2x2 c2mul(C2x2 a, C2x2 b) {
+    return c2(sub2(mul2(a.re, b.re), mul2(a.im, b.im)), fma2(a.re, b.im, mul2(a.im, b.re)));
 }
-__device__ __forceinline__ float2 crcp_a(float2 a) {
-    const float d = rcp_a(fmaf(a.x, a.x, a.y * a.y));
-    return make_float2(a.x * d, -a.y * d);
+__device__ __forceinline__ C2x2 c2mulc(C2x2 a, C2x2 b) {  // a conj(b)
+    return c2(fma2(a.re, b.re, mul2(a.im, b.im)), sub2(mul2(a.im, b.re), mul2(a.re, b.im)));
 }
-// principal root of x + i y, y > 0: with t = (|z| + |x|) / 2 the pair
-// (sqrt t, y / (2 sqrt t)) is (Re, Im) for x >= 0 and (Im, Re) otherwise
-__device__ __forceinline__ float2 csqrt_a(float x, float y) {
-    const float v = fmaf(x, x, y * y);
-    const float t = 0.5f * fmaf(v, rsqrt_a(v), fabsf(x));
-    const float rr = rsqrt_a(t);
-    const float p = t * rr, o = 0.5f * y * rr;
-    return x >= 0.f ? make_float2(p, o) : make_float2(o, p);
+__device__ __forceinline__ C2x2 c2sq(C2x2 a) {
+    const u64 t = mul2(a.re, a.im);
+    return c2(mul2(sub2(a.re, a.im), add2(a.re, a.im)), add2(t, t));
 }
-__device__ __forceinline__ float2 cexp_a(float2 z) {
-    float s, c, e;
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(z.y));
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(z.y));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z.x * 1.44269504088896341f));
-    return make_float2(e * c, e * s);
+__device__ __forceinline__ C2x2 c2scale(C2x2 a, u64 s) { return c2(mul2(a.re, s), mul2(a.im, s)); }
+__device__ __forceinline__ u64 c2inorm(C2x2 a) {  // 1 / |a|^2
+    float m0, m1;
+    up2(fma2(a.re, a.re, mul2(a.im, a.im)), m0, m1);
+    return pk2(rcp_approx(m0), rcp_approx(m1));
+}
+__device__ __forceinline__ C2x2 c2div(C2x2 x, C2x2 a) { return c2scale(c2mulc(x, a), c2inorm(a)); }
+
+// Principal root u of z = lambda^2 + s (Im s > 0) for both abscissae, and
+// 1 / |z| (= 1 / |u|^2).  With t = (|z| + |x|) / 2 the pair
+// (sqrt t, Im s / (2 sqrt t)) is (Re u, Im u) when x = Re z >= 0 and
+// (Im u, Re u) otherwise.  s = ((Re s, Re s), (Im s, Im s)), y2 = (Im s)^2.
+__device__ __forceinline__ C2x2 c2root(u64 lam2, ulonglong2 s, u64 y2, u64 &inv_mod) {
+    const u64 x = add2(lam2, s.x);
+    const u64 v = fma2(x, x, y2);
+    float v0, v1, x0, x1;
+    up2(v, v0, v1);
+    up2(x, x0, x1);
+    const u64 rv = pk2(rsqrt_approx(v0), rsqrt_approx(v1));  // v = |z|^2
+    inv_mod = rv;
+    const u64 t = mul2(add2(mul2(v, rv), pk2(fabsf(x0), fabsf(x1))), kHalf2);
+    float t0, t1;
+    up2(t, t0, t1);
+    const u64 rr = pk2(rsqrt_approx(t0), rsqrt_approx(t1));
+    float p0, p1, o0, o1;
+    up2(mul2(t, rr), p0, p1);
+    up2(mul2(mul2(s.y, kHalf2), rr), o0, o1);
+    return c2(pk2(x0 >= 0.f ? p0 : o0, x1 >= 0.f ? p1 : o1), pk2(x0 >= 0.f ? o0 : p0, x1 >= 0.f ? o1 : p1));
+}
+
+// E = exp(-2 h u) for both abscissae; he = ((-2 h log2 e) x 2, (-2 h) x 2)
+__device__ __forceinline__ C2x2 c2expm(ulonglong2 he, C2x2 u) {
+    float a0, a1, f0, f1, s0, c0, s1, c1;
+    up2(mul2(he.x, u.re), a0, a1);
+    up2(mul2(he.y, u.im), f0, f1);
+    sincos_approx(f0, &s0, &c0);
+    sincos_approx(f1, &s1, &c1);
+    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
+    return c2(mul2(e, pk2(c0, c1)), mul2(e, pk2(s0, s1)));
 }
 
 template <class T>
@@ -89,13 +125,23 @@ struct GradModels {
     const float *logsig, *logh, *m, *logtau, *c;
 };
 
-// Shared memory (dynamic): S[F*LS] (float2 s), DS[F*LS*4] (float2 ds/dp for
-// log10 sigma, m, log10 tau, c), lamhw[K] (float2 {lambda, weight}),
-// af[F], T[G*F], part[kGW * LS * kNP] (float).
+// Shared memory (dynamic), in order: RS[F*LS] (ulonglong2: (Re s, Re s),
+// (Im s, Im s)), lamp[K2] (ulonglong2: (lam_a^2, lam_b^2), (lam_a, lam_b)),
+// DS[F*LS*4] (float2 ds/dp for log10 sigma, m, log10 tau, c), RY2[F*LS] (u64:
+// (Im s)^2 twice), hwp[K2] (float2 weights of the pair), af[F], T[G*F],
+// part[kGW * LS * kNP] (float).
+size_t grad_smem_bytes(int F, int G, int K, int LS) {
+    const size_t K2 = (size_t)(K + 1) / 2, FL = (size_t)F * LS;
+    return sizeof(ulonglong2) * (FL + K2) + sizeof(float2) * (FL * 4) + sizeof(u64) * FL + sizeof(float2) * K2 +
+           sizeof(float) * ((size_t)F + (size_t)G * F + (size_t)kGW * LS * kNP);
+}
+
 // MAXL: the largest layer count the per-thread arrays hold (10 or
-// AEM_MAX_LAYERS), so the common lmax <= 10 keeps them half as large.
+// AEM_MAX_LAYERS), so the common lmax <= 10 keeps them half as large.  Three
+// resident CTAs per SM (80 registers) measured faster than two (128
+// registers, no spills) and four (64 registers, 200 bytes spilled).
 template <int MAXL>
-__global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS,
+__global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS,
                                                           const float *__restrict__ g_omega,
                                                           const float *__restrict__ g_lam,
                                                           const float *__restrict__ g_hw,
@@ -105,12 +151,17 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
                                                           const float *__restrict__ g_gates, float *__restrict__ grad,
                                                           int *__restrict__ work_counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *S = reinterpret_cast<float2 *>(smem_raw);
-    float2 *DS = S + (size_t)F * LS;
-    float2 *lamhw = DS + (size_t)F * LS * 4;
-    float *af = reinterpret_cast<float *>(lamhw + K);
+    const int K2 = (K + 1) / 2;
+    const size_t FL = (size_t)F * LS;
+    ulonglong2 *RS = reinterpret_cast<ulonglong2 *>(smem_raw);
+    ulonglong2 *lamp = RS + FL;
+    float2 *DS = reinterpret_cast<float2 *>(lamp + K2);
+    u64 *RY2 = reinterpret_cast<u64 *>(DS + FL * 4);
+    float2 *hwp = reinterpret_cast<float2 *>(RY2 + FL);
+    float *af = reinterpret_cast<float *>(hwp + K2);
     float *Ts = af + F;
     float *part = Ts + (size_t)G * F;
+    __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
     __shared__ float thick[AEM_MAX_LAYERS];
     __shared__ float sig_s[AEM_MAX_LAYERS], m_s[AEM_MAX_LAYERS], tau_s[AEM_MAX_LAYERS], c_s[AEM_MAX_LAYERS];
     __shared__ double dldy[AEM_MAX_GATES];
@@ -118,8 +169,14 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float mu0 = (float)kMu0, ln10 = 2.302585092994046f;
     for (int i = tid; i < G * F; i += blockDim.x) Ts[i] = g_T[i];
-    for (int k = tid; k < K; k += blockDim.x) lamhw[k] = make_float2(g_lam[k], g_hw[k]);
-    const int FK = F * K;
+    // abscissa pairs (k, k + K2); an odd K pads the last pair with a zero weight
+    for (int k = tid; k < K2; k += blockDim.x) {
+        const int kb = k + K2 < K ? k + K2 : K - 1;
+        const float la = g_lam[k], lb = g_lam[kb];
+        lamp[k] = make_ulonglong2(pk2(la * la, lb * lb), pk2(la, lb));
+        hwp[k] = make_float2(g_hw[k], k + K2 < K ? g_hw[kb] : 0.f);
+    }
+    const int FK2 = F * K2;
 
     // models are claimed from a counter as CTAs finish them (model costs vary
     // with the layer count, so a fixed stride would leave SMs idle at the end)
@@ -131,7 +188,10 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             sig_s[tid] = exp10f(mv.logsig[o]);
-            thick[tid] = exp10f(mv.logh[o]);
+            const float h = exp10f(mv.logh[o]);
+            thick[tid] = h;
+            const float a = -2.f * 1.44269504088896341f * h, b = -2.f * h;
+            HE[tid] = make_ulonglong2(pk2(a, a), pk2(b, b));
             m_s[tid] = mv.m[o];
             tau_s[tid] = exp10f(mv.logtau[o]);
             c_s[tid] = mv.c[o];
@@ -156,7 +216,9 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
             const float2 dx_dlt = cscale(x, cc * ln10);                   // d x / d log10 tau
             const float2 dx_dc = cmul(x, make_float2(lwt, 1.57079632679489662f));
             const float2 iwm = make_float2(0.f, w * mu0);                 // i w mu0
-            S[(size_t)f * LS + n] = cmul(iwm, sg);
+            const float2 sv = cmul(iwm, sg);
+            RS[(size_t)f * LS + n] = make_ulonglong2(pk2(sv.x, sv.x), pk2(sv.y, sv.y));
+            RY2[(size_t)f * LS + n] = pk2(sv.y * sv.y, sv.y * sv.y);
             float2 *d = DS + ((size_t)f * LS + n) * 4;
             d[0] = cmul(iwm, cscale(sg, ln10));
             d[1] = cmul(iwm, dsg_dm);
@@ -181,111 +243,124 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         }
         __syncthreads();
 
-        // ---- pass 2: reverse sweep per item, per-thread accumulators
+        // ---- reverse sweep per pair of items, per-thread accumulators; the
+        // log10 h entries hold sum w Im(u_j tb_j) until the reduction applies
+        // -2 h_j ln10 (d Gamma_0 / d h_j = -2 u_j tb_j, tb_j as below)
         float acc[MAXL * kNP];
         for (int v = 0; v < L * kNP; ++v) acc[v] = 0.f;
-        // reflection coefficients of the bottom-up pass; with MAXL <= 10 also
-        // its vertical wavenumbers and propagation factors, which the top-down
-        // pass then reuses (for 20 layers the larger stack costs more than the
-        // recomputation saves)
-        constexpr bool kKeep = MAXL <= 10;
-        constexpr int MK = kKeep ? MAXL : 1;
-        float2 Gam[MAXL], Us[MK], Es[MK];
-        int f = tid / K, k = tid - (tid / K) * K;
-        for (int item = tid; item < FK; item += blockDim.x) {
-            const float2 lh = lamhw[k];
-            const float wgt = af[f] * lh.y;
-            const float lam = lh.x, lam2 = lam * lam;
-            const float2 *Sf = S + (size_t)f * LS;
+        C2x2 Gam[MAXL];
+        int f = tid / K2, k = tid - (tid / K2) * K2;
+        for (int item = tid; item < FK2; item += blockDim.x) {
+            const ulonglong2 lp = lamp[k];  // (lam^2 pair, lam pair)
+            const float2 hw = hwp[k];
+            const float a = af[f];
+            const u64 wgt = pk2(a * hw.x, a * hw.y);
+            const ulonglong2 *Sf = RS + (size_t)f * LS;
+            const u64 *Yf = RY2 + (size_t)f * LS;
             const float2 *Df = DS + (size_t)f * LS * 4;
+            const C2x2 air = c2(lp.y, kZero2);  // u of the air: lambda
+            u64 imod;
             // bottom-up: Gamma_j for every interface j
             {
-                float2 sb = Sf[L - 1];
-                float2 ub = csqrt_a(lam2 + sb.x, sb.y);
+                C2x2 ub = c2root(lp.x, Sf[L - 1], Yf[L - 1], imod);
                 for (int j = L - 1; j >= 0; --j) {
-                    if constexpr (kKeep) Us[j] = ub;
-                    const float2 sa = j > 0 ? Sf[j - 1] : make_float2(0.f, 0.f);
-                    const float2 ua = j > 0 ? csqrt_a(lam2 + sa.x, sa.y) : make_float2(lam, 0.f);
-                    const float2 q = cadd(ua, ub);
-                    const float2 rho = cmul(csub(sa, Sf[j]), crcp_a(cmul(q, q)));
+                    const ulonglong2 sb = Sf[j];
+                    C2x2 ua, dsab;  // u above the interface; s above minus s below
+                    if (j > 0) {
+                        const ulonglong2 sa = Sf[j - 1];
+                        ua = c2root(lp.x, sa, Yf[j - 1], imod);
+                        dsab = c2(sub2(sa.x, sb.x), sub2(sa.y, sb.y));
+                    } else {
+                        ua = air;
+                        dsab = c2(sub2(kZero2, sb.x), sub2(kZero2, sb.y));
+                    }
+                    const C2x2 rho = c2div(dsab, c2sq(c2add(ua, ub)));
                     if (j == L - 1) {
                         Gam[j] = rho;
                     } else {
-                        const float2 E = cexp_a(cscale(ub, -2.f * thick[j]));
-                        if constexpr (kKeep) Es[j] = E;
-                        const float2 b = cmul(Gam[j + 1], E);
-                        Gam[j] = cmul(cadd(rho, b), crcp_a(cadd(make_float2(1.f, 0.f), cmul(rho, b))));
+                        const C2x2 b = c2mul(Gam[j + 1], c2expm(HE[j], ub));
+                        Gam[j] = c2div(c2add(rho, b), c2add1(c2mul(rho, b)));
                     }
                     ub = ua;
                 }
             }
-            // top-down: adjoints
-            float2 gbar = make_float2(1.f, 0.f);
-            float2 up = make_float2(lam, 0.f), sp = make_float2(0.f, 0.f);
-            float2 ubar_p = make_float2(0.f, 0.f), sbar_p = make_float2(0.f, 0.f);
+            // top-down: adjoints.  gbar = d Gamma_0 / d Gamma_j; sbar_p, ubar_p
+            // collect d Gamma_0 / d s_{j-1}, d / d u_{j-1} of the layer above
+            C2x2 gbar = c2(kOne2, kZero2), up = air, sbar_p = c2(kZero2, kZero2), ubar_p = sbar_p;
+            u64 imod_up = kZero2;
+            ulonglong2 sp = make_ulonglong2(kZero2, kZero2);
+            C2x2 uj = c2root(lp.x, Sf[0], Yf[0], imod);
             for (int j = 0; j < L; ++j) {
-                const float2 sj = Sf[j];
-                float2 uj;
-                if constexpr (kKeep)
-                    uj = Us[j];
-                else
-                    uj = csqrt_a(lam2 + sj.x, sj.y);
-                const float2 q = cadd(up, uj);
-                const float2 iq = crcp_a(q);
-                const float2 iq2 = cmul(iq, iq);
-                const float2 rho = cmul(csub(sp, sj), iq2);
-                float2 rbar, ubar_j = make_float2(0.f, 0.f), gnext = make_float2(0.f, 0.f);
+                const ulonglong2 sj = Sf[j];
+                const C2x2 q = c2add(up, uj);
+                const u64 iqn = c2inorm(q);
+                const C2x2 iq = c2(mul2(q.re, iqn), mul2(sub2(kZero2, q.im), iqn));  // 1 / q
+                const C2x2 iq2 = c2sq(iq);
+                const C2x2 rho = c2mul(c2(sub2(sp.x, sj.x), sub2(sp.y, sj.y)), iq2);
+                C2x2 rbar, ubar_j = c2(kZero2, kZero2), gnext = ubar_j;
                 if (j < L - 1) {
-                    const float h = thick[j];
-                    float2 E;
-                    if constexpr (kKeep)
-                        E = Es[j];
-                    else
-                        E = cexp_a(cscale(uj, -2.f * h));
-                    const float2 Gn = Gam[j + 1];
-                    const float2 b = cmul(Gn, E);
-                    const float2 iden = crcp_a(cadd(make_float2(1.f, 0.f), cmul(rho, b)));
-                    const float2 iden2 = cmul(iden, iden);
-                    rbar = cmul(gbar, cmul(csub(make_float2(1.f, 0.f), cmul(b, b)), iden2));
-                    const float2 tbar = cmul(gbar, cmul(csub(make_float2(1.f, 0.f), cmul(rho, rho)), iden2));
-                    const float2 Ebar = cmul(tbar, Gn);
-                    gnext = cmul(tbar, E);
-                    // d Gamma_0 / d h_j = Ebar (-2 u_j E);  d / d log10 h = h ln10 d / d h
-                    const float2 hbar = cmul(Ebar, cscale(cmul(uj, E), -2.f));
-                    acc[j * kNP + 1] += wgt * hbar.y * h * ln10;
-                    ubar_j = cmul(Ebar, cscale(E, -2.f * h));
+                    const ulonglong2 he = HE[j];
+                    const C2x2 E = c2expm(he, uj);
+                    const C2x2 b = c2mul(Gam[j + 1], E);
+                    // d Gamma_j / d rho = (1 - b^2) / den^2, d Gamma_j / d b = (1 - rho^2) / den^2
+                    const C2x2 g2 = c2div(gbar, c2sq(c2add1(c2mul(rho, b))));
+                    rbar = c2mul(g2, c2sub1(c2sq(b)));
+                    const C2x2 tbar = c2mul(g2, c2sub1(c2sq(rho)));
+                    // tb = tbar b = (d Gamma_0 / d E_j) E_j: d / d u_j through E_j is -2 h tb
+                    const C2x2 tb = c2mul(tbar, b);
+                    gnext = c2mul(tbar, E);
+                    float h0, h1;
+                    up2(mul2(wgt, fma2(uj.re, tb.im, mul2(uj.im, tb.re))), h0, h1);
+                    acc[j * kNP + 1] += h0 + h1;
+                    ubar_j = c2scale(tb, he.y);
                 } else {
                     rbar = gbar;
                 }
-                const float2 dq = cmul(rbar, cmul(cscale(rho, -2.f), iq));  // d rho / d u_{j-1} = d rho / d u_j
+                // d rho / d u_{j-1} = d rho / d u_j = -2 rho / q; d rho / d s_{j-1} = 1 / q^2 = -d rho / d s_j
+                const C2x2 rq = c2mul(rho, iq);
+                const C2x2 dq = c2mul(rbar, c2(sub2(kZero2, add2(rq.re, rq.re)), sub2(kZero2, add2(rq.im, rq.im))));
+                const C2x2 rbi = c2mul(rbar, iq2);
                 if (j > 0) {
-                    sbar_p = cadd(sbar_p, cmul(rbar, iq2));
-                    ubar_p = cadd(ubar_p, dq);
-                    // layer j-1 complete: s enters through u as well (du/ds = 1 / (2 u))
-                    sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp_a(up), 0.5f)));
-                    const float2 *d = Df + (size_t)(j - 1) * 4;
-                    acc[(j - 1) * kNP + 0] += wgt * cmul(sbar_p, d[0]).y;
-                    acc[(j - 1) * kNP + 2] += wgt * cmul(sbar_p, d[1]).y;
-                    acc[(j - 1) * kNP + 3] += wgt * cmul(sbar_p, d[2]).y;
-                    acc[(j - 1) * kNP + 4] += wgt * cmul(sbar_p, d[3]).y;
+                    // layer j-1 complete: s enters through u as well, du/ds = 1 / (2 u) = conj(u) / (2 |z|)
+                    ubar_p = c2add(ubar_p, dq);
+                    sbar_p = c2add(c2add(sbar_p, rbi), c2scale(c2mulc(ubar_p, up), mul2(imod_up, kHalf2)));
+                    float x0, x1, y0, y1;
+                    up2(mul2(wgt, sbar_p.re), x0, x1);
+                    up2(mul2(wgt, sbar_p.im), y0, y1);
+                    const float swx = x0 + x1, swy = y0 + y1;
+                    const float4 *d = reinterpret_cast<const float4 *>(Df + (size_t)(j - 1) * 4);
+                    const float4 d01 = d[0], d23 = d[1];
+                    float *ac = acc + (j - 1) * kNP;
+                    ac[0] += fmaf(swx, d01.y, swy * d01.x);
+                    ac[2] += fmaf(swx, d01.w, swy * d01.z);
+                    ac[3] += fmaf(swx, d23.y, swy * d23.x);
+                    ac[4] += fmaf(swx, d23.w, swy * d23.z);
                 }
-                sbar_p = cscale(cmul(rbar, iq2), -1.f);
-                ubar_p = cadd(ubar_j, dq);
+                sbar_p = c2neg(rbi);
+                ubar_p = c2add(ubar_j, dq);
                 up = uj;
+                imod_up = imod;
                 sp = sj;
                 gbar = gnext;
+                if (j + 1 < L) uj = c2root(lp.x, Sf[j + 1], Yf[j + 1], imod);
             }
-            sbar_p = cadd(sbar_p, cmul(ubar_p, cscale(crcp_a(up), 0.5f)));
             {
-                const float2 *d = Df + (size_t)(L - 1) * 4;
-                acc[(L - 1) * kNP + 0] += wgt * cmul(sbar_p, d[0]).y;
-                acc[(L - 1) * kNP + 2] += wgt * cmul(sbar_p, d[1]).y;
-                acc[(L - 1) * kNP + 3] += wgt * cmul(sbar_p, d[2]).y;
-                acc[(L - 1) * kNP + 4] += wgt * cmul(sbar_p, d[3]).y;
+                sbar_p = c2add(sbar_p, c2scale(c2mulc(ubar_p, up), mul2(imod_up, kHalf2)));
+                float x0, x1, y0, y1;
+                up2(mul2(wgt, sbar_p.re), x0, x1);
+                up2(mul2(wgt, sbar_p.im), y0, y1);
+                const float swx = x0 + x1, swy = y0 + y1;
+                const float4 *d = reinterpret_cast<const float4 *>(Df + (size_t)(L - 1) * 4);
+                const float4 d01 = d[0], d23 = d[1];
+                float *ac = acc + (L - 1) * kNP;
+                ac[0] += fmaf(swx, d01.y, swy * d01.x);
+                ac[2] += fmaf(swx, d01.w, swy * d01.z);
+                ac[3] += fmaf(swx, d23.y, swy * d23.x);
+                ac[4] += fmaf(swx, d23.w, swy * d23.z);
             }
             k += blockDim.x;
-            while (k >= K) {
-                k -= K;
+            while (k >= K2) {
+                k -= K2;
                 ++f;
             }
         }
@@ -297,8 +372,10 @@ __global__ void __launch_bounds__(kGT) loglik_grad_kernel(GradModels mv, int F, 
         __syncthreads();
         for (int v = tid; v < mv.lmax * kNP; v += blockDim.x) {
             float s = 0.f;
-            if (v < L * kNP)
+            if (v < L * kNP) {
                 for (int w = 0; w < kGW; ++w) s += part[w * LS * kNP + v];
+                if (v % kNP == 1) s *= -2.f * thick[v / kNP] * ln10;
+            }
             grad[(size_t)p * mv.lmax * kNP + v] = s;
         }
     }
@@ -318,8 +395,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     if (h.cc_form != AEM_CC_PAPER)
         return fail(AEM_ERR_UNSUPPORTED, "aem_loglik_grad_f32: only the paper's Cole-Cole form is differentiated");
     const int LS = models->lmax;
-    const size_t smem = sizeof(float2) * ((size_t)h.F * LS * 5 + h.K) +
-                        sizeof(float) * ((size_t)h.F + (size_t)h.G * h.F + (size_t)kGW * LS * kNP);
+    const size_t smem = grad_smem_bytes(h.F, h.G, h.K, LS);
     auto kern = LS <= 10 ? loglik_grad_kernel<10> : loglik_grad_kernel<AEM_MAX_LAYERS>;
     if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "aem_internal.h"
+#include "f32x2.h"
 
 namespace aem {
 namespace {
@@ -350,59 +351,7 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
 //   t = |x + i y| + |x|, rr = rsqrt(t); (t rr, y rr) is (Re w, Im w) when
 //   x >= 0 and (Im w, Re w) otherwise.
 // The Moebius step (N, D) <- (r D + N E, D + r N E) keeps R_0 = N / D.
-typedef unsigned long long u64;
-
-__device__ __forceinline__ float rsqrt_approx(float v) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ float rcp_approx(float v) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ float ex2_approx(float v) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ void sincos_approx(float v, float *s, float *c) {
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(v));
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(v));
-}
-__device__ __forceinline__ u64 pk2(float a, float b) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void up2(u64 r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-struct C2x2 {  // two complex numbers: re = (re_a, re_b), im = (im_a, im_b)
-    u64 re, im;
-};
+using namespace f32x2;  // paired FP32 helpers and the hardware approximations (f32x2.h)
 
 // w for both abscissae; sxx = (Re s, Re s), yyy = (Im s ^2, ...), syy = (Im s, Im s)
 __device__ __forceinline__ C2x2 wroot2(u64 lam2, u64 sxx, u64 yyy, u64 syy) {

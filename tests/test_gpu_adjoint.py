@@ -120,6 +120,39 @@ def test_gradient_zero_padding_and_unsupported_form(setup):
         L.loglik_grad_f32(pel, I.to_torch(near_truth(2, seed=4), torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
 
 
+def many_layers(P, seed, L):
+    rng = np.random.default_rng(seed)
+    m = dict(nlayers=np.full(P, L, dtype=np.int8),
+             logsig=rng.uniform(-3.0, -1.0, (P, L)),
+             logh=np.log10(rng.uniform(5.0, 40.0, (P, L))),
+             m=rng.uniform(0.05, 0.5, (P, L)),
+             logtau=-3.0 + rng.uniform(-0.3, 0.3, (P, L)),
+             c=rng.uniform(0.3, 0.9, (P, L)))
+    for k in ("logsig", "logh", "m", "logtau", "c"):
+        m[k] = m[k].astype(np.float32).astype(np.float64)
+    return m
+
+
+def test_gradient_beyond_ten_layers(setup):
+    """lmax > 10 takes the kernel built for AEM_MAX_LAYERS layers: 14-layer
+    models against the oracle's central differences, and 3-layer models padded
+    to lmax 19 give the gradient of the same models at lmax 3."""
+    torch, L, sysg, s, y_obs = setup
+    models = many_layers(6, seed=8, L=14)
+    ll_ref, g_ref = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN)
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    g = g.cpu().numpy().astype(np.float64)
+    y_model, _, _, kap = oracle_ref(models, NAME)
+    _, J = O.forward_jacobian_fd(models, s)
+    check(g, g_ref, "14 layers vs oracle FD", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+    small = near_truth(5, seed=6, L=3)
+    padded = {k: (np.concatenate([v, np.zeros((5, 16))], axis=1) if k != "nlayers" else v) for k, v in small.items()}
+    _, g3 = L.loglik_grad_f32(sysg, I.to_torch(small, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    _, g19 = L.loglik_grad_f32(sysg, I.to_torch(padded, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    assert g19.shape[1] == 19 and torch.all(g19[:, 3:, :] == 0)
+    assert torch.allclose(g19[:, :3, :], g3, rtol=1e-6, atol=0)
+
+
 def test_autograd_function(setup):
     """The torch.autograd.Function path returns the adjoint kernel's gradient,
     scaled by the upstream gradient, on every parameter tensor."""
