@@ -399,8 +399,8 @@ int smc_set_particles(smc_state *st, const smc_particles_host *h, const double *
  *   log nu = gamma_t l_i - log( (1/(t+1)) sum_{l=0}^{t} exp(gamma_l l_i - log Z_{l,k}) )
  * over every stage's gamma and log Z (at most 1024 stages); a model is
  * fitted when its current population holds at least two particles.  The
- * history takes H x P particle records of device memory and is not part of a
- * checkpoint (smc_checkpoint returns AEM_ERR_UNSUPPORTED while recycling).
+ * history takes H x P particle records of device memory; a checkpoint
+ * carries it.
  * With desc.zca = p > 0 a birth or death uses, with probability p (a draw
  * independent of the state) and when the target model (birth) or the current
  * model (death) has a fit, Appendix F's ZCA-coloured move: the new layer's
@@ -438,14 +438,20 @@ int smc_ppd(smc_state *st, double *mean, double *var, double *z, float *gates_ho
 /* Checkpoint / resume.  smc_checkpoint writes a self-describing image of the
  * sampler's dynamic state (current particles with their log-likelihoods,
  * gamma, log Z_k, stage counter, Langevin steps, the previous stage's
- * acceptance counts that set R_t) into the caller's host buffer: with
- * buf == NULL it only stores the image size in *size; otherwise *size is the
- * buffer's capacity on entry (AEM_ERR_INVALID_ARG if too small) and the
- * image's size on return.  Synchronous.  smc_restore loads such an image into
- * a sampler created with the same n_soundings, n_particles, kappa_max and
- * lambda_max (AEM_ERR_INVALID_ARG otherwise, or for a damaged or truncated
- * image); the random streams are counter-based, so resuming reproduces the
- * uninterrupted run exactly when the descriptors match. */
+ * acceptance counts that set R_t; with desc.adaptive the proposal scale of
+ * every (sounding, model), on which the next stage's bisection is centred;
+ * with desc.recycle_stages = H the H history slots and the gamma and log Z_k
+ * of every stage so far) into the caller's host buffer: with buf == NULL it
+ * only stores the image size in *size; otherwise *size is the buffer's
+ * capacity on entry (AEM_ERR_INVALID_ARG if too small) and the image's size
+ * on return.  Take it between stages (after smc_mutate or smc_run returns):
+ * the adaptive fit itself is rebuilt at the start of the next stage's
+ * sweeps.  Synchronous.  smc_restore loads such an image into a sampler
+ * created with the same n_soundings, n_particles, kappa_max, lambda_max,
+ * adaptive flag and recycling window (AEM_ERR_INVALID_ARG otherwise, or for a
+ * damaged or truncated image); the random streams are counter-based, so
+ * resuming reproduces the uninterrupted run exactly when the descriptors
+ * match. */
 int smc_checkpoint(const smc_state *st, void *buf, size_t *size);
 int smc_restore(smc_state *st, const void *buf, size_t size);
 

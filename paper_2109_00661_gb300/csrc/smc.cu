@@ -2169,24 +2169,38 @@ extern "C" int smc_langevin_stats(const smc_state *st, int *accepted, int *propo
 }
 
 // ------------------------------------------------------ checkpoint / restore
-// Image layout (little-endian host order, version 1): a fixed header, then the
+// Image layout (little-endian host order, version 2): a fixed header, then the
 // current particles (kappa, lam int32 [P]; phib, tau, c float [P]; zc, phic,
 // zm, mv float [P][SLOTS]; ll double [P]), gamma [S], log Z [S][M], Langevin
 // step [S] (doubles), and the previous stage's acceptance counts [S][6] x 2
-// (int32, valid when have_prev).
+// (int32, valid when have_prev).  With the adaptive proposal follows the
+// scale a_k of every (sounding, model) [S][M] (double: the next stage's
+// bisection is centred on it; the fit itself is rebuilt at the start of the
+// next stage's sweeps).  With particle recycling follow the H history slots
+// (H x P particle records in the layout of the current particles) and the
+// gamma [S][t+1] and log Z [S][t+1][M] of stages 0..t, t the stage counter.
 namespace {
 constexpr char kCkptMagic[8] = {'A', 'E', 'M', 'S', 'M', 'C', 'C', 'K'};
+constexpr int32_t kCkptVersion = 2;
 struct CkptHeader {
     char magic[8];
     int32_t version, S, N, M, kappa_max, lambda_max, stage, have_prev;
+    int32_t adaptive, recycle_stages, reserved0, reserved1;
     uint64_t seed;
     uint64_t payload_bytes;
 };
 
-size_t ckpt_payload(const smc_state *st) {
-    const size_t P = st->P, S = st->S;
-    return P * (2 * sizeof(int32_t) + 3 * sizeof(float) + 4 * KS * sizeof(float) + sizeof(double)) +
-           S * (2 + st->M) * sizeof(double) + 2 * S * kMoves * sizeof(int32_t);
+size_t particle_bytes(size_t n) {
+    return n * (2 * sizeof(int32_t) + 3 * sizeof(float) + 4 * KS * sizeof(float) + sizeof(double));
+}
+
+size_t ckpt_payload(const smc_state *st, int stage) {
+    const size_t S = st->S, M = st->M;
+    size_t b = particle_bytes(st->P) + S * (2 + M) * sizeof(double) + 2 * S * kMoves * sizeof(int32_t);
+    if (st->d.adaptive) b += S * M * sizeof(double);
+    if (st->d.recycle_stages > 0)
+        b += particle_bytes((size_t)st->d.recycle_stages * st->P) + S * (size_t)(stage + 1) * (1 + M) * sizeof(double);
+    return b;
 }
 
 template <class T>
@@ -2202,14 +2216,50 @@ int h2d(T *dst, const unsigned char *&i, size_t n, cudaStream_t s) {
     i += n * sizeof(T);
     return AEM_OK;
 }
+
+int particles_d2h(unsigned char *&o, const PState &c, size_t n, cudaStream_t s) {
+    int rc;
+    if ((rc = d2h(o, c.kappa, n, s)) || (rc = d2h(o, c.lam, n, s)) || (rc = d2h(o, c.phib, n, s)) ||
+        (rc = d2h(o, c.tau, n, s)) || (rc = d2h(o, c.c, n, s)) || (rc = d2h(o, c.zc, n * KS, s)) ||
+        (rc = d2h(o, c.phic, n * KS, s)) || (rc = d2h(o, c.zm, n * KS, s)) || (rc = d2h(o, c.mv, n * KS, s)) ||
+        (rc = d2h(o, c.ll, n, s)))
+        return rc;
+    return AEM_OK;
+}
+
+int particles_h2d(const PState &c, const unsigned char *&i, size_t n, cudaStream_t s) {
+    int rc;
+    if ((rc = h2d(c.kappa, i, n, s)) || (rc = h2d(c.lam, i, n, s)) || (rc = h2d(c.phib, i, n, s)) ||
+        (rc = h2d(c.tau, i, n, s)) || (rc = h2d(c.c, i, n, s)) || (rc = h2d(c.zc, i, n * KS, s)) ||
+        (rc = h2d(c.phic, i, n * KS, s)) || (rc = h2d(c.zm, i, n * KS, s)) || (rc = h2d(c.mv, i, n * KS, s)) ||
+        (rc = h2d(c.ll, i, n, s)))
+        return rc;
+    return AEM_OK;
+}
+
+// rows of a [S][kMaxRecycleStages][w] device array, the first `cols` entries
+// (of w doubles) of each sounding's row, packed on the host
+int hist_rows_d2h(unsigned char *&o, const double *src, size_t S, size_t cols, size_t w, cudaStream_t s) {
+    const size_t width = cols * w * sizeof(double);
+    AEM_CUDA_TRY(cudaMemcpy2DAsync(o, width, src, (size_t)kMaxRecycleStages * w * sizeof(double), width, S,
+                                   cudaMemcpyDeviceToHost, s));
+    o += width * S;
+    return AEM_OK;
+}
+
+int hist_rows_h2d(double *dst, const unsigned char *&i, size_t S, size_t cols, size_t w, cudaStream_t s) {
+    const size_t width = cols * w * sizeof(double);
+    AEM_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)kMaxRecycleStages * w * sizeof(double), i, width, width, S,
+                                   cudaMemcpyHostToDevice, s));
+    i += width * S;
+    return AEM_OK;
+}
 }  // namespace
 
 extern "C" int smc_checkpoint(const smc_state *cst, void *buf, size_t *size) {
     smc_state *st = const_cast<smc_state *>(cst);
     if (!st || !size) return fail(AEM_ERR_INVALID_ARG, "smc_checkpoint: NULL state or size");
-    if (st->d.recycle_stages > 0)
-        return fail(AEM_ERR_UNSUPPORTED, "smc_checkpoint: the recycling history is not part of the image");
-    const size_t need = sizeof(CkptHeader) + ckpt_payload(st);
+    const size_t need = sizeof(CkptHeader) + ckpt_payload(st, st->stage);
     if (!buf) {
         *size = need;
         return AEM_OK;
@@ -2217,7 +2267,7 @@ extern "C" int smc_checkpoint(const smc_state *cst, void *buf, size_t *size) {
     if (*size < need) return fail(AEM_ERR_INVALID_ARG, "smc_checkpoint: buffer smaller than the image");
     CkptHeader h{};
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = kCkptVersion;
     h.S = st->S;
     h.N = st->N;
     h.M = st->M;
@@ -2225,27 +2275,35 @@ extern "C" int smc_checkpoint(const smc_state *cst, void *buf, size_t *size) {
     h.lambda_max = st->d.lambda_max;
     h.stage = st->stage;
     h.have_prev = st->have_prev ? 1 : 0;
+    h.adaptive = st->d.adaptive ? 1 : 0;
+    h.recycle_stages = st->d.recycle_stages;
     h.seed = st->d.seed;
-    h.payload_bytes = ckpt_payload(st);
+    h.payload_bytes = ckpt_payload(st, st->stage);
     unsigned char *o = (unsigned char *)buf;
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
-    const size_t P = st->P, S = st->S;
-    const PState c = st->cur;
+    const size_t P = st->P, S = st->S, M = st->M;
     cudaStream_t sm = st->stream;
     int rc;
-    if ((rc = d2h(o, c.kappa, P, sm)) || (rc = d2h(o, c.lam, P, sm)) || (rc = d2h(o, c.phib, P, sm)) ||
-        (rc = d2h(o, c.tau, P, sm)) || (rc = d2h(o, c.c, P, sm)) || (rc = d2h(o, c.zc, P * KS, sm)) ||
-        (rc = d2h(o, c.phic, P * KS, sm)) || (rc = d2h(o, c.zm, P * KS, sm)) || (rc = d2h(o, c.mv, P * KS, sm)) ||
-        (rc = d2h(o, c.ll, P, sm)) || (rc = d2h(o, st->gamma, S, sm)) || (rc = d2h(o, st->logz, S * st->M, sm)) ||
-        (rc = d2h(o, st->lang_h, S, sm)))
+    if ((rc = particles_d2h(o, st->cur, P, sm)) || (rc = d2h(o, st->gamma, S, sm)) ||
+        (rc = d2h(o, st->logz, S * M, sm)) || (rc = d2h(o, st->lang_h, S, sm)))
         return rc;
+    unsigned char *counts = o;
+    o += 2 * S * kMoves * sizeof(int32_t);
+    if (st->d.adaptive && (rc = d2h(o, st->pca_a, S * M, sm))) return rc;
+    if (st->d.recycle_stages > 0) {
+        const size_t cols = (size_t)st->stage + 1;
+        if ((rc = particles_d2h(o, st->hist, (size_t)st->d.recycle_stages * P, sm)) ||
+            (rc = hist_rows_d2h(o, st->gamma_hist, S, cols, 1, sm)) ||
+            (rc = hist_rows_d2h(o, st->logz_hist, S, cols, M, sm)))
+            return rc;
+    }
     AEM_CUDA_TRY(cudaStreamSynchronize(sm));
     const size_t nc = S * kMoves;
     for (size_t q = 0; q < nc; ++q) {
         const int32_t a = st->have_prev ? st->acc_prev[q] : 0, b = st->have_prev ? st->nprop_prev[q] : 0;
-        std::memcpy(o + q * sizeof(int32_t), &a, sizeof a);
-        std::memcpy(o + (nc + q) * sizeof(int32_t), &b, sizeof b);
+        std::memcpy(counts + q * sizeof(int32_t), &a, sizeof a);
+        std::memcpy(counts + (nc + q) * sizeof(int32_t), &b, sizeof b);
     }
     *size = need;
     return AEM_OK;
@@ -2256,32 +2314,42 @@ extern "C" int smc_restore(smc_state *st, const void *buf, size_t size) {
     CkptHeader h{};
     if (size < sizeof h) return fail(AEM_ERR_INVALID_ARG, "smc_restore: buffer shorter than the header");
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
-        return fail(AEM_ERR_INVALID_ARG, "smc_restore: not a version-1 sampler checkpoint");
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion)
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: not a version-2 sampler checkpoint");
     if (h.S != st->S || h.N != st->N || h.M != st->M || h.kappa_max != st->d.kappa_max ||
         h.lambda_max != st->d.lambda_max)
         return fail(AEM_ERR_INVALID_ARG, "smc_restore: checkpoint sizes differ from this sampler's");
-    if (h.payload_bytes != ckpt_payload(st) || size < sizeof h + h.payload_bytes)
+    if (h.adaptive != (st->d.adaptive ? 1 : 0) || h.recycle_stages != st->d.recycle_stages)
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: adaptive proposal or recycling window differs from this sampler's");
+    if (h.stage < 0 || (h.recycle_stages > 0 && h.stage >= kMaxRecycleStages))
+        return fail(AEM_ERR_INVALID_ARG, "smc_restore: stage counter out of range");
+    if (h.payload_bytes != ckpt_payload(st, h.stage) || size < sizeof h + h.payload_bytes)
         return fail(AEM_ERR_INVALID_ARG, "smc_restore: truncated checkpoint");
     const unsigned char *i = (const unsigned char *)buf + sizeof h;
-    const size_t P = st->P, S = st->S;
-    const PState c = st->cur;
+    const size_t P = st->P, S = st->S, M = st->M;
     cudaStream_t sm = st->stream;
     AEM_CUDA_TRY(cudaStreamSynchronize(sm));
     int rc;
-    if ((rc = h2d(c.kappa, i, P, sm)) || (rc = h2d(c.lam, i, P, sm)) || (rc = h2d(c.phib, i, P, sm)) ||
-        (rc = h2d(c.tau, i, P, sm)) || (rc = h2d(c.c, i, P, sm)) || (rc = h2d(c.zc, i, P * KS, sm)) ||
-        (rc = h2d(c.phic, i, P * KS, sm)) || (rc = h2d(c.zm, i, P * KS, sm)) || (rc = h2d(c.mv, i, P * KS, sm)) ||
-        (rc = h2d(c.ll, i, P, sm)) || (rc = h2d(st->gamma, i, S, sm)) || (rc = h2d(st->logz, i, S * st->M, sm)) ||
-        (rc = h2d(st->lang_h, i, S, sm)))
+    if ((rc = particles_h2d(st->cur, i, P, sm)) || (rc = h2d(st->gamma, i, S, sm)) ||
+        (rc = h2d(st->logz, i, S * M, sm)) || (rc = h2d(st->lang_h, i, S, sm)))
         return rc;
+    const unsigned char *counts = i;
+    i += 2 * S * kMoves * sizeof(int32_t);
+    if (st->d.adaptive && (rc = h2d(st->pca_a, i, S * M, sm))) return rc;
+    if (st->d.recycle_stages > 0) {
+        const size_t cols = (size_t)h.stage + 1;
+        if ((rc = particles_h2d(st->hist, i, (size_t)st->d.recycle_stages * P, sm)) ||
+            (rc = hist_rows_h2d(st->gamma_hist, i, S, cols, 1, sm)) ||
+            (rc = hist_rows_h2d(st->logz_hist, i, S, cols, M, sm)))
+            return rc;
+    }
     AEM_CUDA_TRY(cudaStreamSynchronize(sm));
     const size_t nc = S * kMoves;
     st->acc_prev.assign(nc, 0);
     st->nprop_prev.assign(nc, 0);
     for (size_t q = 0; q < nc; ++q) {
-        std::memcpy(&st->acc_prev[q], i + q * sizeof(int32_t), sizeof(int32_t));
-        std::memcpy(&st->nprop_prev[q], i + (nc + q) * sizeof(int32_t), sizeof(int32_t));
+        std::memcpy(&st->acc_prev[q], counts + q * sizeof(int32_t), sizeof(int32_t));
+        std::memcpy(&st->nprop_prev[q], counts + (nc + q) * sizeof(int32_t), sizeof(int32_t));
     }
     st->have_prev = h.have_prev != 0;
     st->stage = h.stage;

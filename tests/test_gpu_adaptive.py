@@ -212,8 +212,8 @@ def test_recycled_fit_matches_oracle(env):
             n_checked += 1
         sm.mutate(3)
     assert n_checked >= 20
-    with pytest.raises(Exception):
-        sm.checkpoint()
+    # the image carries the recycling history (resume is tested in test_gpu_checkpoint.py)
+    assert len(sm.checkpoint()) > 3 * sm.P * 8
 
 
 @pytest.mark.parametrize("zca", [1.0, 0.5])

@@ -23,9 +23,15 @@ def env():
     return S, gsys, np.stack([data, I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=1)])
 
 
-def make(S, gsys, data, N=128):
+def make(S, gsys, data, N=128, **extra):
     return S.SMC(gsys, data, I.EPS_AN, I.EPS_MN, n_particles=N, n_soundings=2, kappa_max=3, lambda_max=4, seed=21,
-                 r_max=6, n_langevin=1)
+                 r_max=6, n_langevin=1, **extra)
+
+
+# the fixed-scale sampler, and the adaptive proposal with particle recycling
+# (3 history slots) and the ZCA-coloured birth / death: the image then carries
+# the proposal scales and the recycling history as well
+MODES = {"fixed": {}, "adaptive_recycling_zca": dict(adaptive=1, recycle_stages=3, zca=0.5)}
 
 
 def stages(sm, n):
@@ -44,18 +50,23 @@ def snapshot(sm):
                 ll=p.ll, lz=lz, gamma=st["gamma"], stage=st["stage"], acc=st["accepted"], h=h)
 
 
-def test_resume_reproduces_the_uninterrupted_run(env):
+@pytest.mark.parametrize("mode", list(MODES))
+def test_resume_reproduces_the_uninterrupted_run(env, mode):
     S, gsys, data = env
-    a = make(S, gsys, data)
+    a = make(S, gsys, data, **MODES[mode])
     a.init()
     stages(a, 3)
     image = a.checkpoint()
     stages(a, 4)
     ref = snapshot(a)
-    b = make(S, gsys, data)
+    if MODES[mode]:
+        ref.update(a.adaptation())
+    b = make(S, gsys, data, **MODES[mode])
     b.restore(image)
     stages(b, 4)
     got = snapshot(b)
+    if MODES[mode]:
+        got.update(b.adaptation())
     for k in ref:
         assert np.array_equal(np.asarray(got[k]), np.asarray(ref[k])), k
     assert ref["stage"] == 7
@@ -73,4 +84,7 @@ def test_restore_refuses_bad_images(env):
     other = make(S, gsys, data, N=64)
     with pytest.raises(Exception):
         other.restore(image)
+    adaptive = make(S, gsys, data, adaptive=1, recycle_stages=3)
+    with pytest.raises(Exception):  # a sampler with another proposal / history layout
+        adaptive.restore(image)
     a.restore(image)  # the intact image still loads
