@@ -13,7 +13,7 @@ import pytest
 
 import oracle as O
 from paper_2109_00661_gb300 import inputs as I
-from parity_util import bound32, gradient_bound, loglik_bound, oracle_ref, oracle_system
+from parity_util import bound32, gradient_bound, kappa, loglik_bound, oracle_ref, oracle_system
 
 pytestmark = pytest.mark.gpu
 
@@ -151,6 +151,21 @@ def test_gradient_beyond_ten_layers(setup):
     _, g19 = L.loglik_grad_f32(sysg, I.to_torch(padded, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
     assert g19.shape[1] == 19 and torch.all(g19[:, 3:, :] == 0)
     assert torch.allclose(g19[:, :3, :], g3, rtol=1e-6, atol=0)
+
+
+def test_gradient_odd_hankel_count(setup):
+    """K = 121: the paired kernel's padded last abscissa pair carries a zero
+    weight and adds nothing."""
+    torch, L, _, s, y_obs = setup
+    sysg = L.System(**dict(I.system_kwargs(NAME), n_hankel=121))
+    s = dict(s, K=121)
+    models = near_truth(8, seed=13, L=3)
+    _, g_ref = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN)
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    y_model, imh, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    _, J = O.forward_jacobian_fd(models, s)
+    kap = kappa(imh, s["T"], y_model, absh)
+    check(g.cpu().numpy().astype(np.float64), g_ref, "K = 121", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
 
 
 def test_autograd_function(setup):

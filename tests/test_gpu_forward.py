@@ -132,6 +132,21 @@ def test_forward_edge_cases(lib, torch_mod):
     assert_within(rel_err(y, y_ref), bound32(kap, sysg.F), "FP32 gates")
 
 
+def test_odd_hankel_count(lib, torch_mod):
+    """An odd K: the FP32 kernel carries the abscissae in pairs (k, k + K/2)
+    and pads the last pair with a zero weight."""
+    name = "sounding-g20-f40-k120"
+    sysg = lib.System(**dict(I.system_kwargs(name), n_hankel=121))
+    s = dict(oracle_system(name), K=121)
+    models = as_f32_inputs(I.random_models(300, seed=5))
+    y, imh = lib.forward_f32(sysg, I.to_torch(models, torch_mod.float32), want_imh=True)
+    y_ref, imh_ref, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    kap = kappa(imh_ref, s["T"], y_ref, absh)
+    imh = imh.cpu().numpy().astype(np.float64)
+    assert spectrum_err(imh, imh_ref, absh).max() < DELTA_S32
+    assert_within(rel_err(y.cpu().numpy().astype(np.float64), y_ref), bound32(kap, sysg.F), "FP32 gates, K = 121")
+
+
 def test_pelton_form(lib, torch_mod):
     name = "sounding-g20-f40-k120"
     models = I.random_models(40, seed=11)
