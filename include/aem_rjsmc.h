@@ -351,15 +351,17 @@ int smc_langevin_stats(const smc_state *st, int *accepted, int *proposed, double
 int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 
 /* smc_run with the stage loop on the device: one stage (reweight,
- * resample, n_sweeps >= 1 sweeps of the fixed-scale moves) is captured once
- * into a CUDA graph as the body of a conditional WHILE node.  A kernel at the
- * end of the body advances nothing on the host; it sets the loop condition
- * from the new gammas (another stage while any sounding's gamma < 1 and fewer
- * than max_stages stages have run), and the stage number lives in device
- * memory.  No host synchronisation happens between stages.  Same results as
- * smc_run(st, max_stages, n_sweeps) bit for bit.  Samplers with the adaptive
- * proposal, Langevin sweeps or recycling return AEM_ERR_UNSUPPORTED.
- * Synchronous; stages_out may be NULL. */
+ * resample, n_sweeps >= 1 sweeps of the moves; with the descriptor's options
+ * also the recycling record, the adaptive fit and scale bisection and the
+ * Langevin sweeps with their step adaptation) is captured once into a CUDA
+ * graph as the body of a conditional WHILE node.  A kernel at the end of the
+ * body advances nothing on the host; it sets the loop condition from the new
+ * gammas (another stage while any sounding's gamma < 1 and fewer than
+ * max_stages stages have run), and the stage number lives in device memory.
+ * No host synchronisation or allocation happens between stages.  Same results
+ * as smc_run(st, max_stages, n_sweeps) bit for bit.  With recycling the stage
+ * counter must stay below 1024 (AEM_ERR_INVALID_ARG otherwise).  Synchronous;
+ * stages_out may be NULL. */
 int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 
 /* Synchronous (a10).  post_k [S x M]: N_k / N; log_bfipd [S]: log of the

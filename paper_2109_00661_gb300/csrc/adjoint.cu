@@ -388,9 +388,14 @@ using namespace aem;
 
 namespace aem {
 
+// scratch layout: the adjoint kernel's claim counter at 0, the forward
+// kernel's at 64, the gates [P][G] from 256
+constexpr size_t kGateOff = 256;
+size_t grad_work_bytes(int n_models, int G) { return kGateOff + sizeof(float) * (size_t)n_models * G; }
+
 int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, void *work_ext) {
     const SystemTables &h = sys->host;
     if (h.cc_form != AEM_CC_PAPER)
         return fail(AEM_ERR_UNSUPPORTED, "aem_loglik_grad_f32: only the paper's Cole-Cole form is differentiated");
@@ -405,13 +410,13 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     if (grid > models->n_models) grid = models->n_models;
     GradModels gm{models->n_models, models->lmax, models->nlayers, models->logsig, models->logh,
                   models->m, models->logtau, models->c};
-    // stream-ordered scratch: the model count for the claim counter, then the gates
-    void *work = nullptr;
-    const size_t gate_off = 256;
-    AEM_CUDA_TRY(cudaMallocAsync(&work, gate_off + sizeof(float) * (size_t)models->n_models * h.G, stream));
+    void *work = work_ext;
+    if (!work_ext) AEM_CUDA_TRY(cudaMallocAsync(&work, grad_work_bytes(models->n_models, h.G), stream));
     int *counter = static_cast<int *>(work);
-    float *gates = reinterpret_cast<float *>(static_cast<char *>(work) + gate_off);
-    int rc = loglik_gates_f32_soundings(sys, models, y_obs, models_per_sounding, eps_an, eps_mn, ll, gates, stream);
+    int *fwd_counter = reinterpret_cast<int *>(static_cast<char *>(work) + 64);
+    float *gates = reinterpret_cast<float *>(static_cast<char *>(work) + kGateOff);
+    int rc = loglik_gates_f32_soundings(sys, models, y_obs, models_per_sounding, eps_an, eps_mn, ll, gates, stream,
+                                        fwd_counter);
     cudaError_t e = cudaSuccess;
     if (rc == AEM_OK) {
         e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
@@ -422,7 +427,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
             e = cudaGetLastError();
         }
     }
-    cudaFreeAsync(work, stream);
+    if (!work_ext) cudaFreeAsync(work, stream);
     if (rc) return rc;
     AEM_CUDA_TRY(e);
     return AEM_OK;

@@ -728,10 +728,11 @@ __device__ inline bool ordered_open(const float *z, int n, double zmax) {
 // valid when theta' is inside the uniform prior support with ordered
 // interfaces; lq = log q(theta' | theta) = -|xi|^2 / 2 (+ const).
 __global__ void langevin_propose_kernel(PState cur, PState prop, const float *gcur, const double *gamma,
-                                        const double *lang_h, Params pr, int stage, int sweep, int8_t *valid_out,
-                                        double *lq) {
+                                        const double *lang_h, Params pr, int stage_arg, int sweep, int8_t *valid_out,
+                                        double *lq, const int *stage_dev) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
+    const int stage = stage_dev ? *stage_dev : stage_arg;
     const int s = i / pr.N, jp = i - s * pr.N;
     const Key key = stream_key(pr.seed, s);
     copy_particle(prop, i, cur, i);
@@ -772,10 +773,11 @@ __global__ void langevin_propose_kernel(PState cur, PState prop, const float *gc
 // on acceptance the particle and its gradient row take the proposal's.
 __global__ void langevin_accept_kernel(PState cur, PState prop, float *gcur, const float *gprop,
                                        const int8_t *valid, const double *lq, const double *gamma,
-                                       const double *lang_h, Params pr, int stage, int sweep, int *lacc,
-                                       int *lprop) {
+                                       const double *lang_h, Params pr, int stage_arg, int sweep, int *lacc,
+                                       int *lprop, const int *stage_dev) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
+    const int stage = stage_dev ? *stage_dev : stage_arg;
     const int s = i / pr.N, jp = i - s * pr.N;
     atomicAdd(&lprop[s], 1);
     if (!valid[i]) return;
@@ -1063,8 +1065,15 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const i
 // (the prior cancels; the printed 1/t over t + 1 terms read as 1/(t+1)).
 constexpr int kMaxRecycleStages = 1024;  // stages whose gamma and log Z are kept
 
+// With stage_dev the stage t comes from the device counter and n_used =
+// min(t + 1, H) (the grid then covers H x P).
 __global__ void recycle_weight_kernel(PState hist, int P, int n_used, int N, int M, int lp1, int t,
-                                      const double *gamma_hist, const double *logz_hist, double *lognu) {
+                                      const double *gamma_hist, const double *logz_hist, double *lognu, int H,
+                                      const int *stage_dev) {
+    if (stage_dev) {
+        t = *stage_dev;
+        n_used = t + 1 < H ? t + 1 : H;
+    }
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n_used * P) return;
     const int i = (int)(idx % (size_t)P), s = i / N;
@@ -1100,7 +1109,9 @@ __device__ inline double block_reduce_128(double v, double *red, bool take_max) 
 __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState hist, const double *lognu, double *wbuf,
                                                                       int n_used, int P, const int *counts, Params pr,
                                                                       double ridge, double *mu_out, double *U_out,
-                                                                      double *lam_out, int *ok_out, double *a_out) {
+                                                                      double *lam_out, int *ok_out, double *a_out,
+                                                                      int H, const int *stage_dev) {
+    if (stage_dev) n_used = *stage_dev + 1 < H ? *stage_dev + 1 : H;
     extern __shared__ double sm_fit[];
     __shared__ double red[kFitThreads];
     const int DM = pr.DM;
@@ -1183,15 +1194,17 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState his
 
 // Stores the current particles as history slot `slot` and this stage's gamma
 // and log Z (per sounding) at row t.
-__global__ void record_slot_kernel(PState hist, PState cur, int P, int slot) {
+__global__ void record_slot_kernel(PState hist, PState cur, int P, int slot, int H, const int *stage_dev) {
+    if (stage_dev) slot = *stage_dev % H;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P) copy_particle(hist, slot * P + i, cur, i);
 }
 
 __global__ void record_stage_kernel(const double *gamma, const double *logz, int S, int M, int t, double *gamma_hist,
-                                    double *logz_hist) {
+                                    double *logz_hist, const int *stage_dev) {
+    if (stage_dev) t = *stage_dev;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    if (s >= S || t >= kMaxRecycleStages) return;
     gamma_hist[(size_t)s * kMaxRecycleStages + t] = gamma[s];
     for (int k = 0; k < M; ++k)
         logz_hist[((size_t)s * kMaxRecycleStages + t) * M + k] = logz[(size_t)s * M + k];
@@ -1202,9 +1215,10 @@ __global__ void record_stage_kernel(const double *gamma, const double *logz, int
 // the trial draws (purpose kPurposePcaTrial, sweep 0) are the same at every
 // bisection step.
 __global__ void pca_trial_kernel(PState cur, PState prop, int8_t *valid_out, Params pr, PcaView pv,
-                                 const double *lo, const double *hi, int stage) {
+                                 const double *lo, const double *hi, int stage_arg, const int *stage_dev) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
+    const int stage = stage_dev ? *stage_dev : stage_arg;
     const int s = i / pr.N, j = i - s * pr.N;
     const int kappa = cur.kappa[i], lam = cur.lam[i];
     const int k = s * pr.M + kappa * (pr.lambda_max + 1) + lam;
@@ -1398,6 +1412,7 @@ struct smc_state {
     // Langevin: merged-layer gradient, particle-space gradients of the current
     // and proposed particles, log q(theta' | theta), per-sounding counts.
     float *mgrad = nullptr, *gcur = nullptr, *gprop = nullptr;
+    unsigned char *grad_work = nullptr;  // the adjoint's claim counters and gates (grad_work_bytes)
     float *ppd_gates = nullptr;  // [P][G], allocated on the first smc_ppd call
     // adaptive within-model proposal, per (sounding, model): mean [DM], U
     // [DM][DM] (column r = direction r), Lambda [DM], ok, scale a, bracket
@@ -1461,7 +1476,7 @@ int run_grad(smc_state *st, PState ps, float *pg) {
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
     int rc = loglik_grad_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->mgrad,
-                                       st->stream);
+                                       st->stream, st->grad_work);
     if (rc) return rc;
     pgrad_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(ps, st->mgrad, st->P, st->LMS,
                                                                  st->d.tau_log_prior, pg);
@@ -1586,6 +1601,7 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->m_m, P * st->LMS)) || (rc = dalloc(st, &st->m_logtau, P * st->LMS)) ||
         (rc = dalloc(st, &st->m_c, P * st->LMS)) || (rc = dalloc(st, &st->y, (size_t)st->S * G)) ||
         (rc = dalloc(st, &st->eps_an, (size_t)G)) || (rc = dalloc(st, &st->mgrad, P * st->LMS * 5)) ||
+        (rc = dalloc(st, &st->grad_work, grad_work_bytes((int)P, G))) ||
         (rc = dalloc(st, &st->gcur, P * GD)) || (rc = dalloc(st, &st->gprop, P * GD)) ||
         (rc = dalloc(st, &st->lq, P)) || (rc = dalloc(st, &st->lacc, (size_t)st->S)) ||
         (rc = dalloc(st, &st->lprop, (size_t)st->S)) || (rc = dalloc(st, &st->lang_h, (size_t)st->S)) ||
@@ -1639,7 +1655,7 @@ extern "C" int smc_destroy(smc_state *st) {
     return AEM_OK;
 }
 
-static int record_history(smc_state *st);
+static int record_history(smc_state *st, const int *stage_dev = nullptr);
 
 extern "C" int smc_init(smc_state *st) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_init: NULL state");
@@ -1723,20 +1739,23 @@ extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
 // proposals (desc.pca_bisect_iters forward passes) towards desc.pca_target.
 // Particle recycling: the current (post-resample) particles become history
 // slot stage mod H; this stage's gamma and log Z are kept for the weights.
-static int record_history(smc_state *st) {
+// stage_dev (graph form): the stage comes from the device counter, whose
+// bound the caller has checked.
+static int record_history(smc_state *st, const int *stage_dev) {
     if (st->d.recycle_stages <= 0) return AEM_OK;
-    const int t = st->stage;
-    if (t >= kMaxRecycleStages) return fail(AEM_ERR_INVALID_ARG, "particle recycling keeps at most 1024 stages");
-    record_slot_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->hist, st->cur, st->P,
-                                                                       t % st->d.recycle_stages);
+    const int t = st->stage, H = st->d.recycle_stages;
+    if (!stage_dev && t >= kMaxRecycleStages)
+        return fail(AEM_ERR_INVALID_ARG, "particle recycling keeps at most 1024 stages");
+    record_slot_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->hist, st->cur, st->P, t % H, H,
+                                                                       stage_dev);
     AEM_CUDA_TRY(cudaGetLastError());
     record_stage_kernel<<<blocks_for(st->S, 128), 128, 0, st->stream>>>(st->gamma, st->logz, st->S, st->M, t,
-                                                                        st->gamma_hist, st->logz_hist);
+                                                                        st->gamma_hist, st->logz_hist, stage_dev);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
 
-static int adapt_stage(smc_state *st) {
+static int adapt_stage(smc_state *st, const int *stage_dev = nullptr) {
     int rc = launch_group(st);
     if (rc) return rc;
     const int nb = st->S * st->M, DM = st->pr.DM;
@@ -1745,17 +1764,19 @@ static int adapt_stage(smc_state *st) {
         AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (st->d.recycle_stages > 0) {
         const int t = st->stage, H = st->d.recycle_stages;
-        const int n_used = t + 1 < H ? t + 1 : H;
+        // with the device counter the grid covers every slot and the kernels
+        // take t and the slots in use from the counter
+        const int n_used = stage_dev ? H : (t + 1 < H ? t + 1 : H);
         if (smem > 48 * 1024)
             AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_recycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         recycle_weight_kernel<<<blocks_for((long long)n_used * st->P, 128), 128, 0, st->stream>>>(
             st->hist, st->P, n_used, st->N, st->M, st->d.lambda_max + 1, t, st->gamma_hist, st->logz_hist,
-            st->hist_lognu);
+            st->hist_lognu, H, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
         pca_fit_recycle_kernel<<<nb, kFitThreads, smem, st->stream>>>(
             st->hist, st->hist_lognu, st->hist_w, n_used, st->P, st->counts, st->pr, st->d.pca_ridge, st->pca_mu,
-            st->pca_U, st->pca_lam, st->pca_ok, st->pca_a);
+            st->pca_U, st->pca_lam, st->pca_ok, st->pca_a, H, stage_dev);
     } else {
         pca_fit_kernel<<<nb, kFitThreads, smem, st->stream>>>(st->cur, st->perm, st->off, st->counts, st->pr,
                                                                st->d.pca_ridge, st->pca_mu, st->pca_U, st->pca_lam,
@@ -1768,7 +1789,7 @@ static int adapt_stage(smc_state *st) {
     for (int it = 0; it < st->d.pca_bisect_iters; ++it) {
         pca_trial_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(st->cur, st->prop, st->valid, st->pr,
                                                                           pca_view(st), st->pca_lo, st->pca_hi,
-                                                                          st->stage);
+                                                                          st->stage, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
         if ((rc = run_loglik(st, st->prop))) return rc;
         pca_stat_kernel<<<nb, 128, 0, st->stream>>>(st->cur.ll, st->prop.ll, st->valid, st->perm, st->off,
@@ -1782,7 +1803,7 @@ static int adapt_stage(smc_state *st) {
     return AEM_OK;
 }
 
-static int langevin_sweeps(smc_state *st, int n) {
+static int langevin_sweeps(smc_state *st, int n, const int *stage_dev = nullptr) {
     AEM_CUDA_TRY(cudaMemsetAsync(st->lacc, 0, sizeof(int) * st->S, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->lprop, 0, sizeof(int) * st->S, st->stream));
     if (n <= 0) return AEM_OK;
@@ -1793,12 +1814,12 @@ static int langevin_sweeps(smc_state *st, int n) {
     st->gcur_valid = true;
     for (int l = 0; l < n; ++l) {
         langevin_propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
-            st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, st->stage, l, st->valid, st->lq);
+            st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, st->stage, l, st->valid, st->lq, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
         if ((rc = run_grad(st, st->prop, st->gprop))) return rc;
         langevin_accept_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
             st->cur, st->prop, st->gcur, st->gprop, st->valid, st->lq, st->gamma, st->lang_h, st->pr, st->stage, l,
-            st->lacc, st->lprop);
+            st->lacc, st->lprop, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     return AEM_OK;
@@ -1884,9 +1905,12 @@ extern "C" int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_
     return AEM_OK;
 }
 
-// One stage of Algorithm 1 (reweight, resample, R sweeps of the fixed-scale
-// moves) enqueued on st->stream without host synchronisation, reading the
-// stage number from st->d_stage; ends with the loop condition.
+// One stage of Algorithm 1 (reweight, resample, R sweeps of the moves, with
+// the recycling record after the resample, the adaptive fit and scale
+// bisection before the sweeps and the Langevin sweeps after them when the
+// descriptor turns those on) enqueued on st->stream without host
+// synchronisation or allocation, reading the stage number from st->d_stage;
+// ends with the loop condition.
 static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphConditionalHandle h) {
     cudaStream_t s = st->stream;
     stage_inc_kernel<<<1, 32, 0, s>>>(st->d_stage);
@@ -1904,15 +1928,22 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     AEM_CUDA_TRY(cudaGetLastError());
     copy_state_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->alt, st->P);
     AEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = record_history(st, st->d_stage))) return rc;
     AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, s));
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, s));
+    if (st->d.adaptive && (rc = adapt_stage(st, st->d_stage))) return rc;
     for (int sw = 0; sw < R; ++sw) {
         propose_kernel<<<blocks_for(st->P, 128), 128, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->pr, 0, sw,
-                                                               pca_view(st), st->d_stage, nullptr);
+                                                               pca_view(st), st->d_stage, st->lf);
         AEM_CUDA_TRY(cudaGetLastError());
         if ((rc = run_loglik(st, st->prop))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->gamma,
-                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage, nullptr);
+                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage, st->lf);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
+    if ((rc = langevin_sweeps(st, st->d.n_langevin, st->d_stage))) return rc;
+    if (st->d.n_langevin > 0 && st->d.langevin_adapt) {
+        langevin_adapt_kernel<<<blocks_for(st->S, 128), 128, 0, s>>>(st->lacc, st->lprop, st->S, st->lang_h);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, h);
@@ -1923,10 +1954,9 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
 extern "C" int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: NULL state");
     if (n_sweeps < 1 || max_stages < 1) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: n_sweeps and max_stages must be >= 1");
-    if (st->d.adaptive || st->d.n_langevin > 0 || st->d.recycle_stages > 0)
-        return fail(AEM_ERR_UNSUPPORTED,
-                    "smc_run_graph: only the fixed-scale moves (no adaptive proposal, Langevin sweeps or recycling)");
     const int s0 = st->stage;
+    if (st->d.recycle_stages > 0 && (long long)s0 + max_stages >= kMaxRecycleStages)
+        return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: particle recycling keeps at most 1024 stages");
     AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
     AEM_CUDA_TRY(cudaMemcpy(st->d_stage, &s0, sizeof(int), cudaMemcpyHostToDevice));
     cudaStream_t user = st->stream, cap = nullptr;
@@ -2093,7 +2123,7 @@ extern "C" int smc_langevin_propose(smc_state *st, int stage, int sweep) {
     if (!st->gcur_valid)
         return fail(AEM_ERR_INVALID_ARG, "smc_langevin_propose: no gradient of the current particles (smc_grad_current)");
     langevin_propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
-        st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, stage, sweep, st->valid, st->lq);
+        st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, stage, sweep, st->valid, st->lq, nullptr);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }

@@ -269,28 +269,48 @@ def test_flight_line_ip_probability_follows_chargeability(torch, L, S):
     assert np.all(np.isfinite(post))
 
 
-def test_graph_captured_run_equals_host_loop(S, gsys, data):
+# sampler options of the graph test: the fixed-scale moves; the adaptive
+# proposal with particle recycling and ZCA-coloured birth / death; Langevin
+# sweeps with step adaptation
+GRAPH_MODES = {"fixed": {}, "adaptive_recycling_zca": dict(adaptive=1, recycle_stages=3, zca=0.5),
+               "langevin": dict(n_langevin=2)}
+
+
+@pytest.mark.parametrize("mode", list(GRAPH_MODES))
+def test_graph_captured_run_equals_host_loop(S, gsys, data, mode):
     """smc_run_graph (one captured stage repeated by a device-side WHILE
     condition) reproduces smc_run bit for bit: particles, log-likelihoods,
-    gammas, evidence estimates and the stage count, on three soundings."""
+    gammas, evidence estimates and the stage count, on three soundings, for
+    each sampler option."""
     import time
     runs = []
+    n_sweeps = 10 if mode == "fixed" else 4
     for graph in (False, True):
         st = settings(n_particles=256, seed=21)
-        sm = gpu_smc(S, gsys, data, st, soundings=3)
+        sm = S.SMC(gsys, np.tile(data, (3, 1)), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles, n_soundings=3,
+                   kappa_max=st.kappa_max, lambda_max=st.lambda_max, zmax=st.zmax, seed=st.seed, r_max=st.r_max,
+                   **GRAPH_MODES[mode])
         sm.init()
         t0 = time.perf_counter()
-        stages = sm.run_graph(max_stages=200, n_sweeps=10) if graph else sm.run(max_stages=200, n_sweeps=10)
+        if graph:
+            stages = sm.run_graph(max_stages=200, n_sweeps=n_sweeps)
+        else:
+            stages = sm.run(max_stages=200, n_sweeps=n_sweeps)
         dt = time.perf_counter() - t0
         p = sm.get_particles(0)
         post, lb, lz = sm.model_odds()
-        runs.append((stages, p, sm.stats()["gamma"], lz, dt))
-    (s0, p0, g0, z0, t0_), (s1, p1, g1, z1, t1_) = runs
-    print(f"\nhost loop {t0_ * 1e3:.1f} ms, graph {t1_ * 1e3:.1f} ms, {s0} stages")
+        extra = sm.langevin_stats()[2] if mode == "langevin" else (sm.adaptation()["scale"] if mode != "fixed" else 0)
+        runs.append((stages, p, sm.stats()["gamma"], lz, dt, extra))
+    (s0, p0, g0, z0, t0_, e0), (s1, p1, g1, z1, t1_, e1) = runs
+    print(f"\n{mode}: host loop {t0_ * 1e3:.1f} ms, graph {t1_ * 1e3:.1f} ms, {s0} stages")
     assert s0 == s1 and np.all(g1 == 1.0)
     assert np.array_equal(g0, g1) and np.array_equal(z0, z1)
+    assert np.array_equal(e0, e1)
     for name in ("kappa", "lam", "phib", "tau", "c", "zc", "phic", "zm", "mv", "ll"):
         assert np.array_equal(getattr(p0, name), getattr(p1, name)), name
+
+
+def test_graph_capped_run(S, gsys, data):
     # a capped run stops after max_stages
     sm = gpu_smc(S, gsys, data, settings(n_particles=256, seed=21), soundings=3)
     sm.init()
