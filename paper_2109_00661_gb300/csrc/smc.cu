@@ -945,116 +945,242 @@ __device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool
 
 constexpr int kFitThreads = 128;
 constexpr int kJacobiSweeps = 30;
+constexpr int kMaxPairs = (AEM_SMC_GRAD_DIM + 1) / 2;  // rotations per round of the parallel ordering
+
+// Fixed-order CTA reduction over kFitThreads threads (sum or maximum).
+__device__ inline double block_reduce_128(double v, double *red, bool take_max) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            red[threadIdx.x] = take_max ? fmax(red[threadIdx.x], red[threadIdx.x + w]) : red[threadIdx.x] + red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
 
 // Cyclic Jacobi rotations on the symmetric d x d matrix A (row stride DM) in
-// place, accumulating the rotations in V: on return A's diagonal holds the
-// eigenvalues and V's columns the eigenvectors.  At most kJacobiSweeps sweeps;
-// stops when the off-diagonal mass falls below 1e-30 of the diagonal's.
-__device__ void jacobi_eigen(double *A, double *V, int d, int DM) {
-    double scale2 = 0.0;
-    for (int j = 0; j < d; ++j) scale2 += A[j * DM + j] * A[j * DM + j];
+// shared memory, accumulating the rotations in V, by the whole CTA: each
+// round of a sweep rotates n / 2 disjoint (p, q) pairs at once (the
+// round-robin ordering of the indices, n = d rounded up to even; an index d
+// pairs with nothing), as A <- A J, A <- J^T A, then the rotated 2 x 2 blocks
+// take their exact values (A_pp - t A_pq, A_qq + t A_pq, 0) and the lower
+// triangle is copied from the upper one.  Each rotation zeroes A_pq with
+// t = tan(phi) the smaller root of t^2 + 2 t th - 1 = 0, th = (A_qq - A_pp) /
+// (2 A_pq).  On return A's diagonal holds the eigenvalues and V's columns the
+// eigenvectors.  At most kJacobiSweeps sweeps; stops when the off-diagonal
+// mass falls below 1e-30 of the diagonal's.
+__device__ void jacobi_eigen_block(double *A, double *V, int d, int DM, double *red) {
+    __shared__ double rc[kMaxPairs], rs[kMaxPairs], rt[kMaxPairs], ra[kMaxPairs], rpp[kMaxPairs], rqq[kMaxPairs];
+    __shared__ int rp[kMaxPairs], rq[kMaxPairs];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = d + (d & 1), half = n / 2;
+    const double scale2 = block_reduce_128(tid < d ? A[tid * DM + tid] * A[tid * DM + tid] : 0.0, red, false);
     for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-        double offn = 0.0;
-        for (int p = 0; p < d; ++p)
-            for (int q = p + 1; q < d; ++q) offn += A[p * DM + q] * A[p * DM + q];
-        if (offn <= 1e-30 * scale2) break;
-        for (int p = 0; p < d; ++p) {
-            for (int q = p + 1; q < d; ++q) {
-                const double apq = A[p * DM + q];
-                if (apq == 0.0) continue;
-                // rotation that zeroes A[p][q]: t = tan(phi) is the smaller root of
-                // t^2 + 2 t th - 1 = 0 with th = (A_qq - A_pp) / (2 A_pq)
-                const double th = (A[q * DM + q] - A[p * DM + p]) / (2.0 * apq);
-                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-                for (int r = 0; r < d; ++r) {
-                    if (r == p || r == q) continue;
-                    const double arp = A[r * DM + p], arq = A[r * DM + q];
-                    const double np_ = c * arp - sn * arq, nq_ = sn * arp + c * arq;
-                    A[r * DM + p] = np_;
-                    A[p * DM + r] = np_;
-                    A[r * DM + q] = nq_;
-                    A[q * DM + r] = nq_;
+        double o = 0.0;
+        for (int e = tid; e < d * d; e += nt) {
+            const int j = e / d, l = e - j * d;
+            if (l > j) o += A[j * DM + l] * A[j * DM + l];
+        }
+        if (block_reduce_128(o, red, false) <= 1e-30 * scale2) break;
+        for (int round = 0; round < n - 1; ++round) {
+            if (tid < half) {
+                const int a = tid == 0 ? n - 1 : (round + tid) % (n - 1);
+                const int b = tid == 0 ? round : (round - tid + (n - 1)) % (n - 1);
+                const int p = a < b ? a : b, q = a < b ? b : a;
+                double c = 1.0, sn = 0.0, t = 0.0, apq = 0.0;
+                if (q < d) {
+                    apq = A[p * DM + q];
+                    if (apq != 0.0) {
+                        const double th = (A[q * DM + q] - A[p * DM + p]) / (2.0 * apq);
+                        t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sn = t * c;
+                    }
+                    rpp[tid] = A[p * DM + p];
+                    rqq[tid] = A[q * DM + q];
                 }
-                A[p * DM + p] -= t * apq;
-                A[q * DM + q] += t * apq;
-                A[p * DM + q] = 0.0;
-                A[q * DM + p] = 0.0;
-                for (int r = 0; r < d; ++r) {
-                    const double vrp = V[r * DM + p], vrq = V[r * DM + q];
-                    V[r * DM + p] = c * vrp - sn * vrq;
-                    V[r * DM + q] = sn * vrp + c * vrq;
-                }
+                rp[tid] = p;
+                rq[tid] = apq != 0.0 ? q : d;  // d: nothing to rotate
+                rc[tid] = c;
+                rs[tid] = sn;
+                rt[tid] = t;
+                ra[tid] = apq;
             }
+            __syncthreads();
+            for (int e = tid; e < d * half; e += nt) {  // columns p, q of A and V
+                const int i = e / d, r = e - i * d, p = rp[i], q = rq[i];
+                if (q >= d) continue;
+                const double c = rc[i], sn = rs[i];
+                const double arp = A[r * DM + p], arq = A[r * DM + q];
+                A[r * DM + p] = c * arp - sn * arq;
+                A[r * DM + q] = sn * arp + c * arq;
+                const double vrp = V[r * DM + p], vrq = V[r * DM + q];
+                V[r * DM + p] = c * vrp - sn * vrq;
+                V[r * DM + q] = sn * vrp + c * vrq;
+            }
+            __syncthreads();
+            for (int e = tid; e < d * half; e += nt) {  // rows p, q of A
+                const int i = e / d, r = e - i * d, p = rp[i], q = rq[i];
+                if (q >= d) continue;
+                const double c = rc[i], sn = rs[i];
+                const double apr = A[p * DM + r], aqr = A[q * DM + r];
+                A[p * DM + r] = c * apr - sn * aqr;
+                A[q * DM + r] = sn * apr + c * aqr;
+            }
+            __syncthreads();
+            if (tid < half && rq[tid] < d) {
+                const int p = rp[tid], q = rq[tid];
+                A[p * DM + p] = rpp[tid] - rt[tid] * ra[tid];
+                A[q * DM + q] = rqq[tid] + rt[tid] * ra[tid];
+                A[p * DM + q] = 0.0;
+            }
+            __syncthreads();
+            for (int e = tid; e < d * d; e += nt) {
+                const int j = e / d, l = e - j * d;
+                if (l < j) A[j * DM + l] = A[l * DM + j];
+            }
+            __syncthreads();
         }
     }
 }
 
-// One CTA per (sounding, model): mean and (biased) covariance of theta over
-// the model's particles in FP64 with fixed-order sums, plus
-// (ridge * step_j)^2 on the diagonal, then cyclic Jacobi rotations (thread 0,
-// in shared memory) to Sigma = U Lambda U^T.  Models with fewer than two
-// particles get ok = 0 and their scale reset to 1.
-__global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const int *perm, const int *off,
-                                                              const int *counts, Params pr, double ridge,
-                                                              double *mu_out, double *U_out, double *lam_out,
-                                                              int *ok_out, double *a_out) {
-    extern __shared__ double sm_fit[];
-    const int DM = pr.DM;
-    double *A = sm_fit, *V = A + DM * DM, *mu = V + DM * DM;
-    const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
-    const int kappa = k / (pr.lambda_max + 1), lam = k - kappa * (pr.lambda_max + 1);
-    const int d = 3 + 2 * kappa + 2 * lam;
-    const int n = counts[b];
-    const int *idx = perm + (size_t)s * pr.N + off[s * (pr.M + 1) + k];
-    const int tid = threadIdx.x;
-    if (n < 2) {
-        if (tid == 0) {
-            ok_out[b] = 0;
-            a_out[b] = 1.0;
+// The weighted Gaussian fit of one model in one CTA, shared by the plain and
+// the recycled fit.  cand(c) gives candidate c's particle index and weight
+// (weight 0: not used) for c < C.  Candidates are taken kFitThreads at a
+// time into shared memory (theta rows X, weights W); the mean and then the
+// covariance of the deviations accumulate per entry in candidate order (the
+// serial order of the definition), each entry on its own thread.  Adds
+// (ridge * step_j)^2 on the diagonal, then A = U Lambda U^T by
+// jacobi_eigen_block; writes mu, U, Lambda (clipped at 0) and ok = 1.
+template <class Cand>
+__device__ void fit_model_block(const PState &ps, Cand cand, int C, double sw, int kappa, int lam, const Params &pr,
+                                double ridge, double *sm, double *red, int b, double *mu_out, double *U_out,
+                                double *lam_out, int *ok_out) {
+    const int DM = pr.DM, tid = threadIdx.x, d = 3 + 2 * kappa + 2 * lam;
+    double *A = sm, *V = A + DM * DM, *mu = V + DM * DM, *X = mu + DM, *W = X + (size_t)kFitThreads * DM;
+    constexpr int kMaxEntries = (AEM_SMC_GRAD_DIM * (AEM_SMC_GRAD_DIM + 1) / 2 + kFitThreads - 1) / kFitThreads;
+    const int ne = d * (d + 1) / 2;
+    int ej[kMaxEntries], el[kMaxEntries];  // this thread's entries of the upper triangle, row-major
+#pragma unroll
+    for (int u = 0; u < kMaxEntries; ++u) {
+        int j = 0, rem = tid + u * kFitThreads;
+        while (j < d && rem >= d - j) {
+            rem -= d - j;
+            ++j;
         }
-        return;
+        ej[u] = j;
+        el[u] = j + rem;
     }
-    for (int j = tid; j < d; j += blockDim.x) {
-        double acc = 0.0;
-        for (int q = 0; q < n; ++q) acc += theta_value(theta_ref(st, idx[q], j, kappa, lam, pr), pr);
-        mu[j] = acc / n;
-    }
-    __syncthreads();
-    for (int e = tid; e < d * d; e += blockDim.x) {
-        const int j = e / d, l = e - (e / d) * d;
-        if (l < j) continue;
-        double acc = 0.0;
-        for (int q = 0; q < n; ++q) {
-            const int i = idx[q];
-            acc += (theta_value(theta_ref(st, i, j, kappa, lam, pr), pr) - mu[j]) *
-                   (theta_value(theta_ref(st, i, l, kappa, lam, pr), pr) - mu[l]);
+    // pass 1: the weighted mean; pass 2: the weighted covariance of the deviations
+    for (int pass = 0; pass < 2; ++pass) {
+        double acc[kMaxEntries];
+#pragma unroll
+        for (int u = 0; u < kMaxEntries; ++u) acc[u] = 0.0;
+        for (int base = 0; base < C; base += kFitThreads) {
+            const int c = base + tid;
+            int i = -1;
+            double w = 0.0;
+            if (c < C) cand(c, i, w);
+            W[tid] = w;
+            for (int j = 0; j < d; ++j) {
+                double x = 0.0;
+                if (w != 0.0) {
+                    x = theta_value(theta_ref(ps, i, j, kappa, lam, pr), pr);
+                    if (pass == 1) x -= mu[j];
+                }
+                X[tid * DM + j] = x;
+            }
+            __syncthreads();
+            const int nc = C - base < kFitThreads ? C - base : kFitThreads;
+            if (pass == 0) {
+                if (tid < d)
+                    for (int q = 0; q < nc; ++q) acc[0] += W[q] * X[q * DM + tid];
+            } else {
+#pragma unroll
+                for (int u = 0; u < kMaxEntries; ++u) {
+                    const int e = tid + u * kFitThreads;
+                    if (e < ne) {
+                        const int j = ej[u], l = el[u];
+                        for (int q = 0; q < nc; ++q) acc[u] += W[q] * X[q * DM + j] * X[q * DM + l];
+                    }
+                }
+            }
+            __syncthreads();
         }
-        double c = acc / n;
-        if (j == l) {
-            const double sj = ridge * theta_ref(st, idx[0], j, kappa, lam, pr).scale;
-            c += sj * sj;
+        if (pass == 0) {
+            if (tid < d) mu[tid] = acc[0] / sw;
+        } else {
+#pragma unroll
+            for (int u = 0; u < kMaxEntries; ++u) {
+                const int e = tid + u * kFitThreads;
+                if (e < ne) {
+                    const int j = ej[u], l = el[u];
+                    double cv = acc[u] / sw;
+                    if (j == l) {
+                        const double sj = ridge * theta_ref(ps, 0, j, kappa, lam, pr).scale;
+                        cv += sj * sj;
+                    }
+                    A[j * DM + l] = cv;
+                    A[l * DM + j] = cv;
+                }
+            }
         }
-        A[j * DM + l] = c;
-        A[l * DM + j] = c;
+        __syncthreads();
     }
-    for (int e = tid; e < d * d; e += blockDim.x) {
+    for (int e = tid; e < d * d; e += kFitThreads) {
         const int j = e / d, l = e - (e / d) * d;
         V[j * DM + l] = j == l ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (tid == 0) jacobi_eigen(A, V, d, DM);
-    __syncthreads();
-    for (int e = tid; e < d * d; e += blockDim.x) {
+    jacobi_eigen_block(A, V, d, DM, red);
+    for (int e = tid; e < d * d; e += kFitThreads) {
         const int j = e / d, l = e - (e / d) * d;
         U_out[(size_t)b * DM * DM + (size_t)j * DM + l] = V[j * DM + l];
     }
-    for (int j = tid; j < d; j += blockDim.x) {
+    for (int j = tid; j < d; j += kFitThreads) {
         mu_out[(size_t)b * DM + j] = mu[j];
         const double lj = A[j * DM + j];
         lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
     }
     if (tid == 0) ok_out[b] = 1;
+}
+
+// Shared memory of the fit kernels, in doubles: A, V [DM][DM], mu [DM], the
+// candidate tile X [kFitThreads][DM] and its weights [kFitThreads].
+size_t fit_smem_bytes(int DM) {
+    return sizeof(double) * (2 * (size_t)DM * DM + DM + (size_t)kFitThreads * DM + kFitThreads);
+}
+
+// One CTA per (sounding, model): mean and (biased) covariance of theta over
+// the model's particles in FP64 with fixed-order sums, plus
+// (ridge * step_j)^2 on the diagonal, then Sigma = U Lambda U^T by parallel
+// Jacobi rotations in shared memory.  Models with fewer than two particles get
+// ok = 0 and their scale reset to 1.
+__global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const int *perm, const int *off,
+                                                              const int *counts, Params pr, double ridge,
+                                                              double *mu_out, double *U_out, double *lam_out,
+                                                              int *ok_out, double *a_out) {
+    extern __shared__ double sm_fit[];
+    __shared__ double red[kFitThreads];
+    const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
+    const int kappa = k / (pr.lambda_max + 1), lam = k - kappa * (pr.lambda_max + 1);
+    const int n = counts[b];
+    const int *idx = perm + (size_t)s * pr.N + off[s * (pr.M + 1) + k];
+    if (n < 2) {
+        if (threadIdx.x == 0) {
+            ok_out[b] = 0;
+            a_out[b] = 1.0;
+        }
+        return;
+    }
+    auto cand = [&](int c, int &i, double &w) {
+        i = idx[c];
+        w = 1.0;
+    };
+    fit_model_block(st, cand, n, (double)n, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out);
 }
 
 // ----------------------------------------------------- particle recycling
@@ -1088,19 +1214,6 @@ __global__ void recycle_weight_kernel(PState hist, int P, int n_used, int N, int
     lognu[idx] = g[t] * l - (m + log(acc) - log((double)(t + 1)));
 }
 
-__device__ inline double block_reduce_128(double v, double *red, bool take_max) {
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            red[threadIdx.x] = take_max ? fmax(red[threadIdx.x], red[threadIdx.x + w]) : red[threadIdx.x] + red[threadIdx.x + w];
-        __syncthreads();
-    }
-    const double r = red[0];
-    __syncthreads();
-    return r;
-}
-
 // One CTA (128 threads) per (sounding, model) with at least two current
 // particles: normalised recycling weights over the model's stored particles
 // (written to wbuf), the weighted mean and covariance of theta in FP64 with
@@ -1114,11 +1227,8 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState his
     if (stage_dev) n_used = *stage_dev + 1 < H ? *stage_dev + 1 : H;
     extern __shared__ double sm_fit[];
     __shared__ double red[kFitThreads];
-    const int DM = pr.DM;
-    double *A = sm_fit, *V = A + DM * DM, *mu = V + DM * DM;
     const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
     const int lp1 = pr.lambda_max + 1, kappa = k / lp1, lam = k - kappa * lp1;
-    const int d = 3 + 2 * kappa + 2 * lam;
     const int tid = threadIdx.x;
     if (counts[b] < 2) {
         if (tid == 0) {
@@ -1146,50 +1256,12 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState his
         }
     }
     sw = block_reduce_128(sw, red, false);  // also orders the wbuf writes before the reads below
-    for (int j = tid; j < d; j += blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < C; ++c) {
-            const size_t idx = cand(c);
-            if (member(idx)) acc += wbuf[idx] * theta_value(theta_ref(hist, (int)idx, j, kappa, lam, pr), pr);
-        }
-        mu[j] = acc / sw;
-    }
-    __syncthreads();
-    for (int e = tid; e < d * d; e += blockDim.x) {
-        const int j = e / d, l = e - (e / d) * d;
-        if (l < j) continue;
-        double acc = 0.0;
-        for (int c = 0; c < C; ++c) {
-            const size_t idx = cand(c);
-            if (!member(idx)) continue;
-            acc += wbuf[idx] * (theta_value(theta_ref(hist, (int)idx, j, kappa, lam, pr), pr) - mu[j]) *
-                   (theta_value(theta_ref(hist, (int)idx, l, kappa, lam, pr), pr) - mu[l]);
-        }
-        double cv = acc / sw;
-        if (j == l) {
-            const double sj = ridge * theta_ref(hist, 0, j, kappa, lam, pr).scale;
-            cv += sj * sj;
-        }
-        A[j * DM + l] = cv;
-        A[l * DM + j] = cv;
-    }
-    for (int e = tid; e < d * d; e += blockDim.x) {
-        const int j = e / d, l = e - (e / d) * d;
-        V[j * DM + l] = j == l ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (tid == 0) jacobi_eigen(A, V, d, DM);
-    __syncthreads();
-    for (int e = tid; e < d * d; e += blockDim.x) {
-        const int j = e / d, l = e - (e / d) * d;
-        U_out[(size_t)b * DM * DM + (size_t)j * DM + l] = V[j * DM + l];
-    }
-    for (int j = tid; j < d; j += blockDim.x) {
-        mu_out[(size_t)b * DM + j] = mu[j];
-        const double lj = A[j * DM + j];
-        lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
-    }
-    if (tid == 0) ok_out[b] = 1;
+    auto wcand = [&](int c, int &i, double &w) {
+        const size_t idx = cand(c);
+        i = (int)idx;
+        w = member(idx) ? wbuf[idx] : 0.0;
+    };
+    fit_model_block(hist, wcand, C, sw, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out);
 }
 
 // Stores the current particles as history slot `slot` and this stage's gamma
@@ -1759,7 +1831,7 @@ static int adapt_stage(smc_state *st, const int *stage_dev = nullptr) {
     int rc = launch_group(st);
     if (rc) return rc;
     const int nb = st->S * st->M, DM = st->pr.DM;
-    const size_t smem = sizeof(double) * (2 * (size_t)DM * DM + DM);
+    const size_t smem = fit_smem_bytes(DM);
     if (smem > 48 * 1024)
         AEM_CUDA_TRY(cudaFuncSetAttribute(pca_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (st->d.recycle_stages > 0) {
