@@ -450,6 +450,7 @@ __global__ void gather_kernel(PState dst, PState src, const int *anc, int P) {
 struct PcaView {
     const double *U, *lam, *a;
     const int *ok;
+    const double *Z;  // ZCA roots U Lambda^(1/2) U^T [DM][DM] per (sounding, model)
 };
 __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int lam, const Params &pr, PcaView pv,
                          double a, double u_comp, double xi);
@@ -843,12 +844,6 @@ __device__ bool pca_step(PState cur, PState prop, int i, int s, int kappa, int l
 // J = Z[i, i] - Z[i, h] (h the copied value's component, absent for the m = 0
 // background).  Death: the interface floor(u1 n) of model k, u solved from
 // the two values, the reciprocal factor.
-__device__ inline double zca_entry(const double *U, const double *lam, int DM, int d, int i, int jj) {
-    double z = 0.0;
-    for (int r = 0; r < d; ++r) z += U[(size_t)i * DM + r] * sqrt(lam[r] > 0.0 ? lam[r] : 0.0) * U[(size_t)jj * DM + r];
-    return z;
-}
-
 __device__ inline void theta_store(const ThetaRef &r, const Params &pr, double v) {
     *r.x = (float)((r.is_tau && pr.tau_log_prior) ? pow(10.0, v) : v);
 }
@@ -884,14 +879,14 @@ __device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool
         const int d = 3 + 2 * k2 + 2 * l2;
         const int o_val = cond ? 1 : 1 + 2 * k2 + l2, o_dep = cond ? 1 + k2 : 1 + 2 * k2;
         const int j_new = o_val + at, j_z = o_dep + at, h = cond ? (at == 0 ? 0 : o_val + at - 1) : (at == 0 ? -1 : o_val + at - 1);
-        const double *U = pv.U + (size_t)kk * DM * DM, *L = pv.lam + (size_t)kk * DM;
+        const double *Zk = pv.Z + (size_t)kk * DM * DM + (size_t)j_new * DM;  // row j_new of the ZCA root
         double th[3 + 4 * AEM_SMC_SLOTS];
         // the new value's base is the copied value (exact in float), then the shift
         for (int jj = 0; jj < d; ++jj) th[jj] = theta_value(theta_ref(prop, i, jj, k2, l2, pr), pr);
         for (int jj = 0; jj < d; ++jj)
-            if (jj != j_z) th[jj] += zca_entry(U, L, DM, d, j_new, jj) * xi;
+            if (jj != j_z) th[jj] += Zk[jj] * xi;
         for (int jj = 0; jj < d; ++jj) theta_store(theta_ref(prop, i, jj, k2, l2, pr), pr, th[jj]);
-        const double jac = zca_entry(U, L, DM, d, j_new, j_new) - (h >= 0 ? zca_entry(U, L, DM, d, j_new, h) : 0.0);
+        const double jac = Zk[j_new] - (h >= 0 ? Zk[h] : 0.0);
         lf = log(fabs(jac)) - log(width) - (log_phi0 - 0.5 * xi * xi);
     } else {
         const int n = cond ? kappa : lam;
@@ -903,13 +898,13 @@ __device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool
         const int d = 3 + 2 * kappa + 2 * lam;
         const int o_val = cond ? 1 : 1 + 2 * kappa + lam, o_dep = cond ? 1 + kappa : 1 + 2 * kappa;
         const int j_new = o_val + at, j_z = o_dep + at, h = cond ? (at == 0 ? 0 : o_val + at - 1) : (at == 0 ? -1 : o_val + at - 1);
-        const double *U = pv.U + (size_t)kk * DM * DM, *L = pv.lam + (size_t)kk * DM;
+        const double *Zk = pv.Z + (size_t)kk * DM * DM + (size_t)j_new * DM;
         double th[3 + 4 * AEM_SMC_SLOTS];
         for (int jj = 0; jj < d; ++jj) th[jj] = theta_value(theta_ref(cur, i, jj, kappa, lam, pr), pr);
-        const double jac = zca_entry(U, L, DM, d, j_new, j_new) - (h >= 0 ? zca_entry(U, L, DM, d, j_new, h) : 0.0);
+        const double jac = Zk[j_new] - (h >= 0 ? Zk[h] : 0.0);
         const double u = (th[j_new] - (h >= 0 ? th[h] : 0.0)) / jac;
         for (int jj = 0; jj < d; ++jj)
-            if (jj != j_z && jj != j_new) th[jj] -= zca_entry(U, L, DM, d, j_new, jj) * u;
+            if (jj != j_z && jj != j_new) th[jj] -= Zk[jj] * u;
         // drop the two components, then the interface from the profile
         int w = 0;
         for (int jj = 0; jj < d; ++jj)
@@ -1058,7 +1053,7 @@ __device__ void jacobi_eigen_block(double *A, double *V, int d, int DM, double *
 template <class Cand>
 __device__ void fit_model_block(const PState &ps, Cand cand, int C, double sw, int kappa, int lam, const Params &pr,
                                 double ridge, double *sm, double *red, int b, double *mu_out, double *U_out,
-                                double *lam_out, int *ok_out) {
+                                double *lam_out, int *ok_out, double *Z_out) {
     const int DM = pr.DM, tid = threadIdx.x, d = 3 + 2 * kappa + 2 * lam;
     double *A = sm, *V = A + DM * DM, *mu = V + DM * DM, *X = mu + DM, *W = X + (size_t)kFitThreads * DM;
     constexpr int kMaxEntries = (AEM_SMC_GRAD_DIM * (AEM_SMC_GRAD_DIM + 1) / 2 + kFitThreads - 1) / kFitThreads;
@@ -1145,6 +1140,16 @@ __device__ void fit_model_block(const PState &ps, Cand cand, int C, double sw, i
         const double lj = A[j * DM + j];
         lam_out[(size_t)b * DM + j] = lj > 0.0 ? lj : 0.0;
     }
+    // the ZCA root Z = U Lambda^(1/2) U^T (Lambda clipped at 0), summed over r in order
+    for (int e = tid; e < d * d; e += kFitThreads) {
+        const int j = e / d, l = e - (e / d) * d;
+        double z = 0.0;
+        for (int r = 0; r < d; ++r) {
+            const double lr = A[r * DM + r];
+            z += V[j * DM + r] * sqrt(lr > 0.0 ? lr : 0.0) * V[l * DM + r];
+        }
+        Z_out[(size_t)b * DM * DM + (size_t)j * DM + l] = z;
+    }
     if (tid == 0) ok_out[b] = 1;
 }
 
@@ -1162,7 +1167,7 @@ size_t fit_smem_bytes(int DM) {
 __global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const int *perm, const int *off,
                                                               const int *counts, Params pr, double ridge,
                                                               double *mu_out, double *U_out, double *lam_out,
-                                                              int *ok_out, double *a_out) {
+                                                              int *ok_out, double *a_out, double *Z_out) {
     extern __shared__ double sm_fit[];
     __shared__ double red[kFitThreads];
     const int b = blockIdx.x, s = b / pr.M, k = b - (b / pr.M) * pr.M;
@@ -1180,7 +1185,8 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_kernel(PState st, const i
         i = idx[c];
         w = 1.0;
     };
-    fit_model_block(st, cand, n, (double)n, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out);
+    fit_model_block(st, cand, n, (double)n, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out,
+                    Z_out);
 }
 
 // ----------------------------------------------------- particle recycling
@@ -1223,7 +1229,7 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState his
                                                                       int n_used, int P, const int *counts, Params pr,
                                                                       double ridge, double *mu_out, double *U_out,
                                                                       double *lam_out, int *ok_out, double *a_out,
-                                                                      int H, const int *stage_dev) {
+                                                                      int H, const int *stage_dev, double *Z_out) {
     if (stage_dev) n_used = *stage_dev + 1 < H ? *stage_dev + 1 : H;
     extern __shared__ double sm_fit[];
     __shared__ double red[kFitThreads];
@@ -1261,7 +1267,8 @@ __global__ void __launch_bounds__(kFitThreads) pca_fit_recycle_kernel(PState his
         i = (int)idx;
         w = member(idx) ? wbuf[idx] : 0.0;
     };
-    fit_model_block(hist, wcand, C, sw, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out);
+    fit_model_block(hist, wcand, C, sw, kappa, lam, pr, ridge, sm_fit, red, b, mu_out, U_out, lam_out, ok_out,
+                    Z_out);
 }
 
 // Stores the current particles as history slot `slot` and this stage's gamma
@@ -1489,7 +1496,7 @@ struct smc_state {
     // adaptive within-model proposal, per (sounding, model): mean [DM], U
     // [DM][DM] (column r = direction r), Lambda [DM], ok, scale a, bracket
     double *pca_mu = nullptr, *pca_U = nullptr, *pca_lam = nullptr, *pca_a = nullptr, *pca_lo = nullptr,
-           *pca_hi = nullptr;
+           *pca_hi = nullptr, *pca_Z = nullptr;
     int *pca_ok = nullptr;
     // particle recycling: the last H post-resample populations ([H * P] in
     // every particle array, slot = stage mod H), their log nu and weights, and
@@ -1679,6 +1686,7 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->lprop, (size_t)st->S)) || (rc = dalloc(st, &st->lang_h, (size_t)st->S)) ||
         (rc = dalloc(st, &st->pca_mu, (size_t)st->S * st->M * p.DM)) ||
         (rc = dalloc(st, &st->pca_U, (size_t)st->S * st->M * p.DM * p.DM)) ||
+        (rc = dalloc(st, &st->pca_Z, (size_t)st->S * st->M * p.DM * p.DM)) ||
         (rc = dalloc(st, &st->pca_lam, (size_t)st->S * st->M * p.DM)) ||
         (rc = dalloc(st, &st->pca_a, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_lo, (size_t)st->S * st->M)) ||
         (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M)) ||
@@ -1796,7 +1804,7 @@ extern "C" int smc_resample(smc_state *st) {
     return record_history(st);
 }
 
-static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, st->pca_a, st->pca_ok}; }
+static PcaView pca_view(smc_state *st) { return PcaView{st->pca_U, st->pca_lam, st->pca_a, st->pca_ok, st->pca_Z}; }
 
 extern "C" int smc_propose(smc_state *st, int stage, int sweep) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_propose: NULL state");
@@ -1848,11 +1856,11 @@ static int adapt_stage(smc_state *st, const int *stage_dev = nullptr) {
         AEM_CUDA_TRY(cudaGetLastError());
         pca_fit_recycle_kernel<<<nb, kFitThreads, smem, st->stream>>>(
             st->hist, st->hist_lognu, st->hist_w, n_used, st->P, st->counts, st->pr, st->d.pca_ridge, st->pca_mu,
-            st->pca_U, st->pca_lam, st->pca_ok, st->pca_a, H, stage_dev);
+            st->pca_U, st->pca_lam, st->pca_ok, st->pca_a, H, stage_dev, st->pca_Z);
     } else {
         pca_fit_kernel<<<nb, kFitThreads, smem, st->stream>>>(st->cur, st->perm, st->off, st->counts, st->pr,
                                                                st->d.pca_ridge, st->pca_mu, st->pca_U, st->pca_lam,
-                                                               st->pca_ok, st->pca_a);
+                                                               st->pca_ok, st->pca_a, st->pca_Z);
     }
     AEM_CUDA_TRY(cudaGetLastError());
     pca_bracket_kernel<<<blocks_for(nb, 128), 128, 0, st->stream>>>(st->pca_ok, st->pca_a, nb, 3.0, st->pca_lo,
