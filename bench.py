@@ -176,12 +176,13 @@ def cpu_baseline(target_seconds=15.0):
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
-                  reduce=None, n_langevin=0, graph=False):
+                  reduce=None, n_langevin=0, graph=False, adaptive=None):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
     (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s.  With
     n_langevin > 0 every stage ends with that many adjoint-driven Langevin
-    sweeps (adapted step)."""
+    sweeps (adapted step); adaptive: smc_desc fields of the adaptive proposal
+    (fit and scale bisection, recycling window, ZCA mixture)."""
     from paper_2109_00661_gb300 import smc as S
     sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
     lms = kappa_max + lambda_max + 1
@@ -192,7 +193,8 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
         y_true = np.repeat(y_true, n_soundings, axis=0)
     y_obs = np.stack([I.noisy(y_true[s], seed=1000 + s) for s in range(n_soundings)])
     sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n_soundings,
-               kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps, n_langevin=n_langevin)
+               kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps, n_langevin=n_langevin,
+               **(adaptive or {}))
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -218,6 +220,7 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
            "config": f"{n_soundings} soundings x {n_particles} particles, kappa<={kappa_max}, lambda<={lambda_max}, "
                      f"{sweeps} sweeps/stage" + (f" + {n_langevin} Langevin sweeps/stage" if n_langevin else "") +
                      (", stages in one CUDA graph with a device-side loop condition" if graph else "") +
+                     (", adaptive proposal " + ", ".join(f"{k}={v}" for k, v in adaptive.items()) if adaptive else "") +
                      ", alpha=0.5, sounding system G=20 F=40 K=120",
            "median_log_bfipd": float(np.median(np.clip(lb, -50, 50))),
            "forward_launch_shape": shape,
@@ -544,7 +547,12 @@ def main():
                  combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
                                              reduce=reduce, n_langevin=2) for sd in seeds]),
                  rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
-                               graph=True))
+                               graph=True),
+                 # Section 3.2's adaptive within-model proposal with particle
+                 # recycling over 3 stages and Appendix F's ZCA-coloured
+                 # birth / death in half the trans-dimensional moves
+                 rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
+                               adaptive=dict(adaptive=1, recycle_stages=3, zca=0.5)))
 
     if rank == 0:
         flops = steps_work * FLOPS_PER_LAYER_STEP
@@ -580,7 +588,8 @@ def main():
         if fp64 is not None:
             line["fp64_plain"] = fp64
         if rjsmc is not None:
-            line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"], line["rjsmc_graph"] = rjsmc
+            (line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"], line["rjsmc_graph"],
+             line["rjsmc_adaptive"]) = rjsmc
         if adjoint is not None:
             line["adjoint"] = adjoint
         if transforms is not None:
