@@ -168,6 +168,27 @@ def test_gradient_odd_hankel_count(setup):
     check(g.cpu().numpy().astype(np.float64), g_ref, "K = 121", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
 
 
+def test_gradient_maximum_sizes(setup):
+    """F = 128, G = 64, K = 512 and 20 merged layers (the adjoint's shared
+    tables about 182 KB, one CTA per SM, the 20-layer kernel): 3 models against
+    the oracle's central differences."""
+    torch, L, _, _, _ = setup
+    name = "forward-g30-f60-k200"
+    sysg = L.System(**dict(I.system_kwargs(name), n_freq=128, gate_times=I.gate_times(64), n_hankel=512))
+    s = I.oracle_system(name)
+    s.update(freqs=np.exp(np.linspace(np.log(I.F_MIN_HZ), np.log(I.F_MAX_HZ), 128)), times=I.gate_times(64), K=512)
+    s["T"] = O.tmatrix(s["freqs"], s["times"])
+    y_obs = I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=0)
+    models = many_layers(3, seed=12, L=20)
+    _, g_ref = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN)
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    y_model, imh, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    _, J = O.forward_jacobian_fd(models, s)
+    kap = kappa(imh, s["T"], y_model, absh)
+    check(g.cpu().numpy().astype(np.float64), g_ref, "maximum sizes",
+          gradient_bound(y_model, J, y_obs, bound32(kap, 128)))
+
+
 def test_autograd_function(setup):
     """The torch.autograd.Function path returns the adjoint kernel's gradient,
     scaled by the upstream gradient, on every parameter tensor."""

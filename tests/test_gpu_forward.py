@@ -147,6 +147,37 @@ def test_odd_hankel_count(lib, torch_mod):
     assert_within(rel_err(y.cpu().numpy().astype(np.float64), y_ref), bound32(kap, sysg.F), "FP32 gates, K = 121")
 
 
+def max_size_system(lib):
+    """The largest system the library accepts: AEM_MAX_FREQ = 128 frequencies,
+    AEM_MAX_GATES = 64 gates, AEM_MAX_HANKEL = 512 Hankel points, with the
+    oracle's copy of it (its own transform table)."""
+    name = "forward-g30-f60-k200"
+    kw = dict(I.system_kwargs(name), n_freq=128, gate_times=I.gate_times(64), n_hankel=512)
+    s = I.oracle_system(name)
+    s.update(freqs=np.exp(np.linspace(np.log(I.F_MIN_HZ), np.log(I.F_MAX_HZ), 128)), times=I.gate_times(64), K=512)
+    s["T"] = O.tmatrix(s["freqs"], s["times"])
+    return lib.System(**kw), s
+
+
+def test_maximum_sizes(lib, torch_mod):
+    """F = 128, G = 64, K = 512 and 20 merged layers (the forward kernel's
+    shared-memory tables are then about 206 KB, one CTA per SM): FP32 and FP64
+    gates against the oracle."""
+    sysg, s = max_size_system(lib)
+    models = I.random_models(40, seed=31, lmax=20, layers_max=20)
+    models["nlayers"][:8] = 20
+    y_ref, imh_ref, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    kap = kappa(imh_ref, s["T"], y_ref, absh)
+    y64 = lib.forward_f64(sysg, I.to_torch(models, torch_mod.float64)).cpu().numpy()
+    assert_within(rel_err(y64, y_ref), bound64(kap), "FP64 gates, maximum sizes")
+    m32 = as_f32_inputs(models)
+    y_ref, imh_ref, absh = O.forward(m32, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
+    kap = kappa(imh_ref, s["T"], y_ref, absh)
+    y, imh = lib.forward_f32(sysg, I.to_torch(m32, torch_mod.float32), want_imh=True)
+    assert spectrum_err(imh.cpu().numpy().astype(np.float64), imh_ref, absh).max() < DELTA_S32
+    assert_within(rel_err(y.cpu().numpy().astype(np.float64), y_ref), bound32(kap, 128), "FP32 gates, maximum sizes")
+
+
 def test_pelton_form(lib, torch_mod):
     name = "sounding-g20-f40-k120"
     models = I.random_models(40, seed=11)
