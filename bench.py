@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-rjsmc", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 form, gate-transform variants, bucketed order and adjoint measurements")
-    ap.add_argument("--rjsmc-only", action="store_true", help="run only the RJSMC measurement (profiling)")
+    ap.add_argument("--rjsmc-only", nargs="?", const="fixed", choices=["fixed", "adaptive"],
+                    help="run only one RJSMC measurement, 128 x 256 (profiling): the fixed-scale moves, or the "
+                         "adaptive proposal with recycling and ZCA moves")
     ap.add_argument("--convergence-study", action="store_true",
                     help="fraction of soundings whose best particle reaches the truth's likelihood level, per "
                          "sampler setting (8 soundings of the 3-layer data, 2 seeds)")
@@ -353,7 +355,9 @@ def main():
         print(json.dumps({"convergence_study": convergence_study(torch, L, I)}), flush=True)
         return
     if args.rjsmc_only:
-        print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer())}), flush=True)
+        ad = dict(adaptive=1, recycle_stages=3, zca=0.5) if args.rjsmc_only == "adaptive" else None
+        print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), adaptive=ad)}),
+              flush=True)
         return
     sysg = L.System(**I.system_kwargs(WORKLOAD))
     F, K, G = sysg.F, sysg.K, sysg.G
