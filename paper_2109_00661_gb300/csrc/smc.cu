@@ -62,8 +62,7 @@ __host__ __device__ inline Key stream_key(unsigned long long seed, int sounding)
 // Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC 2011).
 __host__ __device__ inline void philox(uint32_t c[4], Key key) {
     uint32_t k0 = key.k0, k1 = key.k1;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 0; r < 10; ++r) {  // fixed trip count: unrolled by the compiler
         uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
         uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
         uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
