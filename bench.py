@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--convergence-study", action="store_true",
                     help="fraction of soundings whose best particle reaches the truth's likelihood level, per "
                          "sampler setting (8 soundings of the 3-layer data, 2 seeds)")
+    ap.add_argument("--detectability", action="store_true",
+                    help="run only the synthetic detectability study: log BFIPD over layer depth x chargeability "
+                         "for the four basement conductivities, all soundings in one sampler")
     ap.add_argument("--flight-line", type=int, default=0, metavar="S",
                     help="run only the flight-line sampler: S soundings x 2048 particles in one sampler")
     return ap.parse_args()
@@ -252,6 +255,40 @@ def combine_runs(runs):
     return out
 
 
+def detectability_study(torch, L, I, n_particles=2048):
+    """Section 4.1's synthetic study: the 3-layer earth with its chargeable
+    second layer (20 m, 0.1 S/m, tau = 4.07e-4 s, c = 1) at 6 depths x 6
+    chargeabilities over each of the four basements, 144 soundings in one
+    sampler (N per sounding, kappa <= 3, lambda <= 4, 10 sweeps per stage,
+    log-uniform tau prior); returns the log BFIPD grid and the timing."""
+    from paper_2109_00661_gb300 import smc as S
+    depths, ms = [10.0, 20.0, 30.0, 40.0, 60.0, 80.0], [0.0, 0.1, 0.2, 0.3, 0.5, 0.8]
+    grids = [I.detectability_grid(depths, ms, b) for b in I.DETECT_BASEMENTS]
+    truth = {k: np.concatenate([g[k] for g in grids]) for k in grids[0]}
+    n = len(truth["nlayers"])
+    sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
+    lms = 3 + 4 + 1
+    sysg.autotune(I.to_torch(I.random_models(1 << 15, seed=9, lmax=lms, layers_max=lms), torch.float32))
+    y = L.forward_f32(sysg, I.to_torch(truth, torch.float32)).cpu().numpy().astype(np.float64)
+    y_obs = np.stack([I.noisy(y[s], seed=3000 + s) for s in range(n)])
+    sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n, kappa_max=3, lambda_max=4,
+               seed=0, r_max=10, tau_log_prior=1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    sm.init()
+    stages = sm.run(max_stages=500, n_sweeps=10)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    _, lb, _ = sm.model_odds()
+    grid = np.clip(lb, -50, 50).reshape(len(I.DETECT_BASEMENTS), len(depths), len(ms))
+    return {"depths_m": depths, "chargeability": ms, "basement_S_per_m": list(I.DETECT_BASEMENTS),
+            "log_bfipd": np.round(grid, 2).tolist(), "soundings": n, "particles_per_sounding": n_particles,
+            "stages": stages, "seconds": sec, "soundings_per_s": n / sec}
+
+
 def convergence_study(torch, L, I):
     """8 noisy copies of the 3-layer sounding, N = 256, kappa <= 3, lambda <= 4:
     for each sampler setting and seed, the fraction of soundings whose best
@@ -346,6 +383,9 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.detectability:
+        print(json.dumps({"detectability": detectability_study(torch, L, I)}), flush=True)
+        return
     if args.flight_line:
         truth, _ = I.flight_line(args.flight_line)
         out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth)

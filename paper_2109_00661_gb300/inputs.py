@@ -109,6 +109,28 @@ def subset(models, idx):
     return {k: np.asarray(v)[idx] for k, v in models.items()}
 
 
+DETECT_BASEMENTS = (0.001, 0.01, 0.032, 0.1)  # S/m: igneous, hard sedimentary, moderate, conductive
+
+
+def detectability_grid(depths, ms, basement_sigma, tau=4.07e-4, c=1.0):
+    """The synthetic detectability study (Section 4.1): a 3-layer earth with
+    sigma 0.01 S/m over a 20 m thick chargeable layer of 0.1 S/m whose top is at
+    the given depth, over a basement of basement_sigma S/m; Cole-Cole tau and c
+    fixed, chargeability m in the second layer only.  One sounding per
+    (depth, m) pair, depth-major."""
+    D, Mv = np.meshgrid(np.asarray(depths, dtype=np.float64), np.asarray(ms, dtype=np.float64), indexing="ij")
+    D, Mv = D.ravel(), Mv.ravel()
+    S = D.size
+    return dict(
+        nlayers=np.full(S, 3, dtype=np.int8),
+        logsig=np.tile(np.log10([0.01, 0.1, basement_sigma]), (S, 1)),
+        logh=np.stack([np.log10(D), np.full(S, np.log10(20.0)), np.zeros(S)], axis=1),
+        m=np.stack([np.zeros(S), Mv, np.zeros(S)], axis=1),
+        logtau=np.full((S, 3), np.log10(tau)),
+        c=np.full((S, 3), c),
+    )
+
+
 def flight_line(n_soundings):
     """Synthetic flight line: sounding s at x = s / (S - 1) over a 3-layer earth
     (sigma 0.01, 0.1, 0.01 S/m) whose chargeable second layer (30 m thick,
