@@ -60,7 +60,6 @@ __device__ __forceinline__ C2x2 c2(u64 re, u64 im) {
 __device__ __forceinline__ C2x2 c2add(C2x2 a, C2x2 b) { return c2(add2(a.re, b.re), add2(a.im, b.im)); }
 __device__ __forceinline__ C2x2 c2neg(C2x2 a) { return c2(sub2(kZero2, a.re), sub2(kZero2, a.im)); }
 __device__ __forceinline__ C2x2 c2add1(C2x2 a) { return c2(add2(kOne2, a.re), a.im); }         // 1 + a
-__device__ __forceinline__ C2x2 c2sub1(C2x2 a) { return c2(sub2(kOne2, a.re), sub2(kZero2, a.im)); }  // 1 - a
 __device__ __forceinline__ C2x2 c2mul(C2x2 a, C2x2 b) {
     return c2(sub2(mul2(a.re, b.re), mul2(a.im, b.im)), fma2(a.re, b.im, mul2(a.im, b.re)));
 }
@@ -72,6 +71,10 @@ __device__ __forceinline__ C2x2 c2sq(C2x2 a) {
     return c2(mul2(sub2(a.re, a.im), add2(a.re, a.im)), add2(t, t));
 }
 __device__ __forceinline__ C2x2 c2scale(C2x2 a, u64 s) { return c2(mul2(a.re, s), mul2(a.im, s)); }
+constexpr u64 kMinus2 = 0xc0000000c0000000ull;  // (-2, -2)
+__device__ __forceinline__ C2x2 c2one_minus_sq(C2x2 a) {  // 1 - a^2
+    return c2(fma2(a.im, a.im, sub2(kOne2, mul2(a.re, a.re))), mul2(mul2(a.re, a.im), kMinus2));
+}
 __device__ __forceinline__ u64 c2inorm(C2x2 a) {  // 1 / |a|^2
     float m0, m1;
     up2(fma2(a.re, a.re, mul2(a.im, a.im)), m0, m1);
@@ -80,7 +83,7 @@ __device__ __forceinline__ u64 c2inorm(C2x2 a) {  // 1 / |a|^2
 __device__ __forceinline__ C2x2 c2div(C2x2 x, C2x2 a) { return c2scale(c2mulc(x, a), c2inorm(a)); }
 
 // Principal root u of z = lambda^2 + s (Im s > 0) for both abscissae, and
-// 1 / |z| (= 1 / |u|^2).  With t = (|z| + |x|) / 2 the pair
+// 1 / (2 |z|) (= 1 / (2 |u|^2), for du/ds = 1 / (2 u) = conj(u) / (2 |z|)).  With t = (|z| + |x|) / 2 the pair
 // (sqrt t, Im s / (2 sqrt t)) is (Re u, Im u) when x = Re z >= 0 and
 // (Im u, Re u) otherwise.  s = ((Re s, Re s), (Im s, Im s)), y2 = (Im s)^2.
 __device__ __forceinline__ C2x2 c2root(u64 lam2, ulonglong2 s, u64 y2, u64 &inv_mod) {
@@ -90,7 +93,7 @@ __device__ __forceinline__ C2x2 c2root(u64 lam2, ulonglong2 s, u64 y2, u64 &inv_
     up2(v, v0, v1);
     up2(x, x0, x1);
     const u64 rv = pk2(rsqrt_approx(v0), rsqrt_approx(v1));  // v = |z|^2
-    inv_mod = rv;
+    inv_mod = mul2(rv, kHalf2);
     const u64 t = mul2(add2(mul2(v, rv), pk2(fabsf(x0), fabsf(x1))), kHalf2);
     float t0, t1;
     up2(t, t0, t1);
@@ -294,9 +297,9 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                 const ulonglong2 sj = Sf[j];
                 const C2x2 q = c2add(up, uj);
                 const u64 iqn = c2inorm(q);
-                const C2x2 iq = c2(mul2(q.re, iqn), mul2(sub2(kZero2, q.im), iqn));  // 1 / q
-                const C2x2 iq2 = c2sq(iq);
-                const C2x2 rho = c2mul(c2(sub2(sp.x, sj.x), sub2(sp.y, sj.y)), iq2);
+                const C2x2 iqc = c2scale(q, iqn);  // conj(1 / q)
+                const C2x2 iq2c = c2sq(iqc);       // conj(1 / q^2)
+                const C2x2 rho = c2mulc(c2(sub2(sp.x, sj.x), sub2(sp.y, sj.y)), iq2c);
                 C2x2 rbar, ubar_j = c2(kZero2, kZero2), gnext = ubar_j;
                 if (j < L - 1) {
                     const ulonglong2 he = HE[j];
@@ -304,8 +307,8 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                     const C2x2 b = c2mul(Gam[j + 1], E);
                     // d Gamma_j / d rho = (1 - b^2) / den^2, d Gamma_j / d b = (1 - rho^2) / den^2
                     const C2x2 g2 = c2div(gbar, c2sq(c2add1(c2mul(rho, b))));
-                    rbar = c2mul(g2, c2sub1(c2sq(b)));
-                    const C2x2 tbar = c2mul(g2, c2sub1(c2sq(rho)));
+                    rbar = c2mul(g2, c2one_minus_sq(b));
+                    const C2x2 tbar = c2mul(g2, c2one_minus_sq(rho));
                     // tb = tbar b = (d Gamma_0 / d E_j) E_j: d / d u_j through E_j is -2 h tb
                     const C2x2 tb = c2mul(tbar, b);
                     gnext = c2mul(tbar, E);
@@ -317,13 +320,13 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                     rbar = gbar;
                 }
                 // d rho / d u_{j-1} = d rho / d u_j = -2 rho / q; d rho / d s_{j-1} = 1 / q^2 = -d rho / d s_j
-                const C2x2 rq = c2mul(rho, iq);
-                const C2x2 dq = c2mul(rbar, c2(sub2(kZero2, add2(rq.re, rq.re)), sub2(kZero2, add2(rq.im, rq.im))));
-                const C2x2 rbi = c2mul(rbar, iq2);
+                // dq2 = rbar rho / q, so the rho term of d / d u is -2 dq2
+                const C2x2 dq2 = c2mul(rbar, c2mulc(rho, iqc));
+                const C2x2 rbi = c2mulc(rbar, iq2c);
                 if (j > 0) {
                     // layer j-1 complete: s enters through u as well, du/ds = 1 / (2 u) = conj(u) / (2 |z|)
-                    ubar_p = c2add(ubar_p, dq);
-                    sbar_p = c2add(c2add(sbar_p, rbi), c2scale(c2mulc(ubar_p, up), mul2(imod_up, kHalf2)));
+                    ubar_p = c2(fma2(dq2.re, kMinus2, ubar_p.re), fma2(dq2.im, kMinus2, ubar_p.im));
+                    sbar_p = c2add(c2add(sbar_p, rbi), c2scale(c2mulc(ubar_p, up), imod_up));
                     float x0, x1, y0, y1;
                     up2(mul2(wgt, sbar_p.re), x0, x1);
                     up2(mul2(wgt, sbar_p.im), y0, y1);
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                     ac[4] += fmaf(swx, d23.w, swy * d23.z);
                 }
                 sbar_p = c2neg(rbi);
-                ubar_p = c2add(ubar_j, dq);
+                ubar_p = c2(fma2(dq2.re, kMinus2, ubar_j.re), fma2(dq2.im, kMinus2, ubar_j.im));
                 up = uj;
                 imod_up = imod;
                 sp = sj;
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                 if (j + 1 < L) uj = c2root(lp.x, Sf[j + 1], Yf[j + 1], imod);
             }
             {
-                sbar_p = c2add(sbar_p, c2scale(c2mulc(ubar_p, up), mul2(imod_up, kHalf2)));
+                sbar_p = c2add(sbar_p, c2scale(c2mulc(ubar_p, up), imod_up));
                 float x0, x1, y0, y1;
                 up2(mul2(wgt, sbar_p.re), x0, x1);
                 up2(mul2(wgt, sbar_p.im), y0, y1);
