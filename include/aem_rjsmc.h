@@ -43,7 +43,10 @@ typedef enum {
  * and notes Pelton's form is a bijective reparameterisation of it. */
 typedef enum {
     AEM_CC_PAPER = 0, /* log10 sigma parameter is log10 sigma_inf (high-frequency) */
-    AEM_CC_PELTON = 1 /* 1/rho, rho = rho_0 (1 - m (1 - 1/(1 + (i w tau)^c))); parameter is log10 sigma_0 (DC) */
+    AEM_CC_PELTON = 1, /* 1/rho, rho = rho_0 (1 - m (1 - 1/(1 + (i w tau)^c))); parameter is log10 sigma_0 (DC) */
+    AEM_CC_LITERAL = 2 /* sigma_0 (1 - m (1 - 1/(1 + (i w tau)^c))) taken as a conductivity: sigma_0 at DC,
+                          sigma_0 (1 - m) at high frequency (the paper's form with sigma_inf = sigma_0 (1 - m) and
+                          chargeability -m / (1 - m)) */
 } aem_cc_form;
 
 /* Limits compiled into the kernels. */

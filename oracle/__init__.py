@@ -93,7 +93,8 @@ HANKEL_RULE = 2
 
 
 def colecole(form, sig, m, tau, c, w):
-    """Complex conductivity (Section 2).  form 0: paper, 1: Pelton resistivity."""
+    """Complex conductivity (Section 2).  form 0: paper, 1: Pelton resistivity,
+    2: Pelton's expression taken as a conductivity."""
     out = np.zeros(2)
     lib().orc_colecole(int(form), float(sig), float(m), float(tau), float(c), float(w), _ptr(out))
     return complex(out[0], out[1])

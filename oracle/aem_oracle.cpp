@@ -150,12 +150,14 @@ static V wynn_epsilon(const std::vector<V> &s) {
 // Cole-Cole complex conductivity (Section 2).
 // form 0: paper's form   s_inf * (1 - m / (1 + (i w tau)^c))       (sig = s_inf)
 // form 1: Pelton (1978)  1 / rho,  rho = (1/s0)(1 - m (1 - 1/(1 + (i w tau)^c)))  (sig = s0)
+// form 2: the expression s0 (1 - m (1 - 1/(1 + (i w tau)^c))) taken as a conductivity
 // ---------------------------------------------------------------------------
 static cd colecole(int form, double sig, double m, double tau, double c, double w) {
     if (m == 0.0) return cd(sig, 0.0);
     cd iwt_c = std::pow(w * tau, c) * std::exp(cd(0.0, 0.5 * PI * c));
     cd one(1.0, 0.0);
     if (form == 0) return sig * (one - m / (one + iwt_c));
+    if (form == 2) return sig * (one - m * (one - one / (one + iwt_c)));
     return sig / (one - m * (one - one / (one + iwt_c)));
 }
 

@@ -21,6 +21,7 @@ __all__ = ["System", "forward_f32", "forward_f64", "spectrum_f32", "loglik_f32",
 
 CC_PAPER = 0
 CC_PELTON = 1
+CC_LITERAL = 2
 GATES_FP32 = 0
 GATES_TF32_SPLIT = 1
 GATES_BF16_SPLIT = 2

@@ -218,6 +218,11 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                     // sigma_inf (1 - m / (1 + x))
                     sr = sig * (R(1) - mm * xr / den);
                     si = sig * (mm * xi / den);
+                } else if (cc_form == AEM_CC_LITERAL) {
+                    // sigma_0 (1 + (1 - m) x) / (1 + x)
+                    R br = R(1) + (R(1) - mm) * mag * cp, bi = (R(1) - mm) * mag * sp;
+                    sr = sig * (br * xr + bi * xi) / den;
+                    si = sig * (bi * xr - br * xi) / den;
                 } else {
                     // sigma_0 (1 + x) / (1 + (1 - m) x)
                     R br = R(1) + (R(1) - mm) * mag * cp, bi = (R(1) - mm) * mag * sp;
@@ -534,6 +539,10 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 if (cc_form == AEM_CC_PAPER) {
                     sr = sig * (1.f - mm * xr / den);
                     si = sig * (mm * xi / den);
+                } else if (cc_form == AEM_CC_LITERAL) {
+                    const float br = 1.f + (1.f - mm) * mag * cp, bi = (1.f - mm) * mag * sp;
+                    sr = sig * (br * xr + bi * xi) / den;
+                    si = sig * (bi * xr - br * xi) / den;
                 } else {
                     const float br = 1.f + (1.f - mm) * mag * cp, bi = (1.f - mm) * mag * sp;
                     const float bd = br * br + bi * bi;

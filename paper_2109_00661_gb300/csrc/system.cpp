@@ -123,7 +123,7 @@ int build_tables(const aem_system_desc *d, SystemTables *t) {
         return fail(AEM_ERR_INVALID_ARG, "aem_system_create: n_hankel out of range");
     if (!(d->f_min_hz > 0) || !(d->f_max_hz > d->f_min_hz))
         return fail(AEM_ERR_INVALID_ARG, "aem_system_create: need 0 < f_min_hz < f_max_hz");
-    if (d->cc_form != AEM_CC_PAPER && d->cc_form != AEM_CC_PELTON)
+    if (d->cc_form != AEM_CC_PAPER && d->cc_form != AEM_CC_PELTON && d->cc_form != AEM_CC_LITERAL)
         return fail(AEM_ERR_INVALID_ARG, "aem_system_create: unknown cc_form");
     for (int g = 0; g < d->n_gates; ++g) {
         if (!(d->gate_times[g] > 0) || (g > 0 && !(d->gate_times[g] > d->gate_times[g - 1])))

@@ -178,12 +178,20 @@ def test_maximum_sizes(lib, torch_mod):
     assert_within(rel_err(y.cpu().numpy().astype(np.float64), y_ref), bound32(kap, 128), "FP32 gates, maximum sizes")
 
 
-def test_pelton_form(lib, torch_mod):
+@pytest.mark.parametrize("form", [1, 2])
+def test_other_colecole_forms(lib, torch_mod, form):
+    """Pelton's resistivity form (1) and Pelton's expression taken as a
+    conductivity (2): FP64 and FP32 gates against the oracle."""
     name = "sounding-g20-f40-k120"
     models = I.random_models(40, seed=11)
-    y_ref, _, _, kap = oracle_ref(models, name, cc_form=1)
-    y = lib.forward_f64(gpu_system(lib, name, cc_form=1), I.to_torch(models, torch_mod.float64)).cpu().numpy()
-    assert_within(rel_err(y, y_ref), bound64(kap), "FP64 gates (Pelton)")
+    sysg = gpu_system(lib, name, cc_form=form)
+    y_ref, _, _, kap = oracle_ref(models, name, cc_form=form)
+    y = lib.forward_f64(sysg, I.to_torch(models, torch_mod.float64)).cpu().numpy()
+    assert_within(rel_err(y, y_ref), bound64(kap), f"FP64 gates (form {form})")
+    m32 = as_f32_inputs(models)
+    y_ref, _, _, kap = oracle_ref(m32, name, cc_form=form)
+    y = lib.forward_f32(sysg, I.to_torch(m32, torch_mod.float32)).cpu().numpy().astype(np.float64)
+    assert_within(rel_err(y, y_ref), bound32(kap, sysg.F), f"FP32 gates (form {form})")
 
 
 def test_imh_output_and_determinism(lib, torch_mod):

@@ -56,6 +56,30 @@ def test_colecole_paper_pelton_bijection():
         assert abs(pel - pap) <= 1e-12 * abs(pel)
 
 
+def test_colecole_literal_form():
+    """Pelton's expression taken as a conductivity (form 2): sigma_0 at DC and
+    sigma_0 (1 - m) at high frequency, the paper's form with sigma_inf =
+    sigma_0 (1 - m) and chargeability -m / (1 - m), and the product with
+    Pelton's form (the reciprocal of the same expression times sigma_0^2)
+    equal to sigma_0^2."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        s0 = 10 ** rng.uniform(-4, 0)
+        m = rng.uniform(0.01, 0.95)
+        tau = 10 ** rng.uniform(-6, -1)
+        c = rng.uniform(0.1, 1.0)
+        w = 10 ** rng.uniform(0, 8)
+        lit = O.colecole(2, s0, m, tau, c, w)
+        pap = O.colecole(0, s0 * (1 - m), -m / (1 - m), tau, c, w)
+        assert abs(lit - pap) <= 1e-12 * abs(lit)
+        assert abs(lit * O.colecole(1, s0, m, tau, c, w) - s0 * s0) <= 1e-12 * s0 * s0
+        assert lit.real > 0 and lit.imag < 0  # the conductivity falls with frequency
+    s0, m, tau, c = 0.05, 0.4, 1e-3, 0.6
+    assert abs(O.colecole(2, s0, m, tau, c, 1e-12) - s0) < 1e-6 * s0
+    assert abs(O.colecole(2, s0, m, tau, c, 1e15) - s0 * (1 - m)) < 1e-3 * s0
+    assert O.colecole(2, s0, 0.0, tau, c, 123.0) == complex(s0, 0.0)
+
+
 # --------------------------------------------------------------- recursion forms
 def test_reflection_matches_admittance_recursion():
     rng = np.random.default_rng(4)
