@@ -198,8 +198,8 @@ int aem_system_status(const aem_system *sys, int *status);
  * grad: [device] P*lmax*5 floats, row-major [model][layer][parameter] with
  * parameters (log10 sigma, log10 thickness, m, log10 tau, c); the basement's
  * thickness entry and layers >= nlayers are 0.  ll: [device] P doubles (may
- * be NULL).  Only the paper's Cole-Cole form (AEM_CC_PAPER) is supported;
- * other forms return AEM_ERR_UNSUPPORTED. */
+ * be NULL).  Every aem_cc_form is differentiated (log10 sigma is the form's
+ * conductivity parameter). */
 int aem_loglik_grad_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                         const double *eps_an, double eps_mn, double *ll, float *grad, void *stream);
 

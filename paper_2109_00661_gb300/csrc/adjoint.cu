@@ -144,7 +144,7 @@ size_t grad_smem_bytes(int F, int G, int K, int LS) {
 // resident CTAs per SM (80 registers) measured faster than two (128
 // registers, no spills) and four (64 registers, 200 bytes spilled).
 template <int MAXL>
-__global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS,
+__global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int F, int G, int K, int LS, int cc_form,
                                                           const float *__restrict__ g_omega,
                                                           const float *__restrict__ g_lam,
                                                           const float *__restrict__ g_hw,
@@ -200,8 +200,11 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
             c_s[tid] = mv.c[o];
         }
         __syncthreads();
-        // Cole-Cole (paper form) and its derivatives, per (frequency, layer):
-        // sig = s_inf (1 - m / (1 + x)), x = (w tau)^c e^{i pi c / 2}, s = i w mu0 sig
+        // Cole-Cole and its derivatives, per (frequency, layer), with
+        // x = (w tau)^c e^{i pi c / 2} and s = i w mu0 sig:
+        //   paper   sig = s_inf (1 - m / (1 + x))
+        //   Pelton  sig = s_0 (1 + x) / (1 + (1 - m) x)
+        //   literal sig = s_0 (1 + (1 - m) x) / (1 + x)
         for (int i = tid; i < F * L; i += blockDim.x) {
             const int f = i / L, n = i - f * L;
             const float w = g_omega[f];
@@ -212,10 +215,24 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
             sincospif(0.5f * cc, &sp, &cp);
             const float2 x = make_float2(mag * cp, mag * sp);
             const float2 ix1 = crcp(make_float2(1.f + x.x, x.y));  // 1 / (1 + x)
-            const float2 sg = make_float2(si * (1.f - mm * ix1.x), -si * mm * ix1.y);
-            const float2 dsg_dm = cscale(ix1, -si);
-            const float2 ix1sq = cmul(ix1, ix1);
-            const float2 dsg_dx = cscale(ix1sq, si * mm);                 // s_inf m / (1 + x)^2
+            float2 sg, dsg_dm, dsg_dx;
+            if (cc_form == AEM_CC_PAPER) {
+                sg = make_float2(si * (1.f - mm * ix1.x), -si * mm * ix1.y);
+                dsg_dm = cscale(ix1, -si);
+                dsg_dx = cscale(cmul(ix1, ix1), si * mm);                // s_inf m / (1 + x)^2
+            } else {
+                const float2 b = make_float2(1.f + (1.f - mm) * x.x, (1.f - mm) * x.y);  // 1 + (1 - m) x
+                if (cc_form == AEM_CC_PELTON) {
+                    const float2 ib = crcp(b);
+                    sg = cscale(cmul(make_float2(1.f + x.x, x.y), ib), si);
+                    dsg_dm = cmul(sg, cmul(x, ib));                      // sig x / (1 + (1 - m) x)
+                    dsg_dx = cscale(cmul(ib, ib), si * mm);              // s_0 m / (1 + (1 - m) x)^2
+                } else {
+                    sg = cscale(cmul(b, ix1), si);
+                    dsg_dm = cscale(cmul(x, ix1), -si);                  // -s_0 x / (1 + x)
+                    dsg_dx = cscale(cmul(ix1, ix1), -si * mm);           // -s_0 m / (1 + x)^2
+                }
+            }
             const float2 dx_dlt = cscale(x, cc * ln10);                   // d x / d log10 tau
             const float2 dx_dc = cmul(x, make_float2(lwt, 1.57079632679489662f));
             const float2 iwm = make_float2(0.f, w * mu0);                 // i w mu0
@@ -400,8 +417,6 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
                               cudaStream_t stream, void *work_ext) {
     const SystemTables &h = sys->host;
-    if (h.cc_form != AEM_CC_PAPER)
-        return fail(AEM_ERR_UNSUPPORTED, "aem_loglik_grad_f32: only the paper's Cole-Cole form is differentiated");
     const int LS = models->lmax;
     const size_t smem = grad_smem_bytes(h.F, h.G, h.K, LS);
     auto kern = LS <= 10 ? loglik_grad_kernel<10> : loglik_grad_kernel<AEM_MAX_LAYERS>;
@@ -424,7 +439,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     if (rc == AEM_OK) {
         e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
         if (e == cudaSuccess) {
-            kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, sys->d_omega_f, sys->d_lam_f,
+            kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, h.cc_form, sys->d_omega_f, sys->d_lam_f,
                                                         sys->d_hw_f, sys->d_T_f, y_obs, models_per_sounding, eps_an,
                                                         eps_mn, gates, grad, counter);
             e = cudaGetLastError();

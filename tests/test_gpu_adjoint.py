@@ -107,7 +107,7 @@ def test_gradient_matches_fd_of_gpu_fp64(setup):
     check(g, ref, "4 layers vs FD of the GPU FP64 forward", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
 
 
-def test_gradient_zero_padding_and_unsupported_form(setup):
+def test_gradient_zero_padding(setup):
     torch, L, sysg, s, y_obs = setup
     models = near_truth(4, seed=3, L=3)
     for k in ("logsig", "logh", "m", "logtau", "c"):
@@ -115,9 +115,22 @@ def test_gradient_zero_padding_and_unsupported_form(setup):
     _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
     g = g.cpu().numpy()
     assert np.all(g[:, 3:, :] == 0) and np.all(g[:, 2, 1] == 0)
-    pel = L.System(**I.system_kwargs(NAME), cc_form=L.CC_PELTON)
-    with pytest.raises(L.AEMError):
-        L.loglik_grad_f32(pel, I.to_torch(near_truth(2, seed=4), torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_gradient_other_colecole_forms(setup, form):
+    """Pelton's form (1) and Pelton's expression as a conductivity (2): the
+    adjoint against the oracle's central differences of the same form."""
+    torch, L, _, _, y_obs = setup
+    sysg = L.System(**I.system_kwargs(NAME), cc_form=form)
+    s = oracle_system(NAME, cc_form=form)
+    models = near_truth(8, seed=20 + form, L=3)
+    _, g_ref = O.loglik_grad_fd(models, s, y_obs, I.EPS_AN, I.EPS_MN)
+    _, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    y_model, _, _, kap = oracle_ref(models, NAME, cc_form=form)
+    _, J = O.forward_jacobian_fd(models, s)
+    check(g.cpu().numpy().astype(np.float64), g_ref, f"Cole-Cole form {form}",
+          gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
 
 
 def many_layers(P, seed, L):
