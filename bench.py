@@ -388,7 +388,8 @@ def main():
         return
     if args.flight_line:
         truth, _ = I.flight_line(args.flight_line)
-        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth)
+        # all soundings in one sampler, its stage loop one captured CUDA graph
+        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth, graph=True)
         print(json.dumps({"flight_line": out}), flush=True)
         return
     if args.convergence_study:
