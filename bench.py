@@ -181,7 +181,7 @@ def cpu_baseline(target_seconds=15.0):
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
-                  reduce=None, n_langevin=0, graph=False, adaptive=None):
+                  reduce=None, n_langevin=0, graph=False, adaptive=None, per_sounding=False):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
     (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s.  With
@@ -231,6 +231,8 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
            "forward_launch_shape": shape,
            "langevin": lang,
            "mean_p_ip": float(np.mean(post.reshape(n_soundings, kappa_max + 1, lambda_max + 1)[:, :, 1:].sum(axis=(1, 2))))}
+    if per_sounding:  # clipped at +-50 (every particle on one side)
+        out["log_bfipd"] = np.clip(lb, -50, 50).tolist()
     sm.close()
     sysg.close()
     return out
@@ -387,9 +389,13 @@ def main():
         print(json.dumps({"detectability": detectability_study(torch, L, I)}), flush=True)
         return
     if args.flight_line:
-        truth, _ = I.flight_line(args.flight_line)
+        truth, x = I.flight_line(args.flight_line)
         # all soundings in one sampler, its stage loop one captured CUDA graph
-        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth, graph=True)
+        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth, graph=True, per_sounding=True)
+        # the section's IP odds along the line, at 20 evenly spaced soundings
+        lbs = out.pop("log_bfipd")
+        step = max(1, args.flight_line // 20)
+        out["log_bfipd_along_line"] = {f"{x[i]:.3f}": round(float(lbs[i]), 2) for i in range(0, args.flight_line, step)}
         print(json.dumps({"flight_line": out}), flush=True)
         return
     if args.convergence_study:
