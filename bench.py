@@ -630,7 +630,13 @@ def main():
                          "traffic": (13221632.0 / 65536 * P) if shape == 5 else None,
                          "traffic_unit": "bytes per launch",
                          "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
-                         "mufu_frac": mufu_frac, "layer_steps_per_s": steps_work / (ms * 1e-3)},
+                         "mufu_frac": mufu_frac,
+                         # the two-pipe roofline: the batch cannot take less than
+                         # max(FP32 ops / FP32 peak, MUFU ops / MUFU peak); the
+                         # fraction of that bound the launch reaches, and its pipe
+                         "roofline_time_frac": max(achieved / peak, mufu_frac),
+                         "binding_pipe": "mufu" if mufu_frac > achieved / peak else "fp32",
+                         "layer_steps_per_s": steps_work / (ms * 1e-3)},
             "gpu_launches": args.steps,
             "clocks": clocks,
             "peaks_measured": peaks,
