@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "aem_internal.h"
 #include "f32x2.h"
@@ -418,11 +419,15 @@ __device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulong
     D.im = Dy;
 }
 
-// Im R_0 for the two abscissae of one work item.
+// Im R_0 for the two abscissae of one work item.  LT > 0: the layer count is
+// the compile-time LT and the layer loop is unrolled completely (the record
+// offsets become immediates); LT = 0: the runtime L.
+template <int LT>
 __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 *__restrict__ RS,
                                            const u64 *__restrict__ RY, const ulonglong2 *__restrict__ RB,
                                            const ulonglong2 *__restrict__ RC, ulonglong2 RAB, ulonglong2 RAC,
-                                           const ulonglong2 *__restrict__ HE, int L, float &out0, float &out1) {
+                                           const ulonglong2 *__restrict__ HE, int L_rt, float &out0, float &out1) {
+    const int L = LT > 0 ? LT : L_rt;
     const C2x2 air = {wair, 0ull};
     ulonglong2 a = RS[L - 1];
     C2x2 wb = wroot2(lam2, a.x, a.y, RY[L - 1]);
@@ -436,14 +441,20 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
     C2x2 D = {pk2(1.f, 1.f), 0ull};
     ulonglong2 he = HE[L - 2];
     wb = wn;
-#pragma unroll 2
-    for (int n = L - 3; n >= 0; --n) {
+    auto step = [&](int n) {
         a = RS[n];
         wn = wroot2(lam2, a.x, a.y, RY[n]);
         const C2x2 r = rcoef2(RB[n], RC[n], wn, wb);
         mobius2(N, D, r, wb, he);
         he = HE[n];
         wb = wn;
+    };
+    if constexpr (LT > 0) {
+#pragma unroll
+        for (int n = LT - 3; n >= 0; --n) step(n);
+    } else {
+#pragma unroll 2
+        for (int n = L - 3; n >= 0; --n) step(n);
     }
     mobius2(N, D, rcoef2(RAB, RAC, air, wb), wb, he);
     float n0, n1, d0, d1;
@@ -574,6 +585,9 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         __syncthreads();
 
         int f = tid / K2, k = tid - (tid / K2) * K2;
+        // the item loop, specialised on the model's layer count up to 10
+        auto items = [&](auto lt) {
+        constexpr int LT = decltype(lt)::value;
         for (int base = 0; base < FK2; base += blockDim.x) {
             const int item = base + tid;
             float val = 0.f;
@@ -583,7 +597,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 const ulonglong2 lw = lamp[k];
                 float r0, r1;
                 const size_t o = (size_t)f * LS;
-                im_r0_pair(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
+                im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
                 const float2 hw = hwp[k];
                 val = fmaf(hw.x, r0, hw.y * r1);
             }
@@ -601,6 +615,20 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 k -= K2;
                 ++f;
             }
+        }
+        };
+        switch (L) {
+            case 1: items(std::integral_constant<int, 1>{}); break;
+            case 2: items(std::integral_constant<int, 2>{}); break;
+            case 3: items(std::integral_constant<int, 3>{}); break;
+            case 4: items(std::integral_constant<int, 4>{}); break;
+            case 5: items(std::integral_constant<int, 5>{}); break;
+            case 6: items(std::integral_constant<int, 6>{}); break;
+            case 7: items(std::integral_constant<int, 7>{}); break;
+            case 8: items(std::integral_constant<int, 8>{}); break;
+            case 9: items(std::integral_constant<int, 9>{}); break;
+            case 10: items(std::integral_constant<int, 10>{}); break;
+            default: items(std::integral_constant<int, 0>{}); break;
         }
         __syncthreads();
         for (int j = tid; j < F; j += blockDim.x) {
