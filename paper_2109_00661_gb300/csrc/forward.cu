@@ -419,6 +419,39 @@ __device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulong
     D.im = Dy;
 }
 
+// rcoef2 for the air above the top layer: w_air = sqrt(2) lambda is real.
+__device__ __forceinline__ C2x2 rcoef2_air(ulonglong2 Bv, ulonglong2 Cv, u64 wair, C2x2 b) {
+    const u64 qx = add2(wair, b.re), qy = b.im;
+    float q0, q1;
+    up2(fma2(qx, qx, mul2(qy, qy)), q0, q1);
+    const u64 ir = pk2(rcp_approx(q0), rcp_approx(q1));
+    const u64 wx = mul2(qx, ir), wy = mul2(qy, ir);
+    const u64 cre = mul2(sub2(wx, wy), add2(wx, wy));
+    const u64 pp = mul2(wx, wy);
+    C2x2 r;
+    r.re = fma2(Bv.x, cre, mul2(Cv.y, pp));
+    r.im = fma2(Bv.y, cre, mul2(Cv.x, pp));
+    return r;
+}
+
+// The first Moebius step, where D = 1: (N, D) <- (r + N E, 1 + r N E).
+__device__ __forceinline__ void mobius2_d1(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
+    float a0, a1, f0, f1;
+    up2(mul2(he.x, wb.re), a0, a1);
+    up2(mul2(he.y, wb.im), f0, f1);
+    float s0, c0, s1, c1;
+    sincos_approx(f0, &s0, &c0);
+    sincos_approx(f1, &s1, &c1);
+    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
+    const u64 Ex = mul2(e, pk2(c0, c1)), Ey = mul2(e, pk2(s0, s1));
+    const u64 Px = sub2(mul2(N.re, Ex), mul2(N.im, Ey));
+    const u64 Py = fma2(N.re, Ey, mul2(N.im, Ex));
+    N.re = add2(r.re, Px);
+    N.im = add2(r.im, Py);
+    D.re = sub2(fma2(r.re, Px, kOne2), mul2(r.im, Py));
+    D.im = fma2(r.re, Py, mul2(r.im, Px));
+}
+
 // Im R_0 for the two abscissae of one work item.  LT > 0: the layer count is
 // the compile-time LT and the layer loop is unrolled completely (the record
 // offsets become immediates); LT = 0: the runtime L.
@@ -428,24 +461,26 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
                                            const ulonglong2 *__restrict__ RC, ulonglong2 RAB, ulonglong2 RAC,
                                            const ulonglong2 *__restrict__ HE, int L_rt, float &out0, float &out1) {
     const int L = LT > 0 ? LT : L_rt;
-    const C2x2 air = {wair, 0ull};
     ulonglong2 a = RS[L - 1];
     C2x2 wb = wroot2(lam2, a.x, a.y, RY[L - 1]);
     if (L == 1) {
-        up2(rcoef2(RAB, RAC, air, wb).im, out0, out1);
+        up2(rcoef2_air(RAB, RAC, wair, wb).im, out0, out1);
         return;
     }
     a = RS[L - 2];
     C2x2 wn = wroot2(lam2, a.x, a.y, RY[L - 2]);
     C2x2 N = rcoef2(RB[L - 2], RC[L - 2], wn, wb);
-    C2x2 D = {pk2(1.f, 1.f), 0ull};
+    C2x2 D;  // 1 until the first Moebius step
     ulonglong2 he = HE[L - 2];
     wb = wn;
     auto step = [&](int n) {
         a = RS[n];
         wn = wroot2(lam2, a.x, a.y, RY[n]);
         const C2x2 r = rcoef2(RB[n], RC[n], wn, wb);
-        mobius2(N, D, r, wb, he);
+        if (n == L - 3)
+            mobius2_d1(N, D, r, wb, he);
+        else
+            mobius2(N, D, r, wb, he);
         he = HE[n];
         wb = wn;
     };
@@ -463,7 +498,10 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
 #pragma unroll 2
         for (int n = L - 3; n >= 0; --n) step(n);
     }
-    mobius2(N, D, rcoef2(RAB, RAC, air, wb), wb, he);
+    if (L == 2)
+        mobius2_d1(N, D, rcoef2_air(RAB, RAC, wair, wb), wb, he);
+    else
+        mobius2(N, D, rcoef2_air(RAB, RAC, wair, wb), wb, he);
     float n0, n1, d0, d1;
     up2(sub2(mul2(N.im, D.re), mul2(N.re, D.im)), n0, n1);
     up2(fma2(D.re, D.re, mul2(D.im, D.im)), d0, d1);
