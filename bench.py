@@ -625,9 +625,9 @@ def main():
                          "frac": achieved / peak,
                          # DRAM bytes of one launch from the ncu capture of the
                          # dynamic-scheduled 256 x 3 shape (profiles/forward_f32_kernel_
-                         # forward-g30-f60-k200.md: 13,279,232 B for 65,536 models), scaled
+                         # forward-g30-f60-k200.md: 13,283,328 B for 65,536 models), scaled
                          # by the model count; null when the autotuner picks another shape
-                         "traffic": (13279232.0 / 65536 * P) if shape == 8 else None,
+                         "traffic": (13283328.0 / 65536 * P) if shape == 8 else None,
                          "traffic_unit": "bytes per launch",
                          "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
                          "mufu_frac": mufu_frac,
