@@ -632,35 +632,35 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         int f = tid / K2, k = tid - (tid / K2) * K2;
         // the item loop, specialised on the model's layer count up to 10
         auto items = [&](auto lt) {
-        constexpr int LT = decltype(lt)::value;
-        for (int base = 0; base < FK2; base += blockDim.x) {
-            const int item = base + tid;
-            float val = 0.f;
-            int fl = -1;
-            if (item < FK2) {
-                fl = f;
-                const ulonglong2 lw = lamp[k];
-                float r0, r1;
-                const size_t o = (size_t)f * LS;
-                im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
-                const float2 hw = hwp[k];
-                val = fmaf(hw.x, r0, hw.y * r1);
+            constexpr int LT = decltype(lt)::value;
+            for (int base = 0; base < FK2; base += blockDim.x) {
+                const int item = base + tid;
+                float val = 0.f;
+                int fl = -1;
+                if (item < FK2) {
+                    fl = f;
+                    const ulonglong2 lw = lamp[k];
+                    float r0, r1;
+                    const size_t o = (size_t)f * LS;
+                    im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
+                    const float2 hw = hwp[k];
+                    val = fmaf(hw.x, r0, hw.y * r1);
+                }
+                // segmented warp reduction over lanes that share a frequency
+                unsigned pending = __ballot_sync(kFull, fl >= 0);
+                while (pending) {
+                    const int leader = __ffs(pending) - 1;
+                    const int fsel = __shfl_sync(kFull, fl, leader);
+                    const float part = warp_sum<float>(fl == fsel ? val : 0.f);
+                    if (lane == leader) imh_w[warp * F + fsel] += part;
+                    pending &= ~__ballot_sync(kFull, fl == fsel);
+                }
+                k += blockDim.x;
+                while (k >= K2) {
+                    k -= K2;
+                    ++f;
+                }
             }
-            // segmented warp reduction over lanes that share a frequency
-            unsigned pending = __ballot_sync(kFull, fl >= 0);
-            while (pending) {
-                const int leader = __ffs(pending) - 1;
-                const int fsel = __shfl_sync(kFull, fl, leader);
-                const float part = warp_sum<float>(fl == fsel ? val : 0.f);
-                if (lane == leader) imh_w[warp * F + fsel] += part;
-                pending &= ~__ballot_sync(kFull, fl == fsel);
-            }
-            k += blockDim.x;
-            while (k >= K2) {
-                k -= K2;
-                ++f;
-            }
-        }
         };
         switch (L) {
             case 1: items(std::integral_constant<int, 1>{}); break;
