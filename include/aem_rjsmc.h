@@ -362,9 +362,13 @@ int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
  * gammas (another stage while any sounding's gamma < 1 and fewer than
  * max_stages stages have run), and the stage number lives in device memory.
  * No host synchronisation or allocation happens between stages.  Same results
- * as smc_run(st, max_stages, n_sweeps) bit for bit.  With recycling the stage
- * counter must stay below 1024 (AEM_ERR_INVALID_ARG otherwise).  Synchronous;
- * stages_out may be NULL. */
+ * as smc_run(st, max_stages, n_sweeps) bit for bit.  n_sweeps <= 0 takes App.
+ * B's R_t as smc_mutate does, decided on the device each stage from the
+ * previous stage's acceptance counts: the graph then holds r_max sweeps whose
+ * kernels return at once beyond R_t (R_t's double-precision logarithm is the
+ * device's, which may differ from the host's in its last bit).  With
+ * recycling the stage counter must stay below 1024 (AEM_ERR_INVALID_ARG
+ * otherwise).  Synchronous; stages_out may be NULL. */
 int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 
 /* Synchronous (a10).  post_k [S x M]: N_k / N; log_bfipd [S]: log of the

@@ -58,10 +58,12 @@ int build_tables(const aem_system_desc *desc, SystemTables *out);
 // FP32 forward + log-likelihood where consecutive blocks of
 // models_per_sounding models use consecutive rows of y_obs (forward.cu).
 // counter: optional device int the dynamic-scheduled shapes use for model
-// claiming instead of a per-launch stream-ordered allocation.
+// claiming instead of a per-launch stream-ordered allocation.  active:
+// optional device int; when it holds 0 the launch does nothing (a sweep of a
+// captured stage loop that the device-side sweep count switched off).
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, int *counter = nullptr);
+                         cudaStream_t stream, int *counter = nullptr, const int *active = nullptr);
 // Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
 // with per-sounding rows of y_obs (forward.cu); counter as above.
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,

@@ -529,7 +529,9 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                                                                const double *__restrict__ y_obs, int obs_per,
                                                                const double *__restrict__ eps_an, double eps_mn,
                                                                double *__restrict__ ll_out,
-                                                               int *__restrict__ work_counter) {
+                                                               int *__restrict__ work_counter,
+                                                               const int *__restrict__ active) {
+    if (active && *active == 0) return;  // a gated launch the caller switched off on the device
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
@@ -734,7 +736,7 @@ constexpr int kNumF32Shapes = 2 * kNumBase;
 template <int NT, int MINB, bool DYN>
 int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                 cudaStream_t stream, int *counter_ext) {
+                 cudaStream_t stream, int *counter_ext, const int *active) {
     const SystemTables &h = sys->host;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS, NT / 32);
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
@@ -755,7 +757,7 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     if (DYN) AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
                                                sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
-                                               ll, counter);
+                                               ll, counter, active);
     const cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(counter, stream);
     AEM_CUDA_TRY(e);
@@ -764,11 +766,11 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
 
 int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
                        float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                       cudaStream_t stream, int *counter_ext = nullptr) {
+                       cudaStream_t stream, int *counter_ext = nullptr, const int *active = nullptr) {
 #define AEM_SHAPE(I, NT, MINB, DYN) \
     case I:                         \
         return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream, \
-                                           counter_ext);
+                                           counter_ext, active);
     switch (idx) {
         AEM_SHAPE(1, 128, 8, false)
         AEM_SHAPE(2, 512, 2, false)
@@ -781,7 +783,7 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
         AEM_SHAPE(9, 128, 6, true)
         default:
             return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream,
-                                               counter_ext);
+                                               counter_ext, active);
     }
 #undef AEM_SHAPE
 }
@@ -789,7 +791,7 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
 template <class Models>
 int launch_forward_f32(const aem_system *sys, const Models *models, float *gates, float *imh, const double *y_obs,
                        int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name,
-                       int *counter_ext = nullptr) {
+                       int *counter_ext = nullptr, const int *active = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -802,7 +804,7 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
                            models->m, models->logtau, models->c};
     const int LS = models->lmax;
     return launch_shape_index(sys->f32_shape[LS], sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
-                              (cudaStream_t)stream, counter_ext);
+                              (cudaStream_t)stream, counter_ext, active);
 }
 
 }  // namespace
@@ -811,9 +813,9 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
 namespace aem {
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, int *counter) {
+                         cudaStream_t stream, int *counter, const int *active) {
     return launch_forward_f32(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding, eps_an,
-                              eps_mn, ll, (void *)stream, "loglik (SMC)", counter);
+                              eps_mn, ll, (void *)stream, "loglik (SMC)", counter, active);
 }
 }  // namespace aem
 

@@ -461,7 +461,9 @@ __device__ bool zca_move(PState cur, PState prop, int i, int s, bool birth, bool
 __device__ inline bool in_bounds_open(double v, double lo, double hi) { return lo < v && v < hi; }
 
 __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t *valid_out, Params pr, int stage_arg,
-                               int sweep, PcaView pv, const int *stage_dev, double *lf_out) {
+                               int sweep, PcaView pv, const int *stage_dev, double *lf_out,
+                               const int *active = nullptr) {
+    if (active && *active == 0) return;  // a sweep beyond the device-side sweep count
     const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
@@ -598,7 +600,8 @@ __global__ void propose_kernel(PState cur, PState prop, int8_t *move_out, int8_t
 // the uniform prior support.
 __global__ void accept_kernel(PState cur, PState prop, const int8_t *move, const int8_t *valid, const double *gamma,
                               Params pr, int stage_arg, int sweep, int *acc, int *nprop, const int *stage_dev,
-                              const double *lf) {
+                              const double *lf, const int *active = nullptr) {
+    if (active && *active == 0) return;
     const int stage = stage_dev ? *stage_dev : stage_arg;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pr.S * pr.N) return;
@@ -1426,6 +1429,39 @@ __global__ void stage_cond_kernel(const double *gamma, int S, const int *d_stage
     cudaGraphSetConditional(h, (!all && *d_stage < stop_stage) ? 1u : 0u);
 }
 
+// App. B's sweep count on the device, from the acceptance counts of the
+// previous stage's sweeps (the first sounding's, as the host path takes them):
+// R = ceil(log c / log(1 - p_min)) clamped to 1..r_max, r_max without counts.
+__global__ void sweep_count_kernel(const int *acc, const int *nprop, const int *have_prev, double c_mut, int r_max,
+                                   int *sweeps) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (!*have_prev) {
+        *sweeps = r_max;
+        return;
+    }
+    double pmin = 1.0;
+    for (int m = 0; m < kMoves; ++m) {
+        const double r = nprop[m] > 0 ? (double)acc[m] / nprop[m] : 1.0;
+        pmin = r < pmin ? r : pmin;
+    }
+    int R;
+    if (pmin <= 0.0)
+        R = r_max;
+    else if (pmin >= 1.0)
+        R = 1;
+    else
+        R = (int)ceil(log(c_mut) / log(1.0 - pmin));
+    *sweeps = R < 1 ? 1 : (R > r_max ? r_max : R);
+}
+
+__global__ void sweep_gate_kernel(const int *sweeps, int sweep, int *gate) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *gate = sweep < *sweeps ? 1 : 0;
+}
+
+__global__ void set_flag_kernel(int *flag, int v) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = v;
+}
+
 __global__ void copy_state_kernel(PState dst, PState src, int P) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P) copy_particle(dst, i, src, i);
@@ -1510,6 +1546,9 @@ struct smc_state {
     // device-side stage counter (graph-captured runs) and the forward kernel's
     // model-claim counter, owned by the sampler so its launches allocate nothing
     int *d_stage = nullptr, *fwd_counter = nullptr;
+    // graph form with App. B's sweep count: R_t, this sweep's gate, whether a
+    // previous stage's acceptance counts exist
+    int *d_sweeps = nullptr, *d_gate = nullptr, *d_have_prev = nullptr;
     std::vector<int> acc_prev, nprop_prev;
     bool have_prev = false;
 };
@@ -1536,13 +1575,13 @@ int alloc_pstate(smc_state *st, PState *ps, size_t count = 0) {
     return AEM_OK;
 }
 
-int run_loglik(smc_state *st, PState ps) {
+int run_loglik(smc_state *st, PState ps, const int *active = nullptr) {
     merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
                                                                 st->m_logh, st->m_m, st->m_logtau, st->m_c);
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
     return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream,
-                                st->fwd_counter);
+                                st->fwd_counter, active);
 }
 
 // Log-likelihood and particle-space gradient of a particle set: merge, the
@@ -1690,6 +1729,8 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->pca_a, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_lo, (size_t)st->S * st->M)) ||
         (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M)) ||
         (rc = dalloc(st, &st->d_stage, 1)) || (rc = dalloc(st, &st->fwd_counter, 1)) ||
+        (rc = dalloc(st, &st->d_sweeps, 1)) || (rc = dalloc(st, &st->d_gate, 1)) ||
+        (rc = dalloc(st, &st->d_have_prev, 1)) ||
         (rc = dalloc(st, &st->lf, P))) {
         smc_destroy(st);
         return rc;
@@ -1991,6 +2032,9 @@ extern "C" int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_
 // synchronisation or allocation, reading the stage number from st->d_stage;
 // ends with the loop condition.
 static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphConditionalHandle h) {
+    // R <= 0: App. B's sweep count, decided on the device each stage; the
+    // graph holds r_max gated sweeps
+    const bool adaptive_r = R <= 0;
     cudaStream_t s = st->stream;
     stage_inc_kernel<<<1, 32, 0, s>>>(st->d_stage);
     AEM_CUDA_TRY(cudaGetLastError());
@@ -2008,16 +2052,28 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     copy_state_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->alt, st->P);
     AEM_CUDA_TRY(cudaGetLastError());
     if ((rc = record_history(st, st->d_stage))) return rc;
+    if (adaptive_r) {  // from the previous stage's counts, before they are cleared
+        sweep_count_kernel<<<1, 32, 0, s>>>(st->acc, st->nprop, st->d_have_prev, st->d.c_mut, st->d.r_max,
+                                            st->d_sweeps);
+        AEM_CUDA_TRY(cudaGetLastError());
+    }
     AEM_CUDA_TRY(cudaMemsetAsync(st->acc, 0, sizeof(int) * st->S * kMoves, s));
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, s));
     if (st->d.adaptive && (rc = adapt_stage(st, st->d_stage))) return rc;
-    for (int sw = 0; sw < R; ++sw) {
+    const int n_sw = adaptive_r ? st->d.r_max : R;
+    const int *gate = adaptive_r ? st->d_gate : nullptr;
+    for (int sw = 0; sw < n_sw; ++sw) {
+        if (adaptive_r) {
+            sweep_gate_kernel<<<1, 32, 0, s>>>(st->d_sweeps, sw, st->d_gate);
+            AEM_CUDA_TRY(cudaGetLastError());
+        }
         propose_kernel<<<blocks_for(st->P, 128), 128, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->pr, 0, sw,
-                                                               pca_view(st), st->d_stage, st->lf);
+                                                               pca_view(st), st->d_stage, st->lf, gate);
         AEM_CUDA_TRY(cudaGetLastError());
-        if ((rc = run_loglik(st, st->prop))) return rc;
+        if ((rc = run_loglik(st, st->prop, gate))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->gamma,
-                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage, st->lf);
+                                                             st->pr, 0, sw, st->acc, st->nprop, st->d_stage, st->lf,
+                                                             gate);
         AEM_CUDA_TRY(cudaGetLastError());
     }
     if ((rc = langevin_sweeps(st, st->d.n_langevin, st->d_stage))) return rc;
@@ -2025,6 +2081,8 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
         langevin_adapt_kernel<<<blocks_for(st->S, 128), 128, 0, s>>>(st->lacc, st->lprop, st->S, st->lang_h);
         AEM_CUDA_TRY(cudaGetLastError());
     }
+    set_flag_kernel<<<1, 32, 0, s>>>(st->d_have_prev, 1);
+    AEM_CUDA_TRY(cudaGetLastError());
     stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, h);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
@@ -2032,12 +2090,21 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
 
 extern "C" int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out) {
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: NULL state");
-    if (n_sweeps < 1 || max_stages < 1) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: n_sweeps and max_stages must be >= 1");
+    if (max_stages < 1) return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: max_stages must be >= 1");
     const int s0 = st->stage;
     if (st->d.recycle_stages > 0 && (long long)s0 + max_stages >= kMaxRecycleStages)
         return fail(AEM_ERR_INVALID_ARG, "smc_run_graph: particle recycling keeps at most 1024 stages");
     AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
     AEM_CUDA_TRY(cudaMemcpy(st->d_stage, &s0, sizeof(int), cudaMemcpyHostToDevice));
+    // the previous stage's acceptance counts as the host path holds them (the
+    // device copies may predate a restore)
+    const int hp = st->have_prev ? 1 : 0;
+    AEM_CUDA_TRY(cudaMemcpy(st->d_have_prev, &hp, sizeof(int), cudaMemcpyHostToDevice));
+    if (st->have_prev) {
+        AEM_CUDA_TRY(cudaMemcpy(st->acc, st->acc_prev.data(), sizeof(int) * st->S * kMoves, cudaMemcpyHostToDevice));
+        AEM_CUDA_TRY(cudaMemcpy(st->nprop, st->nprop_prev.data(), sizeof(int) * st->S * kMoves,
+                                cudaMemcpyHostToDevice));
+    }
     cudaStream_t user = st->stream, cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -124,8 +124,9 @@ class SMC:
 
     def run_graph(self, max_stages=1000, n_sweeps=10):
         """smc_run_graph: the stage loop captured as a CUDA graph with a device-side
-        loop condition (n_sweeps >= 1 random-walk sweeps per stage, plus the
-        descriptor's adaptive, recycling and Langevin steps)."""
+        loop condition (n_sweeps random-walk sweeps per stage, or App. B's R_t
+        decided on the device when n_sweeps <= 0, plus the descriptor's adaptive,
+        recycling and Langevin steps)."""
         t = ctypes.c_int()
         check(_lib.load().smc_run_graph(self._h, int(max_stages), int(n_sweeps), ctypes.byref(t)), "smc_run_graph")
         return t.value

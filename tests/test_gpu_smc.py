@@ -305,7 +305,7 @@ def test_detectability_study_trends(torch, L, S):
 # proposal with particle recycling and ZCA-coloured birth / death; Langevin
 # sweeps with step adaptation
 GRAPH_MODES = {"fixed": {}, "adaptive_recycling_zca": dict(adaptive=1, recycle_stages=3, zca=0.5),
-               "langevin": dict(n_langevin=2)}
+               "langevin": dict(n_langevin=2), "app_b_sweeps": {}}
 
 
 @pytest.mark.parametrize("mode", list(GRAPH_MODES))
@@ -313,10 +313,11 @@ def test_graph_captured_run_equals_host_loop(S, gsys, data, mode):
     """smc_run_graph (one captured stage repeated by a device-side WHILE
     condition) reproduces smc_run bit for bit: particles, log-likelihoods,
     gammas, evidence estimates and the stage count, on three soundings, for
-    each sampler option."""
+    each sampler option, and with App. B's sweep count R_t (n_sweeps = 0),
+    which the graph form decides on the device."""
     import time
     runs = []
-    n_sweeps = 10 if mode == "fixed" else 4
+    n_sweeps = {"fixed": 10, "app_b_sweeps": 0}.get(mode, 4)
     for graph in (False, True):
         st = settings(n_particles=256, seed=21)
         sm = S.SMC(gsys, np.tile(data, (3, 1)), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles, n_soundings=3,
@@ -331,7 +332,9 @@ def test_graph_captured_run_equals_host_loop(S, gsys, data, mode):
         dt = time.perf_counter() - t0
         p = sm.get_particles(0)
         post, lb, lz = sm.model_odds()
-        extra = sm.langevin_stats()[2] if mode == "langevin" else (sm.adaptation()["scale"] if mode != "fixed" else 0)
+        extra = {"langevin": lambda: sm.langevin_stats()[2],
+                 "adaptive_recycling_zca": lambda: sm.adaptation()["scale"],
+                 "app_b_sweeps": lambda: sm.stats()["accepted"]}.get(mode, lambda: 0)()
         runs.append((stages, p, sm.stats()["gamma"], lz, dt, extra))
     (s0, p0, g0, z0, t0_, e0), (s1, p1, g1, z1, t1_, e1) = runs
     print(f"\n{mode}: host loop {t0_ * 1e3:.1f} ms, graph {t1_ * 1e3:.1f} ms, {s0} stages")
