@@ -242,18 +242,27 @@ def test_loglik_matches_oracle(lib, torch_mod, prec):
 
 
 def test_full_size_sampled_parity(lib, torch_mod):
-    """2^20 models in the launch configuration the benchmark times; 48 sampled
-    models checked one by one against the oracle."""
+    """2^20 models in the launch configuration the benchmark times (the
+    autotuner's shape for this batch's lmax, chosen on its first 65,536
+    models, and the same aem_loglik_f32 call with the gates kept); 48 sampled
+    models checked one by one against the oracle, gates and log-likelihoods."""
     name = "forward-g30-f60-k200"
-    sysg = gpu_system(lib, name)
+    sysg = lib.System(**I.system_kwargs(name))
     models = as_f32_inputs(I.random_models(1 << 20, seed=0))
-    y = lib.forward_f32(sysg, I.to_torch(models, torch_mod.float32))
+    tm = I.to_torch(models, torch_mod.float32)
+    sysg.autotune(I.to_torch(I.subset(models, np.arange(1 << 16)), torch_mod.float32))
+    s = oracle_system(name)
+    y_obs = I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=0)
+    ll, y = lib.loglik_f32(sysg, tm, y_obs, I.EPS_AN, I.EPS_MN, want_gates=True)
     torch_mod.cuda.synchronize()
     idx = np.random.default_rng(5).choice(1 << 20, 48, replace=False)
     y_ref, _, _, kap = oracle_ref(I.subset(models, idx), name)
     e = rel_err(y[idx].cpu().numpy().astype(np.float64), y_ref)
     assert_within(e, bound32(kap, sysg.F), "FP32 gates at full size")
-    assert torch_mod.isfinite(y).all()
+    ll_ref = O.loglik(y_ref, y_obs, I.EPS_AN, I.EPS_MN)
+    bound = loglik_bound(y_ref, y_obs, bound32(kap, sysg.F)) + 1e-9 * np.abs(ll_ref)
+    assert np.all(np.abs(ll[idx].cpu().numpy() - ll_ref) <= bound)
+    assert torch_mod.isfinite(y).all() and torch_mod.isfinite(ll).all()
 
 
 @pytest.mark.parametrize("shape", range(F32_SHAPES))
