@@ -237,6 +237,7 @@ def test_full_size_sampled_gradient(setup):
     models = I.random_models(P, seed=21)
     for k in ("logsig", "logh", "m", "logtau", "c"):
         models[k] = models[k].astype(np.float32).astype(np.float64)
+    sysg.autotune(I.to_torch(models, torch.float32))  # the forward pass in the benchmark's shape
     ll, g = L.loglik_grad_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
     g = g.cpu().numpy().astype(np.float64)
     idx = np.random.default_rng(4).choice(P, 24, replace=False)
