@@ -24,7 +24,11 @@ Tweedie 1996); it leaves pi_t invariant like the paper's random walks do.
 Random numbers come from Philox4x32-10 (Salmon et al., SC 2011) written out
 here from its published definition, keyed per sounding and counted per
 (particle, draw, stage, sweep), so the GPU sampler can reproduce the same
-uniforms.  Readings of the paper used here are listed in the design doc.
+uniforms.  Where the paper leaves a choice open the readings are: the six
+move types drawn uniformly, an impossible move counted as a rejection; one
+systematic-resampling uniform per model and stage; 60 bisection steps for
+the tempering increment with alpha = 0.5; the tempered likelihood in every
+acceptance; P(kappa), P(lambda) uniform on 0..max (Section 2.3.1).
 """
 from __future__ import annotations
 
