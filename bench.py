@@ -623,10 +623,10 @@ def main():
                        "l2": "inputs larger than L2 (210 MB of model parameters per step)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         # DRAM bytes of one launch from the ncu capture of the
-                         # dynamic-scheduled 256 x 3 shape (profiles/forward_f32_kernel_
-                         # forward-g30-f60-k200.md: 13,283,328 B for 65,536 models), scaled
-                         # by the model count; null when the autotuner picks another shape
+                         # DRAM bytes of one launch from an ncu capture of the
+                         # dynamic-scheduled 256 x 3 shape (13,283,328 B for 65,536
+                         # models of this workload), scaled by the model count; null
+                         # when the autotuner picks another shape
                          "traffic": (13283328.0 / 65536 * P) if shape == 8 else None,
                          "traffic_unit": "bytes per launch",
                          "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
