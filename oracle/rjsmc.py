@@ -621,9 +621,10 @@ class SMCResult:
 class ForwardLik:
     """Log-likelihood of merged particles through the oracle forward model."""
 
-    def __init__(self, system, y_obs, eps_an, eps_mn, lmax, mode=None):
+    def __init__(self, system, y_obs, eps_an, eps_mn, lmax, mode=None, nthreads=None):
         import oracle as O
         self.O = O
+        self.nthreads = nthreads
         self.system = dict(system)
         if self.system.get("T") is None:
             self.system["T"] = O.tmatrix(self.system["freqs"], self.system["times"])
@@ -637,7 +638,7 @@ class ForwardLik:
         if not parts:
             return np.zeros(0)
         mb = merged_batch(parts, self.lmax)
-        y = self.O.forward(mb, self.system, mode=self.mode)
+        y = self.O.forward(mb, self.system, mode=self.mode, nthreads=self.nthreads)
         return self.O.loglik(y, self.y_obs, self.eps_an, self.eps_mn)
 
 
@@ -724,20 +725,42 @@ def run(s: SMCSettings, loglik, max_stages=500, prior=sample_prior, proposer=pro
     return res
 
 
-def model_odds(counts, kappa_max, lambda_max):
-    """pi(k|y) = N_k / N and log BFIPD (Section 2.3.3) with uniform p(k):
-    B = (|M_kappa| sum_{IP} pi/p) / (|M_lambda| sum_{non-IP} pi/p) = N_IP / (lambda_max N_nonIP)."""
+def grouped_bayes_factor(post, prior, chargeable):
+    """The BFIPD statistic of Section 2.3.3, written out as the paper defines
+    it: with M_lambda the chargeable models and M_kappa the others,
+
+        B = |M_kappa| sum_{k in M_lambda} post_k / prior_k
+            / ( |M_lambda| sum_{k in M_kappa} post_k / prior_k ).
+
+    post: estimated posterior model probabilities pi(k|y); prior: p(k) > 0;
+    chargeable: boolean per model.  Returns log B (+inf when no non-chargeable
+    model has posterior mass, -inf when no chargeable one has)."""
+    post = np.asarray(post, dtype=np.float64)
+    prior = np.asarray(prior, dtype=np.float64)
+    ip = np.asarray(chargeable, dtype=bool)
+    n_ip, n_non = int(ip.sum()), int((~ip).sum())
+    s_ip = float(np.sum(post[ip] / prior[ip]))
+    s_non = float(np.sum(post[~ip] / prior[~ip]))
+    if s_non == 0.0:
+        return math.inf
+    if s_ip == 0.0:
+        return -math.inf
+    return math.log(n_non * s_ip) - math.log(n_ip * s_non)
+
+
+def model_odds(counts, kappa_max, lambda_max, prior=None):
+    """pi(k|y) = N_k / N (Section 3.2.1) and log BFIPD (Section 2.3.3) over the
+    (kappa_max + 1) x (lambda_max + 1) grid of decoupled models, k = kappa
+    (lambda_max + 1) + lambda, chargeable when lambda >= 1.  prior: p(k); None
+    is the sampler's prior, uniform on kappa and on lambda, under which B
+    reduces to the posterior odds over the prior odds, N_IP / (lambda_max N_nonIP)."""
     counts = np.asarray(counts, dtype=np.float64)
-    N = counts.sum()
-    post = counts / N
-    grid = counts.reshape(kappa_max + 1, lambda_max + 1)
-    n_non = grid[:, 0].sum()
-    n_ip = grid[:, 1:].sum()
-    if n_non == 0:
-        return post, math.inf
-    if n_ip == 0:
-        return post, -math.inf
-    return post, math.log(n_ip / (lambda_max * n_non))
+    post = counts / counts.sum()
+    M = (kappa_max + 1) * (lambda_max + 1)
+    if prior is None:
+        prior = np.full(M, 1.0 / M)
+    chargeable = (np.arange(M) % (lambda_max + 1)) >= 1
+    return post, grouped_bayes_factor(post, prior, chargeable)
 
 
 # ------------------------------------------- adaptive within-model proposal

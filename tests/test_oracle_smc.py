@@ -421,3 +421,49 @@ def test_zca_chargeable_birth_death_is_reversible():
     freq = cnt / cnt.sum()
     assert np.all(np.abs(freq - toy_rj_m_posterior()) < 0.03), freq
     assert n_zca > 3000
+
+
+# ---------------------------------------------------------------- BFIPD (Section 2.3.3)
+# A 2 x 3 model grid (kappa_max = 1, lambda_max = 2): k = 3 kappa + lambda, the
+# non-chargeable models are k = 0 and 3 (|M_kappa| = 2), the chargeable ones
+# k = 1, 2, 4, 5 (|M_lambda| = 4).  Counts of 20 particles, worked by hand:
+BF_COUNTS = np.array([5, 3, 2, 4, 0, 6])
+
+
+def test_bfipd_general_prior_hand_example():
+    """Non-uniform p(k) = (0.1, 0.2, 0.1, 0.3, 0.2, 0.1):
+    sum_IP pi/p = 0.15/0.2 + 0.10/0.1 + 0/0.2 + 0.30/0.1 = 4.75,
+    sum_non pi/p = 0.25/0.1 + 0.20/0.3 = 19/6,
+    B = 2 * 4.75 / (4 * 19/6) = 0.75."""
+    prior = np.array([0.1, 0.2, 0.1, 0.3, 0.2, 0.1])
+    post, lb = R.model_odds(BF_COUNTS, 1, 2, prior=prior)
+    assert np.allclose(post, BF_COUNTS / 20.0)
+    assert lb == pytest.approx(math.log(0.75), rel=1e-14)
+    # the same through the grouped form directly (chargeable = lambda >= 1)
+    assert R.grouped_bayes_factor(post, prior, [False, True, True, False, True, True]) == pytest.approx(math.log(0.75))
+    # the statistic is posterior odds / prior odds only for a uniform prior:
+    # here the prior odds are 0.6/0.4 and the posterior odds 11/9
+    assert abs(lb - math.log((11 / 9) / (0.6 / 0.4))) > 0.05
+
+
+def test_bfipd_uniform_prior_is_count_ratio():
+    """Uniform p(k) = 1/6: B = 2 * (6 * 11/20) / (4 * (6 * 9/20)) = 11 / 18 =
+    N_IP / (lambda_max N_nonIP)."""
+    post, lb = R.model_odds(BF_COUNTS, 1, 2)
+    assert lb == pytest.approx(math.log(11.0 / 18.0), rel=1e-14)
+    # a 4 x 5 grid (kappa_max = 3, lambda_max = 4): N_IP = 30, N_nonIP = 10 -> 30 / 40
+    counts = np.zeros(20, dtype=int)
+    counts[[0, 5]] = 5           # lambda = 0 (non-chargeable): 10 particles
+    counts[[1, 7, 19]] = 10      # chargeable: 30 particles
+    assert R.model_odds(counts, 3, 4)[1] == pytest.approx(math.log(0.75), rel=1e-14)
+
+
+def test_bfipd_one_sided_populations():
+    """Every particle chargeable: B = +inf; none chargeable: B = -inf."""
+    only_ip = np.array([0, 3, 2, 0, 0, 6])
+    none_ip = np.array([5, 0, 0, 4, 0, 0])
+    assert R.model_odds(only_ip, 1, 2)[1] == math.inf
+    assert R.model_odds(none_ip, 1, 2)[1] == -math.inf
+    prior = np.array([0.1, 0.2, 0.1, 0.3, 0.2, 0.1])
+    assert R.model_odds(only_ip, 1, 2, prior=prior)[1] == math.inf
+    assert R.model_odds(none_ip, 1, 2, prior=prior)[1] == -math.inf
