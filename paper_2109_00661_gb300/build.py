@@ -13,8 +13,13 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(PKG, "_build")
-LIB = os.path.join(PKG, "_build", "libaemrjsmc.so")
+# Measurement builds: AEM_NVCC_DEFINES (e.g. "-DAEM_F32_ACCURATE_MATH=1") adds
+# preprocessor definitions and AEM_BUILD_DIR names the output folder (under the
+# package; the loader reads the same variable), so a variant never replaces the
+# default library.
+BUILD = os.path.join(PKG, os.environ.get("AEM_BUILD_DIR", "_build"))
+LIB = os.path.join(BUILD, "libaemrjsmc.so")
+DEFINES = os.environ.get("AEM_NVCC_DEFINES", "").split()
 SOURCES = ["system.cpp", "forward.cu", "adjoint.cu", "gates_tc.cu", "smc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -49,7 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = nvcc_path()
     os.makedirs(BUILD, exist_ok=True)
-    common = [nvcc, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    common = [nvcc, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+              *DEFINES]
     if verbose:
         common += ["-Xptxas", "-v"]
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]

@@ -108,7 +108,7 @@ __device__ __forceinline__ C2x2 c2root(u64 lam2, ulonglong2 s, u64 y2, u64 &inv_
 __device__ __forceinline__ C2x2 c2expm(ulonglong2 he, C2x2 u) {
     float a0, a1, f0, f1, s0, c0, s1, c1;
     up2(mul2(he.x, u.re), a0, a1);
-    up2(mul2(he.y, u.im), f0, f1);
+    up2(reduce_2pi2(mul2(he.y, u.im)), f0, f1);
     sincos_approx(f0, &s0, &c0);
     sincos_approx(f1, &s1, &c1);
     const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
@@ -216,19 +216,23 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
             const float2 x = make_float2(mag * cp, mag * sp);
             const float2 ix1 = crcp(make_float2(1.f + x.x, x.y));  // 1 / (1 + x)
             float2 sg, dsg_dm, dsg_dx;
+            // sig itself without cancellation, as the forward kernel forms it:
+            // real parts as sums of non-negative terms (Re x >= 0), imaginary
+            // parts as the single product m Im x / |.|^2
             if (cc_form == AEM_CC_PAPER) {
-                sg = make_float2(si * (1.f - mm * ix1.x), -si * mm * ix1.y);
+                // s_inf ((1 - m) + x) / (1 + x); ix1.y <= 0
+                sg = make_float2(si * fmaf((1.f - mm) + x.x, ix1.x, -x.y * ix1.y), -si * mm * ix1.y);
                 dsg_dm = cscale(ix1, -si);
                 dsg_dx = cscale(cmul(ix1, ix1), si * mm);                // s_inf m / (1 + x)^2
             } else {
                 const float2 b = make_float2(1.f + (1.f - mm) * x.x, (1.f - mm) * x.y);  // 1 + (1 - m) x
                 if (cc_form == AEM_CC_PELTON) {
-                    const float2 ib = crcp(b);
-                    sg = cscale(cmul(make_float2(1.f + x.x, x.y), ib), si);
+                    const float2 ib = crcp(b);                           // conj(b) / |b|^2
+                    sg = make_float2(si * fmaf(1.f + x.x, ib.x, -x.y * ib.y), si * mm * x.y / (b.x * b.x + b.y * b.y));
                     dsg_dm = cmul(sg, cmul(x, ib));                      // sig x / (1 + (1 - m) x)
                     dsg_dx = cscale(cmul(ib, ib), si * mm);              // s_0 m / (1 + (1 - m) x)^2
                 } else {
-                    sg = cscale(cmul(b, ix1), si);
+                    sg = make_float2(si * fmaf(b.x, ix1.x, -b.y * ix1.y), si * mm * ix1.y);
                     dsg_dm = cscale(cmul(x, ix1), -si);                  // -s_0 x / (1 + x)
                     dsg_dx = cscale(cmul(ix1, ix1), -si * mm);           // -s_0 m / (1 + x)^2
                 }

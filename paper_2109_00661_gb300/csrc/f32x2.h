@@ -21,24 +21,57 @@ constexpr u64 kZero2 = 0ull;                   // (0, 0)
 constexpr u64 kOne2 = 0x3f8000003f800000ull;   // (1, 1)
 constexpr u64 kHalf2 = 0x3f0000003f000000ull;  // (0.5, 0.5)
 
+// Measurement builds (off by default; build.py passes them through its
+// AEM_NVCC_DEFINES environment variable):
+//   AEM_F32_ACCURATE_MATH=1  the round-to-nearest reciprocal and reciprocal
+//     square root and the library's exp2f / sincosf (full range reduction) in
+//     place of the hardware approximations, to separate the approximations'
+//     share of the FP32 error from the FP32 arithmetic's;
+//   AEM_F32_REDUCE_PHASE=1   the Moebius step's phase reduced modulo 2 pi
+//     (Cody & Waite 1980: k = round(x / 2 pi) by the 1.5 * 2^23 shifter, then
+//     x - k C1 - k C2 with C1 + C2 = 2 pi, C1 the nearest float) before the
+//     hardware sine and cosine.
+#ifndef AEM_F32_ACCURATE_MATH
+#define AEM_F32_ACCURATE_MATH 0
+#endif
+#ifndef AEM_F32_REDUCE_PHASE
+#define AEM_F32_REDUCE_PHASE 0
+#endif
+
 __device__ __forceinline__ float rsqrt_approx(float v) {
+#if AEM_F32_ACCURATE_MATH
+    return __frsqrt_rn(v);
+#else
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
+#endif
 }
 __device__ __forceinline__ float rcp_approx(float v) {
+#if AEM_F32_ACCURATE_MATH
+    return __frcp_rn(v);
+#else
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
+#endif
 }
 __device__ __forceinline__ float ex2_approx(float v) {
+#if AEM_F32_ACCURATE_MATH
+    return exp2f(v);
+#else
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
+#endif
 }
 __device__ __forceinline__ void sincos_approx(float v, float *s, float *c) {
+#if AEM_F32_ACCURATE_MATH
+    sincosf(v, s, c);
+#else
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(v));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(v));
+#endif
 }
 __device__ __forceinline__ u64 pk2(float a, float b) {
     u64 r;
@@ -72,6 +105,21 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
 struct C2x2 {  // two complex numbers: re = (re_a, re_b), im = (im_a, im_b)
     u64 re, im;
 };
+
+// Both phases of a pair reduced into [-pi, pi] modulo 2 pi (AEM_F32_REDUCE_PHASE):
+// the shifter 1.5 * 2^23 rounds x / (2 pi) to the nearest integer k for
+// |x| < 2^22 pi; C1 = float(2 pi), C2 = float(2 pi - C1).
+__device__ __forceinline__ u64 reduce_2pi2(u64 x) {
+#if AEM_F32_REDUCE_PHASE
+    const float inv2pi = 0.159154943091895336f, shift = 12582912.0f;
+    const float c1 = 6.28318548202514648f, c2 = -1.74845553146951215e-7f;
+    const u64 t = fma2(x, pk2(inv2pi, inv2pi), pk2(shift, shift));
+    const u64 k = sub2(t, pk2(shift, shift));
+    return fma2(k, pk2(-c2, -c2), fma2(k, pk2(-c1, -c1), x));
+#else
+    return x;
+#endif
+}
 
 }  // namespace f32x2
 }  // namespace aem

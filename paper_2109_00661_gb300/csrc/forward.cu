@@ -163,8 +163,10 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                                                            typename Ops::R *__restrict__ imh_out,
                                                            const double *__restrict__ y_obs, int obs_per,
                                                            const double *__restrict__ eps_an, double eps_mn,
-                                                           double *__restrict__ ll_out) {
+                                                           double *__restrict__ ll_out,
+                                                           const int *__restrict__ active) {
     using R = typename Ops::R;
+    if (active && *active == 0) return;  // a gated launch the caller switched off on the device
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LM = AEM_MAX_LAYERS;
     C2<R> *s_tab = reinterpret_cast<C2<R> *>(smem_raw);
@@ -215,21 +217,22 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                 sincospi_r(R(0.5) * cc, &sp, &cp);
                 R xr = R(1) + mag * cp, xi = mag * sp;  // 1 + x
                 R den = xr * xr + xi * xi;
+                // every form is written without cancellation (see the FP32 kernel)
                 if (cc_form == AEM_CC_PAPER) {
-                    // sigma_inf (1 - m / (1 + x))
-                    sr = sig * (R(1) - mm * xr / den);
+                    // sigma_inf ((1 - m) + x) / (1 + x)
+                    sr = sig * (((R(1) - mm) + mag * cp) * xr + xi * xi) / den;
                     si = sig * (mm * xi / den);
                 } else if (cc_form == AEM_CC_LITERAL) {
                     // sigma_0 (1 + (1 - m) x) / (1 + x)
                     R br = R(1) + (R(1) - mm) * mag * cp, bi = (R(1) - mm) * mag * sp;
                     sr = sig * (br * xr + bi * xi) / den;
-                    si = sig * (bi * xr - br * xi) / den;
+                    si = -sig * (mm * xi / den);
                 } else {
                     // sigma_0 (1 + x) / (1 + (1 - m) x)
                     R br = R(1) + (R(1) - mm) * mag * cp, bi = (R(1) - mm) * mag * sp;
                     R bd = br * br + bi * bi;
                     sr = sig * (xr * br + xi * bi) / bd;
-                    si = sig * (xi * br - xr * bi) / bd;
+                    si = sig * (mm * xi / bd);
                 }
             }
             // s = i w mu0 sigma
@@ -315,7 +318,7 @@ template <class Ops, class Models>
 int launch_forward(const aem_system *sys, const Models *models, typename Ops::R *gates, typename Ops::R *imh,
                    const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream,
                    const typename Ops::R *omega, const typename Ops::R *lam, const typename Ops::R *hw,
-                   const typename Ops::R *T, const char *name) {
+                   const typename Ops::R *T, const char *name, const int *active = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -336,7 +339,8 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
     long long grid = (long long)sys->num_sms * per_sm;
     if (grid > models->n_models) grid = models->n_models;
     kern<<<(unsigned)grid, kThreads, smem, (cudaStream_t)stream>>>(mv, h.F, h.G, h.K, h.cc_form, omega, lam, hw, T,
-                                                                   gates, imh, y_obs, obs_per, eps_an, eps_mn, ll);
+                                                                   gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
+                                                                   active);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -401,7 +405,7 @@ __device__ __forceinline__ C2x2 rcoef2(ulonglong2 Bv, ulonglong2 Cv, C2x2 a, C2x
 __device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
     float a0, a1, f0, f1;
     up2(mul2(he.x, wb.re), a0, a1);
-    up2(mul2(he.y, wb.im), f0, f1);
+    up2(reduce_2pi2(mul2(he.y, wb.im)), f0, f1);
     float s0, c0, s1, c1;
     sincos_approx(f0, &s0, &c0);
     sincos_approx(f1, &s1, &c1);
@@ -438,7 +442,7 @@ __device__ __forceinline__ C2x2 rcoef2_air(ulonglong2 Bv, ulonglong2 Cv, u64 wai
 __device__ __forceinline__ void mobius2_d1(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
     float a0, a1, f0, f1;
     up2(mul2(he.x, wb.re), a0, a1);
-    up2(mul2(he.y, wb.im), f0, f1);
+    up2(reduce_2pi2(mul2(he.y, wb.im)), f0, f1);
     float s0, c0, s1, c1;
     sincos_approx(f0, &s0, &c0);
     sincos_approx(f1, &s1, &c1);
@@ -594,18 +598,26 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 sincospif(0.5f * cc, &sp, &cp);
                 const float xr = 1.f + mag * cp, xi = mag * sp;
                 const float den = xr * xr + xi * xi;
+                // Each form is evaluated without cancellation.  The paper's
+                // sigma_inf (1 - m / (1 + x)) as 1 - m Re(1/(1+x)) loses the
+                // digits of 1 - m when m -> 1 at small w tau (a relative error
+                // of 2^-24 / (1 - m) in Re sigma, up to 3e-5 of the Hankel
+                // sum on the random-model workload); written as
+                // ((1 - m) + x) / (1 + x), with 1 - m exact for m >= 1/2, every
+                // real part is a sum of non-negative terms (c <= 1 so Re x >= 0)
+                // and every imaginary part is a single product m Im x / |.|^2.
                 if (cc_form == AEM_CC_PAPER) {
-                    sr = sig * (1.f - mm * xr / den);
+                    sr = sig * (fmaf((1.f - mm) + mag * cp, xr, xi * xi) / den);
                     si = sig * (mm * xi / den);
                 } else if (cc_form == AEM_CC_LITERAL) {
                     const float br = 1.f + (1.f - mm) * mag * cp, bi = (1.f - mm) * mag * sp;
-                    sr = sig * (br * xr + bi * xi) / den;
-                    si = sig * (bi * xr - br * xi) / den;
+                    sr = sig * (fmaf(br, xr, bi * xi) / den);
+                    si = -sig * (mm * xi / den);
                 } else {
                     const float br = 1.f + (1.f - mm) * mag * cp, bi = (1.f - mm) * mag * sp;
                     const float bd = br * br + bi * bi;
-                    sr = sig * (xr * br + xi * bi) / bd;
-                    si = sig * (xi * br - xr * bi) / bd;
+                    sr = sig * (fmaf(xr, br, xi * bi) / bd);
+                    si = sig * (mm * xi / bd);
                 }
             }
             const float sx = -w * mu0 * si, sy = w * mu0 * sr;
@@ -811,6 +823,14 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
 }  // namespace aem
 
 namespace aem {
+int loglik_f64_soundings(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
+                         int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
+                         cudaStream_t stream, const int *active) {
+    return launch_forward<FP64Ops>(sys, models, (double *)nullptr, (double *)nullptr, y_obs, models_per_sounding,
+                                   eps_an, eps_mn, ll, (void *)stream, sys ? sys->d_omega_d : nullptr,
+                                   sys ? sys->d_lam_d : nullptr, sys ? sys->d_hw_d : nullptr,
+                                   sys ? sys->d_T_d : nullptr, "loglik (SMC, FP64)", active);
+}
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
                          cudaStream_t stream, int *counter, const int *active) {

@@ -17,7 +17,13 @@ import oracle as O
 from paper_2109_00661_gb300 import inputs as I
 
 EPS_AN = I.EPS_AN
-DELTA_S32 = 3e-5   # FP32 spectrum, relative to A_f (worst of 20,000 models per system: 2.0e-5, at L = 1-2)
+# FP32 spectrum, relative to A_f: 2^-17 (128 units of 2^-24).  With the
+# Cole-Cole conductivity evaluated without cancellation, the FP32 recursion's
+# own rounding is what remains; it is the same with correctly rounded special
+# functions in place of the hardware approximations (largest measured on 4096
+# throughput-workload and 2048 single-sounding models: 3.7e-6 approximations,
+# 2.6e-6 correctly rounded), so the bar is twice the measured worst case.
+DELTA_S32 = 2.0 ** -17
 DELTA_S64 = 1e-12  # FP64 spectrum, relative to A_f
 DELTA_T = 1e-8     # table agreement, relative to each row's largest entry
 
@@ -62,6 +68,14 @@ def bound64(kap):
 
 def bound32(kap, F):
     return 1e-4 + kap[2] * DELTA_S32 + kap[0] * (F + 1) * 2.0 ** -24 + kap[1] * DELTA_T
+
+
+def rounding32(kap, F):
+    """The part of bound32 no FP32 output can avoid: rounding of the spectrum
+    to FP32 and of the G x F transform, kappa_g (F + 1) 2^-24, plus the table
+    difference.  Gates where this is below 1e-4 are the well-conditioned ones,
+    on which the plain 1e-4 per-gate tolerance is asked for."""
+    return kap[0] * (F + 1) * 2.0 ** -24 + kap[1] * DELTA_T
 
 
 def assert_within(e, bound, what):

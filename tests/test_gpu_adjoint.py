@@ -2,7 +2,9 @@
 against central finite differences of the FP64 oracle and of the GPU's own
 FP64 forward model, on models near the single-sounding truth.
 
-Bar: per model, the relative gradient error |g - g_ref|_2 / |g_ref|_2 <= 1e-3;
+Bar: per model, the relative gradient error |g - g_ref|_2 / |g_ref|_2 <= 1e-3
+plus |b|_2 / |g_ref|_2, and the plain 1e-3 on every model whose b_round (the
+propagation of the forward's unavoidable FP32 rounding alone) is below 1e-3;
 per component, |g - g_ref| <= 5e-3 max(|g_ref|, 1e-2 max_j |g_ref_j|) + b with
 b the first-order propagation of the FP32 forward's per-gate bound through
 d ll / d yhat and the gate Jacobian (components formed by cancellation of much
@@ -13,7 +15,7 @@ import pytest
 
 import oracle as O
 from paper_2109_00661_gb300 import inputs as I
-from parity_util import bound32, gradient_bound, kappa, loglik_bound, oracle_ref, oracle_system
+from parity_util import bound32, gradient_bound, kappa, loglik_bound, oracle_ref, oracle_system, rounding32
 
 pytestmark = pytest.mark.gpu
 
@@ -44,17 +46,31 @@ def norm_err(g, ref):
     return np.linalg.norm((g - ref).reshape(len(g), -1), axis=1) / np.linalg.norm(ref.reshape(len(g), -1), axis=1)
 
 
-def check(g, ref, what, b=None):
+def gbounds(y_model, J, y_obs, kap, F):
+    """(b, b_round): the first-order propagation through d ll / d yhat and the
+    gate Jacobian of the FP32 forward's full per-gate bound, and of its
+    unavoidable rounding part alone (rounding32)."""
+    return (gradient_bound(y_model, J, y_obs, bound32(kap, F)),
+            gradient_bound(y_model, J, y_obs, rounding32(kap, F)))
+
+
+def check(g, ref, what, b=None, b_round=None):
     b = np.zeros_like(ref) if b is None else b
+    b_round = np.zeros_like(ref) if b_round is None else b_round
     e = within(g, ref, b)
     ne = norm_err(g, ref)
     nb = norm_err(ref + b, ref)  # |b|_2 / |g_ref|_2
+    nr = norm_err(ref + b_round, ref)
+    good = nr < 1e-3
     i = np.unravel_index(np.argmax(e), e.shape)
     print(f"\n{what}: relative gradient error (norm) max {ne.max():.2e} median {np.median(ne):.2e}, "
-          f"{np.sum(ne <= 1e-3)} of {len(ne)} models within 1e-3; "
+          f"{np.sum(ne <= 1e-3)} of {len(ne)} models within 1e-3, {np.sum(ne[good] <= 1e-3)} of the {good.sum()} "
+          f"whose propagated rounding term is below 1e-3; "
           f"component max {e.max():.2e} at (model, layer, param) {i}: {g[i]:.6e} vs {ref[i]:.6e}")
     assert np.all(ne <= 1e-3 + nb)
-    assert np.mean(ne <= 1e-3) >= 0.75
+    # the plain 1e-3 wherever the FP32 forward's unavoidable rounding,
+    # propagated to the gradient, stays below it
+    assert np.all(ne[good] <= 1e-3)
     assert e.max() <= 5e-3
 
 
@@ -77,7 +93,7 @@ def test_gradient_matches_oracle_fd(setup, L_layers):
     g = g.cpu().numpy().astype(np.float64)
     y_model, _, _, kap = oracle_ref(models, NAME)
     _, J = O.forward_jacobian_fd(models, s)
-    check(g, g_ref, f"{L_layers} layers vs oracle FD", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+    check(g, g_ref, f"{L_layers} layers vs oracle FD", *gbounds(y_model, J, y_obs, kap, sysg.F))
     # the likelihood value it returns is the FP32 forward path's, within the
     # first-order bound the per-gate FP32 error bound gives
     bound = loglik_bound(y_model, y_obs, bound32(kap, sysg.F)) + 1e-9 * np.abs(ll_ref)
@@ -104,7 +120,7 @@ def test_gradient_matches_fd_of_gpu_fp64(setup):
             ref[:, n, pi] = (fp - fm) / (2 * step)
     y_model, _, _, kap = oracle_ref(models, NAME)
     _, J = O.forward_jacobian_fd(models, s)
-    check(g, ref, "4 layers vs FD of the GPU FP64 forward", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+    check(g, ref, "4 layers vs FD of the GPU FP64 forward", *gbounds(y_model, J, y_obs, kap, sysg.F))
 
 
 def test_gradient_zero_padding(setup):
@@ -130,7 +146,7 @@ def test_gradient_other_colecole_forms(setup, form):
     y_model, _, _, kap = oracle_ref(models, NAME, cc_form=form)
     _, J = O.forward_jacobian_fd(models, s)
     check(g.cpu().numpy().astype(np.float64), g_ref, f"Cole-Cole form {form}",
-          gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+          *gbounds(y_model, J, y_obs, kap, sysg.F))
 
 
 def many_layers(P, seed, L):
@@ -157,7 +173,7 @@ def test_gradient_beyond_ten_layers(setup):
     g = g.cpu().numpy().astype(np.float64)
     y_model, _, _, kap = oracle_ref(models, NAME)
     _, J = O.forward_jacobian_fd(models, s)
-    check(g, g_ref, "14 layers vs oracle FD", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+    check(g, g_ref, "14 layers vs oracle FD", *gbounds(y_model, J, y_obs, kap, sysg.F))
     small = near_truth(5, seed=6, L=3)
     padded = {k: (np.concatenate([v, np.zeros((5, 16))], axis=1) if k != "nlayers" else v) for k, v in small.items()}
     _, g3 = L.loglik_grad_f32(sysg, I.to_torch(small, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
@@ -178,7 +194,7 @@ def test_gradient_odd_hankel_count(setup):
     y_model, imh, absh = O.forward(models, s, mode=O.HANKEL_RULE, want_imh=True, want_absh=True)
     _, J = O.forward_jacobian_fd(models, s)
     kap = kappa(imh, s["T"], y_model, absh)
-    check(g.cpu().numpy().astype(np.float64), g_ref, "K = 121", gradient_bound(y_model, J, y_obs, bound32(kap, sysg.F)))
+    check(g.cpu().numpy().astype(np.float64), g_ref, "K = 121", *gbounds(y_model, J, y_obs, kap, sysg.F))
 
 
 def test_gradient_maximum_sizes(setup):
@@ -199,7 +215,7 @@ def test_gradient_maximum_sizes(setup):
     _, J = O.forward_jacobian_fd(models, s)
     kap = kappa(imh, s["T"], y_model, absh)
     check(g.cpu().numpy().astype(np.float64), g_ref, "maximum sizes",
-          gradient_bound(y_model, J, y_obs, bound32(kap, 128)))
+          *gbounds(y_model, J, y_obs, kap, 128))
 
 
 def test_autograd_function(setup):
@@ -245,12 +261,14 @@ def test_full_size_sampled_gradient(setup):
     _, g_ref = O.loglik_grad_fd(sub, s, y_obs, I.EPS_AN, I.EPS_MN)
     y, J = O.forward_jacobian_fd(sub, s)
     _, _, _, kap = oracle_ref(sub, name)
-    b = gradient_bound(y, J, y_obs, bound32(kap, sysg.F))
+    b, b_round = gbounds(y, J, y_obs, kap, sysg.F)
     err = np.linalg.norm((g[idx] - g_ref).reshape(24, -1), axis=1)
     ref = np.linalg.norm(g_ref.reshape(24, -1), axis=1)
     bn = np.linalg.norm(b.reshape(24, -1), axis=1)
+    good = np.linalg.norm(b_round.reshape(24, -1), axis=1) < 1e-3 * ref
     plain = err <= 1e-3 * ref
-    print(f"\nfull size: {plain.sum()} of 24 sampled models within 1e-3 (median {np.median(err / ref):.1e}); "
+    print(f"\nfull size: {plain.sum()} of 24 sampled models within 1e-3 (median {np.median(err / ref):.1e}), "
+          f"{plain[good].sum()} of the {good.sum()} whose propagated rounding term is below 1e-3; "
           f"worst error / allowed {np.max(err / (1e-3 * ref + bn)):.2f}")
     assert np.all(err <= 1e-3 * ref + bn)
-    assert plain.sum() >= 18
+    assert np.all(plain[good])

@@ -15,8 +15,10 @@ delta one of the component accuracies asserted separately (the spectrum
 relative to the Hankel sum's magnitude A_f, the two transform tables relative
 to each row's largest entry):
   FP64:  e_g <= 1e-7 + kappa_H,g 1e-12 + kappa_g 2^-46 + kappa_T,g 1e-8
-  FP32:  e_g <= 1e-4 + kappa_H,g 3e-5 + kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8
-and the fraction of gates inside the plain 1e-4 FP32 bound is reported.
+  FP32:  e_g <= 1e-4 + kappa_H,g 2^-17 + kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8
+and, on the well-conditioned gates (kappa_g (F + 1) 2^-24 + kappa_T,g 1e-8 <
+1e-4), at least 99.9 % inside the plain 1e-4; the fraction of all gates inside
+1e-4 is reported.
 """
 import numpy as np
 import pytest
@@ -25,7 +27,7 @@ import oracle as O
 from paper_2109_00661_gb300 import F32_SHAPES
 from paper_2109_00661_gb300 import inputs as I
 from parity_util import (DELTA_S32, DELTA_S64, DELTA_T, assert_within, bound32, bound64, kappa, loglik_bound,
-                         oracle_ref, oracle_system, rel_err, spectrum_err)
+                         oracle_ref, oracle_system, rel_err, rounding32, spectrum_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -99,11 +101,17 @@ def test_forward_f32_matches_oracle(lib, torch_mod, name):
     es = spectrum_err(imh, imh_ref, absh)
     e = rel_err(y, y_ref)
     F = imh.shape[1]
+    good = rounding32(kap, F) < 1e-4
     print(f"\n{name}: FP32 spectrum error max {es.max():.2e} p99 {np.quantile(es, 0.99):.2e}; "
           f"per-gate error max {e.max():.2e} median {np.median(e):.2e} p99 {np.quantile(e, 0.99):.2e}; "
-          f"within 1e-4: {np.mean(e <= 1e-4):.4f} of gates; e/kappa max {np.max(e / kap[0]):.2e}")
+          f"within 1e-4: {np.mean(e <= 1e-4):.4f} of gates; well-conditioned gates {good.mean():.3f} of all, "
+          f"{np.mean(e[good] <= 1e-4):.5f} of them within 1e-4 (worst {e[good].max():.2e})")
     assert es.max() < DELTA_S32, f"spectrum error {es.max():.3e}"
     assert_within(e, bound32(kap, F), "FP32 gates")
+    # the plain 1e-4 tolerance on the gates whose unavoidable FP32 rounding is
+    # below it: the few that miss sit where the Hankel sum cancels (A_f >> |Im H|),
+    # which multiplies the recursion's rounding (the kappa_H term)
+    assert np.mean(e[good] <= 1e-4) >= 0.999
 
 
 def test_forward_edge_cases(lib, torch_mod):
