@@ -192,6 +192,20 @@ int aem_loglik_f32_tc(const aem_system *sys, const aem_models_f32 *models, const
  * AEM_ERR_TIMEOUT a kernel recorded since the last call. */
 int aem_system_status(const aem_system *sys, int *status);
 
+/* Diagnostics of the bounded device wait (for tests; no counterpart in the
+ * paper).  spins > 0 sets the iteration limit of the tensor-core transform's
+ * completion wait (0 restores the default, 2^22 polls); skip_first_mma = 1
+ * makes each CTA of that kernel issue no MMA and no commit for its first
+ * tile, so its wait runs out with no tensor-core work in flight: the CTA then
+ * records AEM_ERR_TIMEOUT in the status word, frees its tensor memory and
+ * returns, leaving the outputs of its tiles unwritten.  The limit applies to
+ * the first wait only; the wait for a CTA's own MMAs after a timeout keeps the
+ * full limit (should that one also run out, the MMAs may still be in flight
+ * when the tensor memory is freed, which is undefined: treat a context that
+ * reported a timeout as unreliable).  Not thread-safe against launches on the
+ * same system.  skip_first_mma must be 0 or 1 (AEM_ERR_INVALID_ARG). */
+int aem_debug_bounded_wait(aem_system *sys, unsigned int spins, int skip_first_mma);
+
 /* Gradient of the log-likelihood above (FP32 forward model) with respect to
  * every merged layer's parameters, by reverse-mode differentiation of the
  * forward model of Section 2 and the likelihood of Section 2.3.2.
@@ -249,7 +263,13 @@ typedef struct {
     double pca_ridge;                      /* covariance ridge, fraction of the random-walk steps (>= 0) */
     int recycle_stages;                    /* 0..32; > 0 (with adaptive): particle recycling over that many stages */
     double zca;                            /* 0..1 (with adaptive): probability of the ZCA-coloured birth / death */
+    int precision;                         /* AEM_SMC_FP32 (default): every forward evaluation by the FP32 kernel;
+                                              AEM_SMC_FP64: the plain FP64 forward model (Algorithm 1 unchanged; the
+                                              Langevin moves, FP32 adjoint, are then unsupported) */
 } smc_desc;
+
+#define AEM_SMC_FP32 0
+#define AEM_SMC_FP64 1
 
 typedef struct smc_state smc_state;
 
@@ -372,10 +392,28 @@ int smc_run(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *stages_out);
 
 /* Synchronous (a10).  post_k [S x M]: N_k / N; log_bfipd [S]: log of the
- * BFIPD statistic of Section 2.3.3 with uniform p(k), i.e.
- * log(N_IP / (lambda_max N_nonIP)), +inf when no particle is non-chargeable;
- * log_z_k [S x M]: accumulated log Z_k.  Any pointer may be NULL. */
+ * BFIPD statistic of Section 2.3.3, the grouped Bayes factor
+ * |M_kappa| sum_{k chargeable} (pi_k / p_k) / (|M_lambda| sum_{k not} (pi_k / p_k))
+ * with the sampler's uniform p(k), i.e. log(N_IP / (lambda_max N_nonIP)):
+ * +inf when no particle is non-chargeable, -inf when none is chargeable
+ * (never clipped); log_z_k [S x M]: accumulated log Z_k.  The counts, the
+ * posterior probabilities and log BFIPD are formed on the device in FP64.  Any
+ * pointer may be NULL. */
 int smc_model_odds(const smc_state *st, double *post_k, double *log_bfipd, double *log_z_k);
+
+/* Failure reporting (synchronous).  status: AEM_OK, or the first failure a
+ * reweight step recorded since the last call (read and cleared):
+ * AEM_ERR_NONFINITE when a sounding had no particle with a finite
+ * log-likelihood (its gamma and log Z are left unchanged and its weights
+ * uniform within each model), AEM_ERR_NO_BRACKET when no probed tempering
+ * step kept TESS >= alpha N (more than (1 - alpha) N particles with ll = -inf;
+ * the smallest probed step is taken).  smc_reweight with gamma_out != NULL,
+ * smc_run and smc_run_graph return these codes themselves (smc_run stops at
+ * that stage; smc_run_graph finishes it, then stops).  nonfinite [S] (may be
+ * NULL): per sounding, how many log-likelihoods came out NaN or +inf since
+ * smc_init; the sampler sets each such value to -inf, so that particle has no
+ * weight and a proposal that produced one is rejected. */
+int smc_status(smc_state *st, int *status, int *nonfinite);
 
 /* Synchronous.  gamma [S], stage, accepted / proposed [S x 6] counts of the
  * last smc_mutate call by move type.  Any pointer may be NULL. */

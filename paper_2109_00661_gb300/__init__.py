@@ -16,7 +16,8 @@ from . import _lib
 from ._lib import AEMError, check
 
 __all__ = ["System", "forward_f32", "forward_f64", "spectrum_f32", "loglik_f32", "loglik_f64", "loglik_f32_tc",
-           "gates_from_spectrum", "loglik_grad_f32", "loglik", "system_status", "probe_peaks", "AEMError",
+           "gates_from_spectrum", "loglik_grad_f32", "loglik", "system_status", "debug_bounded_wait", "probe_peaks",
+           "AEMError",
            "CC_PAPER", "CC_PELTON", "GATES_FP32", "GATES_TF32_SPLIT", "GATES_BF16_SPLIT"]
 
 CC_PAPER = 0
@@ -192,6 +193,13 @@ def loglik_f32_tc(system, models, y_obs, eps_an, eps_mn, mode=GATES_TF32_SPLIT, 
     return (ll, gates) if want_gates else ll
 
 
+def debug_bounded_wait(system, spins=0, skip_first_mma=False):
+    """aem_debug_bounded_wait: the tensor-core transform's completion-wait limit
+    (0: the default) and whether its CTAs skip the first tile's MMAs (tests)."""
+    check(_lib.load().aem_debug_bounded_wait(system.handle, int(spins), int(skip_first_mma)),
+          "aem_debug_bounded_wait")
+
+
 def system_status(system):
     """aem_system_status: 0, or the error a kernel recorded (cleared on read)."""
     v = ctypes.c_int()
@@ -277,8 +285,14 @@ def loglik(system, models, y_obs, eps_an, eps_mn):
     """Differentiable FP32 log-likelihood: a torch.autograd.Function whose
     backward is the reverse-mode adjoint kernel.  models holds float32 CUDA
     tensors (logsig, logh, m, logtau, c) of shape [P, lmax] (any of which may
-    require grad) and int8 nlayers [P]; returns ll [P] float64."""
+    require grad) and int8 nlayers [P]; returns ll [P] float64.  When no
+    gradient can be needed (grad mode off, or no parameter tensor requires
+    grad) it is the plain aem_loglik_f32 launch, without the adjoint."""
     global _LOGLIK_FN
+    torch = _torch()
+    if not (torch.is_grad_enabled() and any(models[k].requires_grad for k in PARAMS)):
+        plain = {k: (models[k].detach() if k in PARAMS else models[k]) for k in ("nlayers",) + PARAMS}
+        return loglik_f32(system, plain, y_obs, eps_an, eps_mn)
     if _LOGLIK_FN is None:
         _LOGLIK_FN = _autograd_function()
     return _LOGLIK_FN.apply(system, models["nlayers"], y_obs, eps_an, eps_mn, *[models[k] for k in PARAMS])

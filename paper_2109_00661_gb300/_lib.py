@@ -76,6 +76,7 @@ class SMCDesc(ctypes.Structure):
         ("pca_ridge", c_double),
         ("recycle_stages", c_int),
         ("zca", c_double),
+        ("precision", c_int),
     ]
 
 
@@ -104,6 +105,7 @@ SIGNATURES = {
     "aem_loglik_f32_tc": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                            c_void_p, c_void_p], c_int),
     "aem_system_status": ([c_void_p, c_void_p], c_int),
+    "aem_debug_bounded_wait": ([c_void_p, ctypes.c_uint, c_int], c_int),
     "aem_loglik_grad_f32": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                              c_void_p], c_int),
     "smc_desc_defaults": ([ctypes.POINTER(SMCDesc)], c_int),
@@ -129,6 +131,7 @@ SIGNATURES = {
     "smc_langevin_stats": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_run": ([c_void_p, c_int, c_int, c_void_p], c_int),
     "smc_model_odds": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "smc_status": ([c_void_p, c_void_p, c_void_p], c_int),
     "smc_stats": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "smc_get_particles": ([c_void_p, c_int, ctypes.POINTER(ParticlesHost)], c_int),
     "smc_set_particles": ([c_void_p, ctypes.POINTER(ParticlesHost), c_void_p, c_void_p, c_int], c_int),
@@ -173,4 +176,6 @@ class AEMError(RuntimeError):
 def check(rc: int, what: str):
     if rc != 0:
         msg = load().aem_last_error()
-        raise AEMError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+        err = AEMError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+        err.code = rc
+        raise err

@@ -47,6 +47,10 @@ struct aem_system {
     // device status word: kernels record AEM_ERR_TIMEOUT here when a bounded
     // wait gives up (read and cleared by aem_system_status)
     int *d_status = nullptr;
+    // diagnostics of the tensor-core transform's bounded wait (aem_debug_bounded_wait):
+    // iteration limit (0: the default) and whether CTAs issue nothing for their first tile
+    unsigned int wait_spins = 0;
+    int wait_skip_mma = 0;
     // launch shape of the FP32 forward kernel per lmax (index into its shape
     // table, 0 = default), set by aem_autotune_forward / aem_forward_shape
     int f32_shape[AEM_MAX_LAYERS + 1] = {};
@@ -64,6 +68,11 @@ int build_tables(const aem_system_desc *desc, SystemTables *out);
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
                          cudaStream_t stream, int *counter = nullptr, const int *active = nullptr);
+// The plain FP64 forward model + log-likelihood with the same per-sounding
+// rows of y_obs (forward.cu); active as above.
+int loglik_f64_soundings(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
+                         int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
+                         cudaStream_t stream, const int *active = nullptr);
 // Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
 // with per-sounding rows of y_obs (forward.cu); counter as above.
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,

@@ -12,16 +12,26 @@
 // (11-bit significand) leaves a relative residual near 2^-22 per term, BF16
 // (8-bit) near 2^-17.
 //
-// One CTA of four warps per 128-model tile (persistent over tiles): the
-// threads stage A_hi / A_lo of the tile and, once per CTA, B_hi / B_lo in
+// One CTA of four warps per 128-model tile (persistent over tiles, several
+// CTAs per SM so that one CTA's staging overlaps another's MMA and epilogue):
+// the threads stage A_hi / A_lo of the tile and, once per CTA, B_hi / B_lo in
 // shared memory in the canonical K-major layout without swizzle (core
-// matrices of 8 rows x 16 bytes); one thread issues the tcgen05.mma chain
-// into a TMEM accumulator (row m of the tile in TMEM lane m, gate n in column
-// n) and commits it to an mbarrier; every warp then reads its 32 lanes with
-// tcgen05.ld and forms the gates and the likelihood of its 32 models.  Every
-// wait is bounded: on a timeout the CTA records AEM_ERR_TIMEOUT in the
-// system's status word, waits (bounded) once more for its own MMAs, frees its
-// TMEM and returns.
+// matrices of 8 rows x 16 bytes), each lane converting one 16-byte core-matrix
+// row so that a warp's stores cover 512 contiguous bytes; one thread issues
+// the tcgen05.mma chain into a TMEM accumulator (row m of the tile in TMEM
+// lane m, gate n in column n) and commits it to an mbarrier; every warp then
+// reads its 32 lanes with tcgen05.ld and forms the gates and the likelihood
+// of its 32 models.  The likelihood terms are FP32 (Section 2.3.2's Gaussian:
+// the residual from a float pair holding the FP64 datum, the variance, one
+// logarithm and one division per gate) and their sum is carried as an
+// unevaluated FP32 pair (Knuth's TwoSum), exact to about 2^-48 of the sum of
+// magnitudes, so no FP64 arithmetic is left per gate.  Every wait is bounded:
+// on a timeout the CTA records AEM_ERR_TIMEOUT in the system's status word,
+// waits (bounded) once more for its own MMAs, frees its TMEM and returns.  If
+// that second wait also gives up, the MMAs it issued may still be in flight
+// when the TMEM is freed, which the tcgen05 model leaves undefined: the
+// recorded timeout then means the device context should be treated as
+// unreliable.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,7 +45,7 @@ namespace {
 constexpr int kTM = 128;       // models per tile = MMA M
 constexpr int kThreads = 128;  // warp w reads TMEM lanes 32w .. 32w + 31
 constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr double kPi = 3.14159265358979323846;
+constexpr double kLn2Pi = 1.83787706640934548356;  // ln(2 pi)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -92,10 +102,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
 }
 
 // Bounded wait for the given phase parity of the mbarrier.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round to nearest, no overflow).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -156,14 +173,6 @@ struct Split<1> {
     }
 };
 
-// Byte offset of element (row r, k) in the K-major no-swizzle layout with
-// K-adjacent core matrices 128 bytes apart and 8-row groups sbo bytes apart.
-template <int ES>
-__device__ __forceinline__ uint32_t kmajor_offset(int r, int k, uint32_t sbo) {
-    constexpr int KC = 16 / ES;
-    return (uint32_t)(r >> 3) * sbo + (uint32_t)(k / KC) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k % KC) * ES;
-}
-
 struct TcArgs {
     const float *imh;  // [P][F]
     int P, F, G, KP, N, ncols;
@@ -175,26 +184,84 @@ struct TcArgs {
     float *gates;  // [P][G] or null
     double *ll;    // [P] or null
     int *status;
+    uint32_t spins;  // iteration limit of the completion wait
+    int skip_mma;    // diagnostics: issue nothing for the first tile (the wait then runs out)
 };
+
+// The likelihood terms of one model's gates (Section 2.3.2), FP32 terms
+// with the TwoSum-carried sum: for gate g, yh the prediction, (yhi, ylo) the
+// float pair of the datum and ea2 = eps_an^2,
+//   r = (yhi - yh) + ylo,  v = ea2 + (eps_mn yh)^2,  t = r^2 / v + ln v,
+// and ll = -1/2 (sum t + G ln 2 pi) formed in FP64 once per model.
+struct LlAcc {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float yh, float2 y, float ea2, float em) {
+        const float r = (y.x - yh) + y.y;
+        const float q = em * yh;
+        const float v = fmaf(q, q, ea2);
+        const float t = __fdiv_rn(r * r, v) + logf(v);
+        float s1, e1;
+        two_sum(s, t, s1, e1);
+        s = s1;
+        e += e1;
+    }
+    __device__ __forceinline__ double ll(int G) const {
+        return -0.5 * (((double)s + (double)e) + (double)G * kLn2Pi);
+    }
+};
+
+// Converts the 16-byte core-matrix row of element chunk (r, kc) of the tile:
+// chunk kc holds elements 16/ES * kc .. of row r.  src: that row's FP32
+// values (nullptr: a padding row), zero past F.
+template <int KIND>
+__device__ __forceinline__ void stage_chunk(const float *__restrict__ src, int F, int kc, bool vec4,
+                                            unsigned char *hi_row, unsigned char *lo_row) {
+    using S = Split<KIND>;
+    constexpr int KC = 16 / S::ES;  // elements per 16-byte core-matrix row
+    float x[KC];
+    const int k0 = kc * KC;
+    if (src && vec4 && k0 + KC <= F) {
+#pragma unroll
+        for (int q = 0; q < KC; q += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(src + k0 + q));
+            x[q] = v.x;
+            x[q + 1] = v.y;
+            x[q + 2] = v.z;
+            x[q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < KC; ++q) x[q] = (src && k0 + q < F) ? __ldg(src + k0 + q) : 0.f;
+    }
+    typename S::T h[KC], l[KC];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) S::run(x[q], h[q], l[q]);
+    *reinterpret_cast<uint4 *>(hi_row) = *reinterpret_cast<const uint4 *>(h);
+    *reinterpret_cast<uint4 *>(lo_row) = *reinterpret_cast<const uint4 *>(l);
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     using S = Split<KIND>;
-    using E = typename S::T;
     constexpr int ES = S::ES;
     constexpr int KI = 32 / ES;  // K of one MMA: two core matrices
+    constexpr int KC = 16 / ES;  // elements per core-matrix row
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     unsigned char *base = smem_raw + pad;
-    const uint32_t sbo = (uint32_t)(a.KP / (16 / ES)) * 128u;  // same for A and B
+    const int NKC = a.KP / KC;                // core-matrix columns (16-byte chunks per row)
+    const uint32_t sbo = (uint32_t)NKC * 128u;  // same for A and B
     const uint32_t a_bytes = (uint32_t)kTM * a.KP * ES, b_bytes = (uint32_t)a.N * a.KP * ES;
     unsigned char *Ahi = base, *Alo = base + a_bytes, *Bhi = base + 2 * a_bytes, *Blo = Bhi + b_bytes;
-    uint64_t *mbar_p = reinterpret_cast<uint64_t *>(Blo + b_bytes);
+    float2 *ysplit = reinterpret_cast<float2 *>(Blo + b_bytes);  // [2][G]: the datum rows of this tile
+    float *ea2 = reinterpret_cast<float *>(ysplit + 2 * AEM_MAX_GATES);
+    uint64_t *mbar_p = reinterpret_cast<uint64_t *>(ea2 + AEM_MAX_GATES);
     uint32_t *slot_p = reinterpret_cast<uint32_t *>(mbar_p + 1);
     int *abort_p = reinterpret_cast<int *>(slot_p + 1);
     const uint32_t mbar = smem_u32(mbar_p);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool vec4 = (a.F & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.imh) & 15) == 0);
 
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -203,15 +270,13 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     __syncwarp();
     if (warp == 0) tmem_alloc(smem_u32(slot_p), (uint32_t)a.ncols);
     // B = T (rows: gates, zero-padded to N; columns: frequencies, zero-padded to KP)
-    for (int i = tid; i < a.N * a.KP; i += kThreads) {
-        const int n = i / a.KP, k = i - (i / a.KP) * a.KP;
-        const float x = (n < a.G && k < a.F) ? a.T[n * a.F + k] : 0.f;
-        E hi, lo;
-        S::run(x, hi, lo);
-        const uint32_t o = kmajor_offset<ES>(n, k, sbo);
-        *reinterpret_cast<E *>(Bhi + o) = hi;
-        *reinterpret_cast<E *>(Blo + o) = lo;
+    for (int c = tid; c < a.N * NKC; c += kThreads) {
+        const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
+        const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
+        stage_chunk<KIND>(r < a.G ? a.T + (size_t)r * a.F : nullptr, a.F, kc, false, Bhi + o, Blo + o);
     }
+    if (a.eps_an)
+        for (int g = tid; g < a.G; g += kThreads) ea2[g] = (float)(a.eps_an[g] * a.eps_an[g]);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
@@ -219,27 +284,39 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     const uint32_t idesc = instr_desc(KIND == 0 ? 2u : 1u, (uint32_t)kTM, (uint32_t)a.N);
     const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
     const int ntiles = (a.P + kTM - 1) / kTM;
+    const float em = (float)a.eps_mn;
     uint32_t phase = 0;
     bool pending = false;  // an MMA chain committed and not yet observed complete
+    bool first = true;
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // stage the tile's spectra (rows past P and columns past F are zero)
         const size_t row0 = (size_t)tile * kTM;
-        for (int i = tid; i < kTM * a.KP; i += kThreads) {
-            const int r = i / a.KP, k = i - (i / a.KP) * a.KP;
+        // the datum rows this tile's models use, as float pairs (at most two
+        // when models_per_row >= the tile; otherwise the epilogue splits per model)
+        const size_t s0 = row0 / (size_t)a.obs_per;
+        const bool split_rows = a.y_obs && (size_t)a.obs_per >= (size_t)kTM;
+        if (split_rows)
+            for (int i = tid; i < 2 * a.G; i += kThreads) {
+                const size_t srow = s0 + (size_t)(i / a.G);
+                const size_t last = ((size_t)a.P - 1) / (size_t)a.obs_per;
+                const double y = a.y_obs[(srow <= last ? srow : last) * a.G + (i % a.G)];
+                const float hi = (float)y;
+                ysplit[i] = make_float2(hi, (float)(y - (double)hi));
+            }
+        // stage the tile's spectra (rows past P and columns past F are zero);
+        // consecutive lanes fill consecutive 16-byte rows of one core matrix
+        for (int c = tid; c < kTM * NKC; c += kThreads) {
+            const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
             const size_t m = row0 + r;
-            const float x = (m < (size_t)a.P && k < a.F) ? a.imh[m * a.F + k] : 0.f;
-            E hi, lo;
-            S::run(x, hi, lo);
-            const uint32_t o = kmajor_offset<ES>(r, k, sbo);
-            *reinterpret_cast<E *>(Ahi + o) = hi;
-            *reinterpret_cast<E *>(Alo + o) = lo;
+            const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
+            stage_chunk<KIND>(m < (size_t)a.P ? a.imh + m * a.F : nullptr, a.F, kc, vec4, Ahi + o, Alo + o);
         }
         fence_async_smem();
         tc_before_sync();
         __syncthreads();
         tc_after_sync();
-        if (tid == 0) {
+        const bool issue = !(first && a.skip_mma);
+        if (tid == 0 && issue) {
             for (int ks = 0; ks < a.KP / KI; ++ks) {
                 const uint32_t off = (uint32_t)ks * 256u;
                 const uint64_t dah = smem_desc(ahi + off, 128u, sbo), dal = smem_desc(alo + off, 128u, sbo);
@@ -250,8 +327,9 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
             }
             mma_commit(mbar);
         }
-        pending = true;
-        const bool done = mbar_wait_bounded(mbar, phase);
+        first = false;
+        pending = issue;
+        const bool done = mbar_wait_bounded(mbar, phase, a.spins);
         if (!done) atomicExch(abort_p, 1);
         __syncthreads();
         if (*abort_p) break;
@@ -261,8 +339,10 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
         // epilogue: this thread's model is row 32 warp + lane of the tile
         const size_t m = row0 + (size_t)warp * 32 + lane;
         const bool valid = m < (size_t)a.P;
-        const double *y = a.y_obs ? a.y_obs + (valid ? (m / (size_t)a.obs_per) * a.G : 0) : nullptr;
-        double acc = 0.0;
+        const size_t srow = valid ? m / (size_t)a.obs_per : 0;
+        const float2 *yrow = split_rows ? ysplit + (srow - s0) * a.G : nullptr;
+        const double *yd = (a.y_obs && !split_rows) ? a.y_obs + srow * a.G : nullptr;
+        LlAcc acc;
         for (int c = 0; c < a.N; c += 8) {
             float v[8];
             tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
@@ -271,22 +351,27 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
                 const int g = c + q;
                 if (valid && g < a.G) {
                     if (a.gates) a.gates[m * a.G + g] = v[q];
-                    if (y) {
-                        const double yh = (double)v[q], ea = a.eps_an[g];
-                        const double var = ea * ea + (a.eps_mn * yh) * (a.eps_mn * yh);
-                        const double r = y[g] - yh;
-                        acc += r * r / var + log(2.0 * kPi * var);
+                    if (a.y_obs) {
+                        float2 y;
+                        if (yrow) {
+                            y = yrow[g];
+                        } else {
+                            const double yv = yd[g];
+                            y.x = (float)yv;
+                            y.y = (float)(yv - (double)y.x);
+                        }
+                        acc.add(v[q], y, ea2[g], em);
                     }
                 }
             }
         }
-        if (valid && a.ll) a.ll[m] = -0.5 * acc;
+        if (valid && a.ll) a.ll[m] = acc.ll(a.G);
         tc_before_sync();
         __syncthreads();  // every lane read before the next chain overwrites the accumulator
     }
     if (*abort_p) {
         if (tid == 0) atomicExch(a.status, (int)AEM_ERR_TIMEOUT);
-        if (pending) mbar_wait_bounded(mbar, phase);  // our own MMAs, once more with a limit
+        if (pending) mbar_wait_bounded(mbar, phase);  // our own MMAs, once more with the full limit
     }
     tc_before_sync();
     __syncthreads();
@@ -295,27 +380,29 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
 }
 
 // FP32 CUDA-core form of the same transform (for comparison): one thread per
-// model, T staged in shared memory.
+// model, T staged in shared memory, the same FP32 likelihood terms.
 __global__ void gates_fp32_kernel(TcArgs a) {
     extern __shared__ float Ts[];
+    __shared__ float ea2[AEM_MAX_GATES];
     for (int i = threadIdx.x; i < a.G * a.F; i += blockDim.x) Ts[i] = a.T[i];
+    if (a.eps_an)
+        for (int g = threadIdx.x; g < a.G; g += blockDim.x) ea2[g] = (float)(a.eps_an[g] * a.eps_an[g]);
     __syncthreads();
+    const float em = (float)a.eps_mn;
     for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < (size_t)a.P; m += (size_t)gridDim.x * blockDim.x) {
         const float *x = a.imh + m * a.F;
         const double *y = a.y_obs ? a.y_obs + (m / (size_t)a.obs_per) * a.G : nullptr;
-        double acc = 0.0;
+        LlAcc acc;
         for (int g = 0; g < a.G; ++g) {
             float s = 0.f;
             for (int k = 0; k < a.F; ++k) s = fmaf(Ts[g * a.F + k], x[k], s);
             if (a.gates) a.gates[m * a.G + g] = s;
             if (y) {
-                const double yh = (double)s, ea = a.eps_an[g];
-                const double var = ea * ea + (a.eps_mn * yh) * (a.eps_mn * yh);
-                const double r = y[g] - yh;
-                acc += r * r / var + log(2.0 * kPi * var);
+                const float hi = (float)y[g];
+                acc.add(s, make_float2(hi, (float)(y[g] - (double)hi)), ea2[g], em);
             }
         }
-        if (a.ll) a.ll[m] = -0.5 * acc;
+        if (a.ll) a.ll[m] = acc.ll(a.G);
     }
 }
 
@@ -328,7 +415,7 @@ int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode
                         cudaStream_t stream) {
     const SystemTables &h = sys->host;
     TcArgs a{imh, P, h.F, h.G, 0, 0, 0, sys->d_T_f, y_obs, obs_per > 0 ? obs_per : 1, eps_an, eps_mn, gates, ll,
-             sys->d_status};
+             sys->d_status, sys->wait_spins ? sys->wait_spins : kSpinLimit, sys->wait_skip_mma};
     if (mode == AEM_GATES_FP32) {
         const size_t smem = sizeof(float) * (size_t)h.G * h.F;
         int grid = (int)((P + 255) / 256);
@@ -342,7 +429,8 @@ int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode
     a.KP = round_up(h.F, KI);
     a.N = round_up(h.G, 16);
     a.ncols = a.N <= 32 ? 32 : 64;
-    const size_t smem = (size_t)2 * (kTM + a.N) * a.KP * ES + 1024 + 64;
+    const size_t smem = (size_t)2 * (kTM + a.N) * a.KP * ES + 1024 + sizeof(float2) * 2 * AEM_MAX_GATES +
+                        sizeof(float) * AEM_MAX_GATES + 64;
     auto kern = tf32 ? gates_tc_kernel<0> : gates_tc_kernel<1>;
     AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -383,6 +471,14 @@ extern "C" int aem_loglik_f32_tc(const aem_system *sys, const aem_models_f32 *mo
     int rc = aem_forward_f32(sys, models, nullptr, imh_work, stream);
     if (rc) return rc;
     return aem_gates_from_spectrum(sys, imh_work, models->n_models, mode, y_obs, eps_an, eps_mn, gates, ll, stream);
+}
+
+extern "C" int aem_debug_bounded_wait(aem_system *sys, unsigned int spins, int skip_first_mma) {
+    if (!sys || (skip_first_mma != 0 && skip_first_mma != 1))
+        return fail(AEM_ERR_INVALID_ARG, "aem_debug_bounded_wait: NULL system or skip_first_mma not 0 / 1");
+    sys->wait_spins = spins;
+    sys->wait_skip_mma = skip_first_mma;
+    return AEM_OK;
 }
 
 extern "C" int aem_system_status(const aem_system *sys, int *status) {

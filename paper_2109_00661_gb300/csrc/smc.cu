@@ -193,8 +193,11 @@ __global__ void prior_kernel(PState st, Params pr) {
 // Direct sum of the two profiles (Section 2.1, Fig. 2): the merged
 // interfaces are the sorted union; each merged layer takes log10 sigma from
 // the conductive profile and m from the chargeable profile at its top.
-__global__ void merge_kernel(PState st, int P, int LMS, int8_t *nl, float *logsig, float *logh, float *m,
-                             float *logtau, float *cc) {
+// T = float for the FP32 forward model, double for the plain FP64 one (the
+// particle's own parameters are floats either way; thicknesses and log10 tau
+// are formed in double and rounded to T).
+template <class T>
+__global__ void merge_kernel(PState st, int P, int LMS, int8_t *nl, T *logsig, T *logh, T *m, T *logtau, T *cc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const int kappa = st.kappa[i], lam = st.lam[i];
@@ -212,8 +215,8 @@ __global__ void merge_kernel(PState st, int P, int LMS, int8_t *nl, float *logsi
         }
     }
     const int L = n + 1;
-    const float lt = (float)log10((double)st.tau[i]);
-    const float cv = st.c[i];
+    const T lt = (T)log10((double)st.tau[i]);
+    const T cv = st.c[i];
     int ic = 0, jm = 0;
     for (int q = 0; q < L; ++q) {
         float top = q == 0 ? 0.f : z[q - 1];
@@ -223,17 +226,17 @@ __global__ void merge_kernel(PState st, int P, int LMS, int8_t *nl, float *logsi
         }
         size_t o = (size_t)i * LMS + q;
         logsig[o] = ic == 0 ? st.phib[i] : st.phic[i * KS + ic - 1];
-        m[o] = jm == 0 ? 0.f : st.mv[i * KS + jm - 1];
+        m[o] = jm == 0 ? T(0) : (T)st.mv[i * KS + jm - 1];
         double th = q < L - 1 ? (double)z[q] - (double)top : 1.0;
-        logh[o] = (float)log10(th > 1e-30 ? th : 1e-30);
+        logh[o] = (T)log10(th > 1e-30 ? th : 1e-30);
         logtau[o] = lt;
         cc[o] = cv;
     }
     for (int q = L; q < LMS; ++q) {
         size_t o = (size_t)i * LMS + q;
-        logsig[o] = 0.f;
-        m[o] = 0.f;
-        logh[o] = 0.f;
+        logsig[o] = T(0);
+        m[o] = T(0);
+        logh[o] = T(0);
         logtau[o] = lt;
         cc[o] = cv;
     }
@@ -299,7 +302,8 @@ __device__ inline double warp_max(double v) {
 // ESS_k = S1^2 / S2 and TESS = sum_k ESS_k.  gamma_t by bisection on TESS = alpha N.
 __global__ void __launch_bounds__(kGroupThreads)
     reweight_kernel(const double *ll, const int *perm, const int *off, const int *counts, int N, int M, double alpha,
-                    int iters, double *gamma, double *logz, double *Wg, double *dgamma_out, int *done_out) {
+                    int iters, double *gamma, double *logz, double *Wg, double *dgamma_out, int *done_out,
+                    int *status = nullptr) {
     __shared__ double s_max[AEM_SMC_MAX_MODELS], s_s1[AEM_SMC_MAX_MODELS], s_ess[AEM_SMC_MAX_MODELS];
     __shared__ double s_tess;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -320,6 +324,25 @@ __global__ void __launch_bounds__(kGroupThreads)
         if (lane == 0) s_max[k] = mx;
     }
     __syncthreads();
+    // no particle of the sounding with a finite log-likelihood: there is no
+    // weight to form; record AEM_ERR_NONFINITE, keep gamma and log Z, and
+    // leave uniform weights within each model so the resample stays defined
+    if (tid == 0) {
+        bool any = false;
+        for (int k = 0; k < M; ++k) any = any || s_max[k] > -INFINITY;
+        s_tess = any ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (s_tess == 0.0) {
+        for (int k = warp; k < M; k += nw)
+            for (int r = lane; r < cnt[k]; r += 32) Wg[s * N + o[k] + r] = 1.0 / (double)cnt[k];
+        if (tid == 0) {
+            dgamma_out[s] = 0.0;
+            done_out[s] = 0;
+            if (status) atomicExch(status, (int)AEM_ERR_NONFINITE);
+        }
+        return;
+    }
     auto evaluate = [&](double dg) {
         for (int k = warp; k < M; k += nw) {
             double s1 = 0.0, s2 = 0.0;
@@ -362,6 +385,10 @@ __global__ void __launch_bounds__(kGroupThreads)
             else
                 hi = mid;
         }
+        // lo = 0: no probed step kept TESS >= alpha N (more than (1 - alpha) N
+        // particles with ll = -inf drop out at any positive step); take the
+        // smallest probed step and record AEM_ERR_NO_BRACKET
+        if (lo == 0.0 && status && tid == 0) atomicExch(status, (int)AEM_ERR_NO_BRACKET);
         dg = lo > 0.0 ? lo : hi;
         done = 0;
         evaluate(dg);
@@ -381,6 +408,48 @@ __global__ void __launch_bounds__(kGroupThreads)
         dgamma_out[s] = dg;
         done_out[s] = done;
     }
+}
+
+// Non-finite log-likelihoods (NaN, or +inf, which no Gaussian likelihood can
+// reach) become -inf, so the particle carries zero weight and every proposal
+// that produced one is rejected; each is counted per sounding.
+__global__ void sanitize_ll_kernel(double *ll, int P, int N, int *nonfinite, const int *active = nullptr) {
+    if (active && *active == 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const double v = ll[i];
+    if (isnan(v) || v == INFINITY) {
+        ll[i] = -INFINITY;
+        atomicAdd(&nonfinite[i / N], 1);
+    }
+}
+
+// ---------------------------------------------------------- model odds (a10)
+// One thread per sounding, FP64: pi(k|y) = N_k / N and the BFIPD statistic of
+// Section 2.3.3 with the sampler's uniform p(k) (uniform on kappa and on
+// lambda), B = |M_kappa| sum_IP (pi / p) / (|M_lambda| sum_nonIP (pi / p)),
+// |M_kappa| = kappa_max + 1 and |M_lambda| = (kappa_max + 1) lambda_max:
+// +inf when no particle is non-chargeable, -inf when none is chargeable.
+__global__ void odds_kernel(const int *counts, int S, int M, int lp1, int N, double *post, double *lbf) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double pk = 1.0 / (double)M;
+    double s_ip = 0.0, s_non = 0.0;
+    for (int k = 0; k < M; ++k) {
+        const double v = (double)counts[s * M + k] / (double)N;
+        post[s * M + k] = v;
+        if (k % lp1 == 0)
+            s_non += v / pk;
+        else
+            s_ip += v / pk;
+    }
+    const double m_kappa = (double)(M / lp1), m_lambda = (double)(M / lp1) * (double)(lp1 - 1);
+    if (s_non == 0.0)
+        lbf[s] = INFINITY;
+    else if (s_ip == 0.0)
+        lbf[s] = -INFINITY;
+    else
+        lbf[s] = log(m_kappa * s_ip) - log(m_lambda * s_non);
 }
 
 // ------------------------------------------------------------- resample (a8)
@@ -1421,12 +1490,13 @@ __global__ void stage_inc_kernel(int *d_stage) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_stage += 1;
 }
 
-__global__ void stage_cond_kernel(const double *gamma, int S, const int *d_stage, int stop_stage,
+__global__ void stage_cond_kernel(const double *gamma, int S, const int *d_stage, int stop_stage, const int *status,
                                   cudaGraphConditionalHandle h) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     bool all = true;
     for (int s = 0; s < S; ++s) all = all && gamma[s] >= 1.0;
-    cudaGraphSetConditional(h, (!all && *d_stage < stop_stage) ? 1u : 0u);
+    // a failed reweight step (status word set) ends the loop after this stage
+    cudaGraphSetConditional(h, (!all && *d_stage < stop_stage && *status == 0) ? 1u : 0u);
 }
 
 // App. B's sweep count on the device, from the acceptance counts of the
@@ -1549,6 +1619,16 @@ struct smc_state {
     // graph form with App. B's sweep count: R_t, this sweep's gate, whether a
     // previous stage's acceptance counts exist
     int *d_sweeps = nullptr, *d_gate = nullptr, *d_have_prev = nullptr;
+    // failure reporting: the sampler's status word (AEM_ERR_NONFINITE /
+    // AEM_ERR_NO_BRACKET recorded by the reweight step, read and cleared by
+    // smc_status) and the per-sounding count of non-finite log-likelihoods
+    // mapped to -inf since smc_init
+    int *d_status = nullptr, *nonfinite = nullptr;
+    // model odds formed on the device in FP64: post [S][M], log BFIPD [S]
+    double *d_post = nullptr, *d_lbf = nullptr;
+    // merged models in FP64 for the plain double-precision forward model
+    // (desc.precision = AEM_SMC_FP64)
+    double *m64_logsig = nullptr, *m64_logh = nullptr, *m64_m = nullptr, *m64_logtau = nullptr, *m64_c = nullptr;
     std::vector<int> acc_prev, nprop_prev;
     bool have_prev = false;
 };
@@ -1575,26 +1655,47 @@ int alloc_pstate(smc_state *st, PState *ps, size_t count = 0) {
     return AEM_OK;
 }
 
-int run_loglik(smc_state *st, PState ps, const int *active = nullptr) {
-    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
-                                                                st->m_logh, st->m_m, st->m_logtau, st->m_c);
+int sanitize(smc_state *st, double *ll, const int *active = nullptr) {
+    sanitize_ll_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ll, st->P, st->N, st->nonfinite, active);
     AEM_CUDA_TRY(cudaGetLastError());
-    aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
-    return loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream,
-                                st->fwd_counter, active);
+    return AEM_OK;
+}
+
+// Merge and forward model + log-likelihood of a particle set, in FP32 or, with
+// desc.precision = AEM_SMC_FP64, in the plain FP64 form; non-finite results
+// become -inf.
+int run_loglik(smc_state *st, PState ps, const int *active = nullptr) {
+    int rc;
+    if (st->d.precision == AEM_SMC_FP64) {
+        merge_kernel<double><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(
+            ps, st->P, st->LMS, st->m_nl, st->m64_logsig, st->m64_logh, st->m64_m, st->m64_logtau, st->m64_c);
+        AEM_CUDA_TRY(cudaGetLastError());
+        aem_models_f64 mm{st->P, st->LMS, st->m_nl, st->m64_logsig, st->m64_logh, st->m64_m, st->m64_logtau, st->m64_c};
+        rc = loglik_f64_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream, active);
+    } else {
+        merge_kernel<float><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(
+            ps, st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c);
+        AEM_CUDA_TRY(cudaGetLastError());
+        aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
+        rc = loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream,
+                                  st->fwd_counter, active);
+    }
+    if (rc) return rc;
+    return sanitize(st, ps.ll, active);
 }
 
 // Log-likelihood and particle-space gradient of a particle set: merge, the
 // adjoint kernel on the merged models, then the chain rule back to the
 // particle's parameters.
 int run_grad(smc_state *st, PState ps, float *pg) {
-    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
+    merge_kernel<float><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
                                                                 st->m_logh, st->m_m, st->m_logtau, st->m_c);
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
     int rc = loglik_grad_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->mgrad,
                                        st->stream, st->grad_work);
     if (rc) return rc;
+    if ((rc = sanitize(st, ps.ll))) return rc;
     pgrad_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(ps, st->mgrad, st->P, st->LMS,
                                                                  st->d.tau_log_prior, pg);
     AEM_CUDA_TRY(cudaGetLastError());
@@ -1625,6 +1726,10 @@ int check_desc(const smc_desc *d) {
         return fail(AEM_ERR_INVALID_ARG, "smc_create: recycle_stages outside 0..32, or set without adaptive");
     if (d->n_langevin < 0 || d->n_langevin > 1000 || !(d->langevin_h > 0))
         return fail(AEM_ERR_INVALID_ARG, "smc_create: n_langevin outside 0..1000 or langevin_h <= 0");
+    if (d->precision != AEM_SMC_FP32 && d->precision != AEM_SMC_FP64)
+        return fail(AEM_ERR_INVALID_ARG, "smc_create: precision is neither AEM_SMC_FP32 nor AEM_SMC_FP64");
+    if (d->precision == AEM_SMC_FP64 && d->n_langevin > 0)
+        return fail(AEM_ERR_UNSUPPORTED, "smc_create: the Langevin moves use the FP32 adjoint; not with AEM_SMC_FP64");
     return AEM_OK;
 }
 
@@ -1662,6 +1767,7 @@ extern "C" int smc_desc_defaults(smc_desc *d) {
     d->pca_ridge = 0.01;
     d->recycle_stages = 0;
     d->zca = 0.0;
+    d->precision = AEM_SMC_FP32;
     return AEM_OK;
 }
 
@@ -1730,7 +1836,13 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         (rc = dalloc(st, &st->pca_hi, (size_t)st->S * st->M)) || (rc = dalloc(st, &st->pca_ok, (size_t)st->S * st->M)) ||
         (rc = dalloc(st, &st->d_stage, 1)) || (rc = dalloc(st, &st->fwd_counter, 1)) ||
         (rc = dalloc(st, &st->d_sweeps, 1)) || (rc = dalloc(st, &st->d_gate, 1)) ||
-        (rc = dalloc(st, &st->d_have_prev, 1)) ||
+        (rc = dalloc(st, &st->d_have_prev, 1)) || (rc = dalloc(st, &st->d_status, 1)) ||
+        (rc = dalloc(st, &st->nonfinite, (size_t)st->S)) || (rc = dalloc(st, &st->d_post, (size_t)st->S * st->M)) ||
+        (rc = dalloc(st, &st->d_lbf, (size_t)st->S)) ||
+        (desc->precision == AEM_SMC_FP64 &&
+         ((rc = dalloc(st, &st->m64_logsig, P * st->LMS)) || (rc = dalloc(st, &st->m64_logh, P * st->LMS)) ||
+          (rc = dalloc(st, &st->m64_m, P * st->LMS)) || (rc = dalloc(st, &st->m64_logtau, P * st->LMS)) ||
+          (rc = dalloc(st, &st->m64_c, P * st->LMS)))) ||
         (rc = dalloc(st, &st->lf, P))) {
         smc_destroy(st);
         return rc;
@@ -1746,6 +1858,8 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         e = cudaMemcpy(st->pca_a, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemset(st->pca_ok, 0, sizeof(int) * st->S * st->M);
+    if (e == cudaSuccess) e = cudaMemset(st->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->nonfinite, 0, sizeof(int) * st->S);
     if (e == cudaSuccess && desc->recycle_stages > 0) {
         const size_t HP = (size_t)desc->recycle_stages * st->P;
         if (HP * KS >= ((size_t)1 << 31)) {
@@ -1787,6 +1901,8 @@ extern "C" int smc_init(smc_state *st) {
     AEM_CUDA_TRY(cudaMemsetAsync(st->nprop, 0, sizeof(int) * st->S * kMoves, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->lacc, 0, sizeof(int) * st->S, st->stream));
     AEM_CUDA_TRY(cudaMemsetAsync(st->lprop, 0, sizeof(int) * st->S, st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->d_status, 0, sizeof(int), st->stream));
+    AEM_CUDA_TRY(cudaMemsetAsync(st->nonfinite, 0, sizeof(int) * st->S, st->stream));
     {
         std::vector<double> h0(st->S, st->d.langevin_h);
         std::vector<double> a0((size_t)st->S * st->M, 1.0);
@@ -1805,6 +1921,19 @@ extern "C" int smc_init(smc_state *st) {
     return record_history(st);
 }
 
+// Synchronises the stream, then reads and clears the sampler's status word:
+// AEM_OK, or the AEM_ERR_NONFINITE / AEM_ERR_NO_BRACKET a reweight step recorded.
+static int take_status(smc_state *st) {
+    int v = 0;
+    AEM_CUDA_TRY(cudaMemcpyAsync(&v, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    if (v == 0) return AEM_OK;
+    AEM_CUDA_TRY(cudaMemsetAsync(st->d_status, 0, sizeof(int), st->stream));
+    return fail(v, v == AEM_ERR_NO_BRACKET
+                       ? "reweight: no tempering step kept TESS >= alpha N (bisection could not bracket)"
+                       : "reweight: a sounding has no particle with a finite log-likelihood");
+}
+
 static int launch_group(smc_state *st) {
     group_kernel<<<st->S, kGroupThreads, st->N, st->stream>>>(st->cur.kappa, st->cur.lam, st->N,
                                                               st->d.lambda_max + 1, st->M, st->perm, st->off,
@@ -1820,11 +1949,11 @@ extern "C" int smc_reweight(smc_state *st, double *gamma_out) {
     st->stage += 1;
     reweight_kernel<<<st->S, kGroupThreads, 0, st->stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
                                                              st->d.alpha, st->d.bisect_iters, st->gamma, st->logz,
-                                                             st->Wg, st->dgamma, st->done);
+                                                             st->Wg, st->dgamma, st->done, st->d_status);
     AEM_CUDA_TRY(cudaGetLastError());
     if (gamma_out) {
         AEM_CUDA_TRY(cudaMemcpyAsync(gamma_out, st->gamma, sizeof(double) * st->S, cudaMemcpyDeviceToHost, st->stream));
-        AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+        return take_status(st);  // synchronises
     }
     return AEM_OK;
 }
@@ -2042,7 +2171,7 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     if (rc) return rc;
     reweight_kernel<<<st->S, kGroupThreads, 0, s>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
                                                     st->d.alpha, st->d.bisect_iters, st->gamma, st->logz, st->Wg,
-                                                    st->dgamma, st->done);
+                                                    st->dgamma, st->done, st->d_status);
     AEM_CUDA_TRY(cudaGetLastError());
     resample_kernel<<<st->S, kGroupThreads, 0, s>>>(st->Wg, st->perm, st->off, st->counts, st->N, st->M, nullptr,
                                                     st->d.seed, 0, st->d_stage, st->C, st->anc);
@@ -2083,7 +2212,7 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     }
     set_flag_kernel<<<1, 32, 0, s>>>(st->d_have_prev, 1);
     AEM_CUDA_TRY(cudaGetLastError());
-    stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, h);
+    stage_cond_kernel<<<1, 32, 0, s>>>(st->gamma, st->S, st->d_stage, stop_stage, st->d_status, h);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -2152,7 +2281,7 @@ extern "C" int smc_run_graph(smc_state *st, int max_stages, int n_sweeps, int *s
     AEM_CUDA_TRY(cudaMemcpy(st->nprop_prev.data(), st->nprop, sizeof(int) * st->S * kMoves, cudaMemcpyDeviceToHost));
     st->have_prev = true;
     if (stages_out) *stages_out = s1 - s0;
-    return AEM_OK;
+    return take_status(st);
 }
 
 extern "C" int smc_model_odds(const smc_state *cst, double *post_k, double *log_bfipd, double *log_z_k) {
@@ -2160,33 +2289,31 @@ extern "C" int smc_model_odds(const smc_state *cst, double *post_k, double *log_
     if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_model_odds: NULL state");
     int rc = launch_group(st);
     if (rc) return rc;
-    std::vector<int> cnt(st->S * st->M);
-    AEM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), st->counts, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st->stream));
+    odds_kernel<<<blocks_for(st->S, 128), 128, 0, st->stream>>>(st->counts, st->S, st->M, st->d.lambda_max + 1, st->N,
+                                                                st->d_post, st->d_lbf);
+    AEM_CUDA_TRY(cudaGetLastError());
+    if (post_k)
+        AEM_CUDA_TRY(cudaMemcpyAsync(post_k, st->d_post, sizeof(double) * st->S * st->M, cudaMemcpyDeviceToHost,
+                                     st->stream));
+    if (log_bfipd)
+        AEM_CUDA_TRY(cudaMemcpyAsync(log_bfipd, st->d_lbf, sizeof(double) * st->S, cudaMemcpyDeviceToHost, st->stream));
     if (log_z_k)
         AEM_CUDA_TRY(cudaMemcpyAsync(log_z_k, st->logz, sizeof(double) * st->S * st->M, cudaMemcpyDeviceToHost,
                                      st->stream));
     AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
-    const int L1 = st->d.lambda_max + 1;
-    for (int s = 0; s < st->S; ++s) {
-        double n_ip = 0, n_non = 0;
-        for (int k = 0; k < st->M; ++k) {
-            double v = cnt[s * st->M + k];
-            if (post_k) post_k[s * st->M + k] = v / st->N;
-            if (k % L1 == 0)
-                n_non += v;
-            else
-                n_ip += v;
-        }
-        if (log_bfipd) {
-            // B = (|M_kappa| sum_IP pi/p) / (|M_lambda| sum_nonIP pi/p) with uniform p(k)
-            if (n_non == 0)
-                log_bfipd[s] = INFINITY;
-            else if (n_ip == 0 || st->d.lambda_max == 0)
-                log_bfipd[s] = -INFINITY;
-            else
-                log_bfipd[s] = std::log(n_ip / (st->d.lambda_max * n_non));
-        }
-    }
+    return AEM_OK;
+}
+
+extern "C" int smc_status(smc_state *st, int *status, int *nonfinite) {
+    if (!st) return fail(AEM_ERR_INVALID_ARG, "smc_status: NULL state");
+    if (nonfinite)
+        AEM_CUDA_TRY(cudaMemcpyAsync(nonfinite, st->nonfinite, sizeof(int) * st->S, cudaMemcpyDeviceToHost,
+                                     st->stream));
+    int v = 0;
+    AEM_CUDA_TRY(cudaMemcpyAsync(&v, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    AEM_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    if (v) AEM_CUDA_TRY(cudaMemsetAsync(st->d_status, 0, sizeof(int), st->stream));
+    if (status) *status = v;
     return AEM_OK;
 }
 
@@ -2291,7 +2418,7 @@ extern "C" int smc_ppd(smc_state *st, double *mean, double *var, double *z, floa
     if (!st->ppd_gates) {
         if ((rc = dalloc(st, &st->ppd_gates, P * G)) || (rc = dalloc(st, &st->ppd_out, 3 * S * G))) return rc;
     }
-    merge_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->P, st->LMS, st->m_nl, st->m_logsig,
+    merge_kernel<float><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->P, st->LMS, st->m_nl, st->m_logsig,
                                                                 st->m_logh, st->m_m, st->m_logtau, st->m_c);
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};

@@ -75,6 +75,20 @@ def truth_3layer():
     )
 
 
+def truth_marginal():
+    """Weakly chargeable sounding (the evidence for IP near even): the
+    three-layer earth of truth_3layer with its second layer 30 m thick from
+    50 m depth and chargeability m = 0.1 (tau = 1e-3 s, c = 0.5)."""
+    return dict(
+        nlayers=np.array([3], dtype=np.int8),
+        logsig=np.log10([[0.01, 0.1, 0.01]]),
+        logh=np.log10([[50.0, 30.0, 1.0]]),
+        m=np.array([[0.0, 0.1, 0.0]]),
+        logtau=np.full((1, 3), -3.0),
+        c=np.full((1, 3), 0.5),
+    )
+
+
 def truth_5layer():
     """Larger truth: sigma (0.01, 0.1, 0.003, 0.03, 0.01) S/m, h (15, 20, 30, 40) m,
     chargeable layers 2 and 4 with m (0.4, 0.2), tau 4.07e-4 s, c 1.0."""

@@ -131,6 +131,15 @@ class SMC:
         check(_lib.load().smc_run_graph(self._h, int(max_stages), int(n_sweeps), ctypes.byref(t)), "smc_run_graph")
         return t.value
 
+    def status(self):
+        """smc_status: (status, nonfinite [S]): the failure a reweight step
+        recorded since the last call (0 for none; cleared on read) and the per
+        sounding count of non-finite log-likelihoods set to -inf since init."""
+        v = ctypes.c_int()
+        nf = np.zeros(self.S, dtype=np.int32)
+        check(_lib.load().smc_status(self._h, ctypes.byref(v), nf.ctypes.data), "smc_status")
+        return v.value, nf
+
     def model_odds(self):
         post = np.zeros((self.S, self.M))
         lb = np.zeros(self.S)
