@@ -35,6 +35,13 @@ WORKLOAD = "forward-g30-f60-k200"
 P_PER_GPU = 1 << 20
 FLOPS_PER_LAYER_STEP = 60  # FP32 flops (FMA = 2) per layer-step of the recursion, counted from forward.cu
 MUFU_PER_LAYER_STEP = 6    # sqrt(|w|), rsqrt, rcp, ex2, sin, cos
+# the adjoint's FP32 flops per layer-step, counted from adjoint.cu: the
+# bottom-up recomputation of the reflection coefficients (60) and the
+# top-down reverse sweep (170: the wavenumber, interface coefficient and
+# propagation factor again, the Moebius step's partial derivatives, the
+# adjoint recursion and the per-layer accumulation)
+ADJ_FLOPS_PER_LAYER_STEP = 230
+ACCURACY_MODELS = 4096     # subset of the batch on which each variant's per-gate error is measured
 METRIC = "forward+loglik evals/s"
 UNIT = "evals/s"
 
@@ -49,11 +56,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rjsmc", action="store_true")
+    ap.add_argument("--no-flight-line", action="store_true",
+                    help="skip the 1000-sounding flight line (about 25 s) of the default run")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 form, gate-transform variants, bucketed order and adjoint measurements")
-    ap.add_argument("--rjsmc-only", nargs="?", const="fixed", choices=["fixed", "adaptive"],
-                    help="run only one RJSMC measurement, 128 x 256 (profiling): the fixed-scale moves, or the "
-                         "adaptive proposal with recycling and ZCA moves")
+    ap.add_argument("--rjsmc-only", nargs="?", const="fixed", choices=["fixed", "adaptive", "large", "fp64"],
+                    help="run only one RJSMC measurement (profiling): 128 x 256 with the fixed-scale moves or the "
+                         "adaptive proposal with recycling and ZCA moves; 4 x 4096 with kappa, lambda <= 9 and "
+                         "20 sweeps (large); 16 x 256 with the plain FP64 forward model (fp64)")
     ap.add_argument("--convergence-study", action="store_true",
                     help="fraction of soundings whose best particle reaches the truth's likelihood level, per "
                          "sampler setting (8 soundings of the 3-layer data, 2 seeds)")
@@ -123,14 +133,17 @@ def layer_steps(nlayers, F, K):
     return float(np.sum(nlayers.astype(np.int64))) * F * K
 
 
-def cpu_baseline(target_seconds=15.0):
+def cpu_baseline(accuracy_models, y_obs_np, target_seconds=15.0):
     """The FP64 oracle (adaptive-quadrature Hankel integrals), as it stands, on
-    a bounded sample of the workload on this host's cores."""
+    a bounded sample of the workload on this host's cores; the oracle with the
+    GPU's discretisation (K-point rule) on the accuracy subset of the batch,
+    whose gates and spectra are returned as the reference the variants' per-gate
+    errors are measured against; the serial oracle RJSMC of the single-sounding
+    configuration."""
     import oracle as O
     from paper_2109_00661_gb300 import inputs as I
     so = I.oracle_system(WORKLOAD)
     so["T"] = O.tmatrix(so["freqs"], so["times"])
-    y_obs = I.noisy(O.forward(I.truth_3layer(), so)[0], seed=0)
     cores = os.cpu_count() or 1
     n = 64
     done, elapsed = 0, 0.0
@@ -138,21 +151,20 @@ def cpu_baseline(target_seconds=15.0):
         models = I.random_models(n, seed=1000 + done)
         t0 = time.perf_counter()
         y = O.forward(models, so, nthreads=cores)
-        O.loglik(y, y_obs, I.EPS_AN, I.EPS_MN)
+        O.loglik(y, y_obs_np, I.EPS_AN, I.EPS_MN)
         elapsed += time.perf_counter() - t0
         done += n
         n = min(n * 2, 4096)
     # the same discretisation as the GPU (the K-point Hankel rule) in FP64 on
-    # the same cores: the fair CPU form of the forward model
-    n, done_r, el_r = 256, 0, 0.0
-    while el_r < target_seconds / 3:
-        models = I.random_models(n, seed=5000 + done_r)
-        t0 = time.perf_counter()
-        y = O.forward(models, so, mode=O.HANKEL_RULE, nthreads=cores)
-        O.loglik(y, y_obs, I.EPS_AN, I.EPS_MN)
-        el_r += time.perf_counter() - t0
-        done_r += n
-        n = min(n * 2, 16384)
+    # the same cores, on the accuracy subset (the models rounded to float32,
+    # as the FP32 path sees them): the fair CPU form of the forward model
+    m32 = {k: (np.asarray(v, dtype=np.float32).astype(np.float64) if k != "nlayers" else v)
+           for k, v in accuracy_models.items()}
+    t0 = time.perf_counter()
+    y_ref, imh_ref, absh = O.forward(m32, so, mode=O.HANKEL_RULE, nthreads=cores, want_imh=True, want_absh=True)
+    O.loglik(y_ref, y_obs_np, I.EPS_AN, I.EPS_MN)
+    el_r = time.perf_counter() - t0
+    done_r = len(m32["nlayers"])
     # the serial oracle RJSMC of the single-sounding configuration (N = 256,
     # kappa <= 3, lambda <= 4, 10 sweeps per stage): prior draw plus one stage,
     # extrapolated to the stage count the GPU sampler takes on it (30)
@@ -169,25 +181,81 @@ def cpu_baseline(target_seconds=15.0):
     t0 = time.perf_counter()
     R.run(st, lik, max_stages=1)
     t_stage = time.perf_counter() - t0 - t_init
-    return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} models of the {WORKLOAD} workload (adaptive-quadrature FP64 oracle, "
-                      f"{cores} threads), {elapsed:.1f} s",
-            "same_discretisation": {"value": done_r / el_r, "unit": UNIT, "cores": cores,
-                                    "sample": f"{done_r} models, FP64 oracle with the GPU's {WORKLOAD.split('-k')[-1]}"
-                                              f"-point Hankel rule, {el_r:.1f} s"},
-            "rjsmc": {"value": 1.0 / (t_init + 30 * t_stage), "unit": "soundings/s", "cores": cores,
-                      "sample": f"serial oracle RJSMC, 256 particles, kappa<=3, lambda<=4, 10 sweeps/stage: prior "
-                                f"draw {t_init:.2f} s + one stage {t_stage:.2f} s, extrapolated to 30 stages"}}
+    out = {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{done} models of the {WORKLOAD} workload (adaptive-quadrature FP64 oracle, "
+                     f"{cores} threads), {elapsed:.1f} s",
+           "same_discretisation": {"value": done_r / el_r, "unit": UNIT, "cores": cores,
+                                   "sample": f"the first {done_r} models of the batch, FP64 oracle with the GPU's "
+                                             f"{WORKLOAD.split('-k')[-1]}-point Hankel rule, {el_r:.2f} s"},
+           "rjsmc": {"value": 1.0 / (t_init + 30 * t_stage), "unit": "soundings/s", "cores": cores,
+                     "sample": f"serial oracle RJSMC, 256 particles, kappa<=3, lambda<=4, 10 sweeps/stage: prior "
+                               f"draw {t_init:.2f} s + one stage {t_stage:.2f} s, extrapolated to 30 stages"}}
+    return out, (y_ref, imh_ref, absh, so["T"])
+
+
+def gate_errors(gates, ref, floor):
+    """Per-gate error statistics of one variant against the oracle's gates on
+    the accuracy subset: e = |gpu - oracle| / max(|oracle|, eps_an); the
+    well-conditioned gates are those whose unavoidable FP32 rounding
+    kappa_g (F + 1) 2^-24 is below the floor."""
+    from paper_2109_00661_gb300 import inputs as I
+    y_ref, imh_ref, _, T = ref
+    den = np.maximum(np.abs(y_ref), I.EPS_AN)
+    e = np.abs(np.asarray(gates, dtype=np.float64) - y_ref) / den
+    kap = (np.abs(imh_ref) @ np.abs(T).T) / den
+    good = kap * (T.shape[1] + 1) * 2.0 ** -24 < floor
+    return {"max": float(e.max()), "median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+            "floor": floor, "frac_within_floor": float(np.mean(e <= floor)),
+            "well_conditioned_frac": float(good.mean()),
+            "well_conditioned_within_floor": float(np.mean(e[good] <= floor)),
+            "models": int(y_ref.shape[0])}
+
+
+def json_num(v):
+    """A float for the JSON line: +-inf as the strings "inf" / "-inf"."""
+    v = float(v)
+    return v if np.isfinite(v) else ("inf" if v > 0 else "-inf")
+
+
+def flight_line_measure(torch, L, I, n_soundings, rank=0, world=1, reduce=None):
+    """Cfg 5: the synthetic flight line (chargeable layer at 20..80 m, m 0..0.5),
+    2048 particles per sounding in one sampler per rank whose stage loop is one
+    captured CUDA graph; with several ranks each takes its contiguous block of
+    the line's soundings (shard_range).  Soundings/s of the whole job and the
+    unclipped log BFIPD at up to 20 evenly spaced soundings of this rank's block."""
+    from paper_2109_00661_gb300.shard import shard_range
+    truth, x = I.flight_line(n_soundings)
+    start, stop = shard_range(n_soundings, rank, world)
+    block = I.subset(truth, np.arange(start, stop))
+    out = rjsmc_measure(torch, L, I, stop - start, 2048, 3, 4, 10, block, graph=True, per_sounding=True,
+                        reduce=reduce, seed=rank, sounding_offset=start)
+    lbs = out.pop("log_bfipd_per_sounding")
+    step = max(1, (stop - start) // 20)
+    out["log_bfipd_along_line"] = {f"{x[start + i]:.3f}": json_num(round(float(lbs[i]), 2))
+                                   for i in range(0, stop - start, step)}
+    out["soundings_of_rank_0"] = [start, stop] if rank == 0 else None
+    return out
+
+
+def bfipd_summary(lb):
+    """Unclipped log BFIPD over soundings: the finite values' median and how
+    many soundings had every particle on one side (+-inf)."""
+    lb = np.asarray(lb, dtype=np.float64)
+    fin = np.isfinite(lb)
+    return {"median_finite": float(np.median(lb[fin])) if fin.any() else None, "n_finite": int(fin.sum()),
+            "n_all_chargeable": int(np.sum(lb == np.inf)), "n_none_chargeable": int(np.sum(lb == -np.inf))}
 
 
 def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, sweeps, truth, seed=0,
-                  reduce=None, n_langevin=0, graph=False, adaptive=None, per_sounding=False):
+                  reduce=None, n_langevin=0, graph=False, adaptive=None, per_sounding=False, precision=0,
+                  sounding_offset=0):
     """Whole RJSMC runs (prior draw, then reweight / resample / mutate until
     gamma = 1) for a batch of independent soundings on the sounding system
     (20 gates, 40 frequencies, 120 Hankel points); returns soundings/s.  With
     n_langevin > 0 every stage ends with that many adjoint-driven Langevin
     sweeps (adapted step); adaptive: smc_desc fields of the adaptive proposal
-    (fit and scale bisection, recycling window, ZCA mixture)."""
+    (fit and scale bisection, recycling window, ZCA mixture); precision 1:
+    the plain FP64 forward model in every evaluation."""
     from paper_2109_00661_gb300 import smc as S
     sysg = L.System(**I.system_kwargs("sounding-g20-f40-k120"))
     lms = kappa_max + lambda_max + 1
@@ -196,10 +264,10 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     y_true = L.forward_f32(sysg, I.to_torch(truth, torch.float32)).cpu().numpy().astype(np.float64)
     if y_true.shape[0] == 1:  # one truth for every sounding, independent noise draws
         y_true = np.repeat(y_true, n_soundings, axis=0)
-    y_obs = np.stack([I.noisy(y_true[s], seed=1000 + s) for s in range(n_soundings)])
+    y_obs = np.stack([I.noisy(y_true[s], seed=1000 + sounding_offset + s) for s in range(n_soundings)])
     sm = S.SMC(sysg, y_obs, I.EPS_AN, I.EPS_MN, n_particles=n_particles, n_soundings=n_soundings,
                kappa_max=kappa_max, lambda_max=lambda_max, seed=seed, r_max=sweeps, n_langevin=n_langevin,
-               **(adaptive or {}))
+               precision=precision, **(adaptive or {}))
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -226,13 +294,15 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
                      f"{sweeps} sweeps/stage" + (f" + {n_langevin} Langevin sweeps/stage" if n_langevin else "") +
                      (", stages in one CUDA graph with a device-side loop condition" if graph else "") +
                      (", adaptive proposal " + ", ".join(f"{k}={v}" for k, v in adaptive.items()) if adaptive else "") +
+                     (", plain FP64 forward model" if precision else "") +
                      ", alpha=0.5, sounding system G=20 F=40 K=120",
-           "median_log_bfipd": float(np.median(np.clip(lb, -50, 50))),
+           "log_bfipd": bfipd_summary(lb),
+           "p_ip_per_model_mean": post.mean(axis=0).round(4).tolist(),
            "forward_launch_shape": shape,
            "langevin": lang,
            "mean_p_ip": float(np.mean(post.reshape(n_soundings, kappa_max + 1, lambda_max + 1)[:, :, 1:].sum(axis=(1, 2))))}
-    if per_sounding:  # clipped at +-50 (every particle on one side)
-        out["log_bfipd"] = np.clip(lb, -50, 50).tolist()
+    if per_sounding:  # unclipped; +-inf where every particle sits on one side
+        out["log_bfipd_per_sounding"] = lb.tolist()
     sm.close()
     sysg.close()
     return out
@@ -249,7 +319,7 @@ def combine_runs(runs):
     out.update(value=sum(r["value"] * r["seconds"] for r in runs) / sec, seconds=sec, stages=stages,
                ms_per_stage=sec / sum(stages) * 1e3, seeds=len(runs),
                forward_evals_per_s=sum(r["forward_evals_per_s"] * r["seconds"] for r in runs) / sec,
-               median_log_bfipd=float(np.median([r["median_log_bfipd"] for r in runs])),
+               log_bfipd=[r["log_bfipd"] for r in runs],
                mean_p_ip=float(np.mean([r["mean_p_ip"] for r in runs])))
     if runs[0]["langevin"]:
         out["langevin"] = dict(runs[-1]["langevin"],
@@ -389,29 +459,32 @@ def main():
         print(json.dumps({"detectability": detectability_study(torch, L, I)}), flush=True)
         return
     if args.flight_line:
-        truth, x = I.flight_line(args.flight_line)
-        # all soundings in one sampler, its stage loop one captured CUDA graph
-        out = rjsmc_measure(torch, L, I, args.flight_line, 2048, 3, 4, 10, truth, graph=True, per_sounding=True)
-        # the section's IP odds along the line, at 20 evenly spaced soundings
-        lbs = out.pop("log_bfipd")
-        step = max(1, args.flight_line // 20)
-        out["log_bfipd_along_line"] = {f"{x[i]:.3f}": round(float(lbs[i]), 2) for i in range(0, args.flight_line, step)}
-        print(json.dumps({"flight_line": out}), flush=True)
+        print(json.dumps({"flight_line": flight_line_measure(torch, L, I, args.flight_line)}), flush=True)
         return
     if args.convergence_study:
         print(json.dumps({"convergence_study": convergence_study(torch, L, I)}), flush=True)
         return
     if args.rjsmc_only:
-        ad = dict(adaptive=1, recycle_stages=3, zca=0.5) if args.rjsmc_only == "adaptive" else None
-        print(json.dumps({"rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), adaptive=ad)}),
-              flush=True)
+        if args.rjsmc_only == "large":
+            out = rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer())
+        elif args.rjsmc_only == "fp64":
+            out = rjsmc_measure(torch, L, I, 16, 256, 3, 4, 10, I.truth_3layer(), precision=1)
+        else:
+            ad = dict(adaptive=1, recycle_stages=3, zca=0.5) if args.rjsmc_only == "adaptive" else None
+            out = rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), adaptive=ad)
+        print(json.dumps({"rjsmc": out}), flush=True)
         return
     sysg = L.System(**I.system_kwargs(WORKLOAD))
     F, K, G = sysg.F, sysg.K, sysg.G
     P = args.models
     models_np = I.random_models(P, seed=rank)
     models = I.to_torch(models_np, torch.float32)
-    y_obs = torch.as_tensor(I.noisy(np.full(G, 1e-11), seed=0), dtype=torch.float64, device="cuda")
+    # the data every model is scored against: the single-sounding truth (three
+    # layers, chargeable second layer) through the FP64 forward model on this
+    # system's 30 gates, with 3 % + 1e-13 T/s noise
+    y_true = L.forward_f64(sysg, I.to_torch(I.truth_3layer(), torch.float64)).cpu().numpy()[0]
+    y_obs_np = I.noisy(y_true, seed=0)
+    y_obs = torch.as_tensor(y_obs_np, dtype=torch.float64, device="cuda")
     eps_an = torch.full((G,), I.EPS_AN, dtype=torch.float64, device="cuda")
     ll = torch.empty(P, dtype=torch.float64, device="cuda")
     steps_work = layer_steps(models_np["nlayers"], F, K)
@@ -569,8 +642,16 @@ def main():
         a1.record(stream)
         torch.cuda.synchronize()
         ams = a0.elapsed_time(a1) / args.steps
+        a_steps = layer_steps(models_np["nlayers"][:na], F, K)
+        a_ach = a_steps * ADJ_FLOPS_PER_LAYER_STEP / (ams * 1e-3) / 1e12
+        a_peak = 2.0 * peaks["fp32_fma_per_s"] / 1e12
         adjoint = {"value": na / (ams * 1e-3), "unit": "gradient evals/s", "models": na, "ms_per_launch": ams,
                    "dtype": "f32", "relative_cost_vs_loglik": (ams / na) / (ms / P),
+                   "roofline": {"bound": "alu", "achieved": a_ach, "peak": a_peak, "unit": "TFLOP/s",
+                                "frac": a_ach / a_peak, "flops_per_layer_step": ADJ_FLOPS_PER_LAYER_STEP,
+                                "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",
+                                "note": "the launch includes the forward kernel's pass for the gates "
+                                        "(60 flops per layer-step, not counted in the adjoint's figure)"},
                    "config": f"{WORKLOAD}: {na} random models, 1..10 layers, 5 parameters per layer"}
 
     # RJSMC soundings/s: the single-sounding configuration (N = 256, kappa <= 3,
@@ -592,18 +673,49 @@ def main():
         # the 4-sounding configurations run three seeds each: their stage
         # counts vary more from one sampler path to another
         seeds = [rank + world * i for i in range(3)]
-        rjsmc = (rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
-                 combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
-                                             reduce=reduce) for sd in seeds]),
-                 combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
-                                             reduce=reduce, n_langevin=2) for sd in seeds]),
-                 rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
-                               graph=True),
-                 # Section 3.2's adaptive within-model proposal with particle
-                 # recycling over 3 stages and Appendix F's ZCA-coloured
-                 # birth / death in half the trans-dimensional moves
-                 rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce,
-                               adaptive=dict(adaptive=1, recycle_stages=3, zca=0.5)))
+        rjsmc = {
+            "rjsmc": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank, reduce=reduce),
+            # the same single-sounding configuration with the plain FP64 forward
+            # model in every evaluation (Algorithm 1 unchanged), on 16 soundings
+            "rjsmc_fp64": rjsmc_measure(torch, L, I, 16, 256, 3, 4, 10, I.truth_3layer(), seed=rank,
+                                        reduce=reduce, precision=1),
+            "rjsmc_large": combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
+                                                       reduce=reduce) for sd in seeds]),
+            "rjsmc_langevin": combine_runs([rjsmc_measure(torch, L, I, 4, 4096, 9, 9, 20, I.truth_5layer(), seed=sd,
+                                                          reduce=reduce, n_langevin=2) for sd in seeds]),
+            "rjsmc_graph": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank,
+                                         reduce=reduce, graph=True),
+            # Section 3.2's adaptive within-model proposal with particle
+            # recycling over 3 stages and Appendix F's ZCA-coloured birth /
+            # death in half the trans-dimensional moves
+            "rjsmc_adaptive": rjsmc_measure(torch, L, I, 128, 256, 3, 4, 10, I.truth_3layer(), seed=rank,
+                                            reduce=reduce, adaptive=dict(adaptive=1, recycle_stages=3, zca=0.5)),
+        }
+        if not args.no_flight_line:
+            # the 1000-sounding flight line in one graph-captured sampler (per rank: its block of soundings)
+            rjsmc["flight_line"] = flight_line_measure(torch, L, I, 1000, rank, world, reduce)
+
+    # per-gate error of every variant against the oracle on the first
+    # ACCURACY_MODELS models of the batch (outside every timed region; the
+    # oracle's reference comes from the cpu_baseline leg)
+    base = None
+    accuracy = None
+    if rank == 0 and not args.no_cpu_baseline:
+        na_ = min(ACCURACY_MODELS, P)
+        # the subset rounded to float32 once: every variant and the oracle see the same inputs
+        sub = {k: (np.asarray(v, dtype=np.float32).astype(np.float64) if k != "nlayers" else v)
+               for k, v in I.subset(models_np, np.arange(na_)).items()}
+        base, ref = cpu_baseline(sub, y_obs_np)
+        if not args.no_variants:
+            ms32 = I.to_torch(sub, torch.float32)
+            accuracy = {"fp64_plain": gate_errors(
+                            L.forward_f64(sysg, I.to_torch(sub, torch.float64)).cpu().numpy(), ref, 1e-4),
+                        "fp32": gate_errors(L.forward_f32(sysg, ms32).cpu().numpy(), ref, 1e-4)}
+            for name, mode, floor in (("fp32_separate_transform", L.GATES_FP32, 1e-4),
+                                      ("tf32_split", L.GATES_TF32_SPLIT, 1e-4),
+                                      ("bf16_split", L.GATES_BF16_SPLIT, 1e-3)):
+                _, g_ = L.loglik_f32_tc(sysg, ms32, y_obs, eps_an, I.EPS_MN, mode, want_gates=True)
+                accuracy[name] = gate_errors(g_.cpu().numpy(), ref, floor)
 
     if rank == 0:
         flops = steps_work * FLOPS_PER_LAYER_STEP
@@ -645,14 +757,15 @@ def main():
         if fp64 is not None:
             line["fp64_plain"] = fp64
         if rjsmc is not None:
-            (line["rjsmc"], line["rjsmc_large"], line["rjsmc_langevin"], line["rjsmc_graph"],
-             line["rjsmc_adaptive"]) = rjsmc
+            line.update(rjsmc)
         if adjoint is not None:
             line["adjoint"] = adjoint
         if transforms is not None:
             line["gate_transform_variants"] = transforms
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+        if accuracy is not None:
+            line["accuracy_vs_oracle"] = accuracy
+        if base is not None:
+            line["cpu_baseline"] = base
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

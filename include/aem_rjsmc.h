@@ -133,7 +133,10 @@ int aem_forward_f64(const aem_system *sys, const aem_models_f64 *models, double 
 /* Gaussian log-likelihood (Section 2.3.2):
  *   ll_p = -1/2 sum_g [ (y_g - yhat_g)^2 / v_g + ln(2 pi v_g) ],
  *   v_g = eps_an[g]^2 + (eps_mn * yhat_g)^2   (variance from the model prediction).
- * y_obs, eps_an: [device] G doubles.  ll: [device] P doubles, summed in FP64.
+ * y_obs, eps_an: [device] G doubles.  ll: [device] P doubles, summed in FP64;
+ * the f32 entry forms each term in FP32 (the residual y_g - yhat_g from an FP64
+ * difference), so eps_an^2 must be a normal float (eps_an >= 1e-18), the f64
+ * entry in FP64.  A NaN parameter gives NaN for that model only.
  * gates: optional [device] P*G copy of the predictions (may be NULL). */
 int aem_loglik_f32(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                    const double *eps_an, double eps_mn, double *ll, float *gates, void *stream);
@@ -509,12 +512,19 @@ int smc_restore(smc_state *st, const void *buf, size_t size);
 size_t aem_smc_workspace_bytes(int n, int n_models);
 /* ll [n], model [n] (0..n_models-1): outputs dgamma [1], reached_one [1],
  * logz_inc [n_models] (0 for empty models) and W [n] normalised within each
- * model, for the step from gamma_prev. */
+ * model, for the step from gamma_prev.  A particle whose model id is outside
+ * [0, n_models) takes no part (its W is 0).  ll must not hold NaN (the
+ * sampler maps NaN to -inf before its reweight step); particles at -inf get
+ * weight 0, and when no probed step keeps TESS >= alpha N the smallest probed
+ * step, (1 - gamma_prev) 2^-bisect_iters, is returned (the sampler reports
+ * that case as AEM_ERR_NO_BRACKET, see smc_status). */
 int aem_reweight(const double *ll, const int *model, int n, int n_models, double gamma_prev, double alpha,
                  int bisect_iters, double *dgamma, int *reached_one, double *logz_inc, double *W, void *work,
                  size_t work_bytes, void *stream);
 /* W [n] normalised within each model, model [n], u40 [n_models] integers in
- * [0, 2^40): ancestor [n] of every particle (bit-exact integer arithmetic). */
+ * [0, 2^40): ancestor [n] of every particle (bit-exact integer arithmetic).
+ * A particle whose model id is outside [0, n_models) takes no part: its
+ * ancestor is -1 and it is never chosen as one. */
 int aem_resample_systematic(const double *W, const int *model, int n, int n_models, const unsigned long long *u40,
                             int *ancestor, void *work, size_t work_bytes, void *stream);
 /* Resampling without any allocation.  The paper has no counterpart: this is

@@ -9,7 +9,8 @@
 // reduces over the abscissae of a frequency with a segmented warp sum into
 // shared memory.  The epilogue applies the G x F step-off transform and, for
 // the likelihood entry points, the Gaussian log-likelihood of Section 2.3.2
-// with its sum in double precision.
+// (FP32 terms with an FP64 sum in the FP32 kernel, FP64 throughout in the
+// FP64 one).
 //
 // Recursion used (quasi-static TE mode, exp(+i w t)):
 //   u_n = sqrt(lambda^2 + s_n), Re u_n > 0
@@ -363,6 +364,8 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
 // The Moebius step (N, D) <- (r D + N E, D + r N E) keeps R_0 = N / D.
 using namespace f32x2;  // paired FP32 helpers and the hardware approximations (f32x2.h)
 
+constexpr double kLn2Pi = 1.83787706640934548356;  // ln(2 pi)
+
 // w for both abscissae; sxx = (Re s, Re s), yyy = (Im s ^2, ...), syy = (Im s, Im s)
 __device__ __forceinline__ C2x2 wroot2(u64 lam2, u64 sxx, u64 yyy, u64 syy) {
     const u64 x = add2(lam2, sxx);
@@ -704,12 +707,14 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             for (int j = 0; j < F; ++j) acc = fmaf(Ts[tid * F + j], imh[j], acc);
             if (gates_out) gates_out[(size_t)p * G + tid] = acc;
             if (ll_out) {
-                const double yh = (double)acc;
-                const double ea = eps_an[tid];
-                const double v = ea * ea + (eps_mn * yh) * (eps_mn * yh);
                 const double *yo = y_obs + (obs_per > 0 ? (size_t)(p / obs_per) * G : 0);
-                const double rr = yo[tid] - yh;
-                term = rr * rr / v + log(2.0 * kPi * v);
+                // FP32 terms (the residual from an FP64 difference, the
+                // variance, one division and one logarithm), FP64 sum: FP64
+                // terms cost this serial epilogue 1 % of the whole launch
+                const float r = (float)(yo[tid] - (double)acc);
+                const float ea = (float)eps_an[tid], q = (float)eps_mn * acc;
+                const float v = fmaf(q, q, ea * ea);
+                term = (double)(__fdiv_rn(r * r, v) + logf(v)) + kLn2Pi;
             }
         }
         if (imh_out)

@@ -240,6 +240,60 @@ __device__ __forceinline__ void stage_chunk(const float *__restrict__ src, int F
     *reinterpret_cast<uint4 *>(lo_row) = *reinterpret_cast<const uint4 *>(l);
 }
 
+// Register prefetch of a tile's spectra: thread tid owns chunks
+// c = tid + j kThreads (j < NKC), each chunk KC / 4 float4 loads; a tile needs
+// NKC KC / 4 <= kPF of them per thread (F <= 64 for both splits) and F a
+// multiple of 4 (16-byte rows).  The next tile's loads are issued before the
+// current tile's MMA wait and epilogue, so their latency overlaps both.
+constexpr int kPF = 16;
+
+template <int KIND>
+struct TilePrefetch {
+    static constexpr int KC = 16 / Split<KIND>::ES;  // elements per core-matrix row
+    static constexpr int Q = KC / 4;                 // float4 loads per chunk
+    float4 v[kPF];
+
+    __device__ __forceinline__ void load(const float *__restrict__ imh, int P, int F, int NKC, size_t row0, int tid) {
+#pragma unroll
+        for (int q = 0; q < kPF; ++q) {
+            const int j = q / Q, part = q - (q / Q) * Q;
+            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < NKC) {
+                const int c = tid + j * kThreads;
+                const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
+                const size_t m = row0 + r;
+                const int k0 = kc * KC + part * 4;
+                if (m < (size_t)P && k0 < F) v[q] = __ldg(reinterpret_cast<const float4 *>(imh + m * F + k0));
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store(int NKC, uint32_t sbo, int tid, unsigned char *hi, unsigned char *lo) const {
+        using S = Split<KIND>;
+#pragma unroll
+        for (int j = 0; j < kPF / Q; ++j) {
+            if (j < NKC) {
+                const int c = tid + j * kThreads;
+                const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
+                const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
+                float x[KC];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    x[4 * q] = v[j * Q + q].x;
+                    x[4 * q + 1] = v[j * Q + q].y;
+                    x[4 * q + 2] = v[j * Q + q].z;
+                    x[4 * q + 3] = v[j * Q + q].w;
+                }
+                typename S::T h[KC], l[KC];
+#pragma unroll
+                for (int q = 0; q < KC; ++q) S::run(x[q], h[q], l[q]);
+                *reinterpret_cast<uint4 *>(hi + o) = *reinterpret_cast<const uint4 *>(h);
+                *reinterpret_cast<uint4 *>(lo + o) = *reinterpret_cast<const uint4 *>(l);
+            }
+        }
+    }
+};
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     using S = Split<KIND>;
@@ -288,6 +342,9 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     uint32_t phase = 0;
     bool pending = false;  // an MMA chain committed and not yet observed complete
     bool first = true;
+    const bool pf_ok = vec4 && NKC * TilePrefetch<KIND>::Q <= kPF;
+    TilePrefetch<KIND> pf;
+    if (pf_ok && (int)blockIdx.x < ntiles) pf.load(a.imh, a.P, a.F, NKC, (size_t)blockIdx.x * kTM, tid);
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const size_t row0 = (size_t)tile * kTM;
@@ -305,11 +362,15 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
             }
         // stage the tile's spectra (rows past P and columns past F are zero);
         // consecutive lanes fill consecutive 16-byte rows of one core matrix
-        for (int c = tid; c < kTM * NKC; c += kThreads) {
-            const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
-            const size_t m = row0 + r;
-            const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
-            stage_chunk<KIND>(m < (size_t)a.P ? a.imh + m * a.F : nullptr, a.F, kc, vec4, Ahi + o, Alo + o);
+        if (pf_ok) {
+            pf.store(NKC, sbo, tid, Ahi, Alo);
+        } else {
+            for (int c = tid; c < kTM * NKC; c += kThreads) {
+                const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
+                const size_t m = row0 + r;
+                const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
+                stage_chunk<KIND>(m < (size_t)a.P ? a.imh + m * a.F : nullptr, a.F, kc, vec4, Ahi + o, Alo + o);
+            }
         }
         fence_async_smem();
         tc_before_sync();
@@ -329,6 +390,9 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
         }
         first = false;
         pending = issue;
+        // the next tile's loads go out while the MMA runs and the epilogue reads it
+        if (pf_ok && tile + (int)gridDim.x < ntiles)
+            pf.load(a.imh, a.P, a.F, NKC, (size_t)(tile + gridDim.x) * kTM, tid);
         const bool done = mbar_wait_bounded(mbar, phase, a.spins);
         if (!done) atomicExch(abort_p, 1);
         __syncthreads();
@@ -433,9 +497,27 @@ int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode
                         sizeof(float) * AEM_MAX_GATES + 64;
     auto kern = tf32 ? gates_tc_kernel<0> : gates_tc_kernel<1>;
     AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // all of the SM's unified storage to shared memory, so that several CTAs
+    // (two for the TF32 split's 84 KB, five for the BF16 split's 43 KB) stay resident
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) return fail(AEM_ERR_UNSUPPORTED, "aem_gates_from_spectrum: tile does not fit in shared memory");
+    // the occupancy query has reported one CTA per SM for the TF32 tile where
+    // two fit (the profiler's shared-memory limit says two); take the count
+    // the SM's shared memory allows when it is larger (registers allow four,
+    // warps sixteen, the tensor memory 512 / ncols)
+    {
+        int smem_sm = 0, reserved = 0;
+        AEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sys->device));
+        AEM_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, sys->device));
+        int by_smem = smem_sm / (int)(smem + (size_t)reserved);
+        const int by_tmem = 512 / a.ncols;
+        if (by_smem > by_tmem) by_smem = by_tmem;
+        if (by_smem > 4) by_smem = 4;
+        if (by_smem > per_sm) per_sm = by_smem;
+    }
     const int ntiles = (P + kTM - 1) / kTM;
     int grid = sys->num_sms * per_sm;
     if (grid > ntiles) grid = ntiles;

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kGroupThreads)
         __syncthreads();
         return s_tess;
     };
-    const double target = alpha * (double)N;
+    const double target = alpha * (double)o[M];  // N, less any particle the grouping left out
     double hi = 1.0 - g0, dg;
     int done;
     if (evaluate(hi) >= target) {
@@ -1547,22 +1547,31 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 
 // Model ids from a plain int array (the standalone reweight / resample entry
 // points take the model of each particle directly).
-__global__ void split_model_kernel(const int *model, int n, int lp1, int *kappa, int *lam) {
+// Model ids of the standalone a7 / a8 entries.  An id outside [0, n_models)
+// takes no part: it is given a group key no model has (255 > AEM_SMC_MAX_MODELS),
+// and its ancestor (resample) or weight (reweight) output is set to -1 / 0.
+__global__ void split_model_kernel(const int *model, int n, int n_models, int *kappa, int *lam, int *anc_out,
+                                   double *w_out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        kappa[i] = model[i] / lp1;
-        lam[i] = model[i] - (model[i] / lp1) * lp1;
-    }
+    if (i >= n) return;
+    const int id = model[i];
+    const bool ok = id >= 0 && id < n_models;
+    kappa[i] = ok ? id : 255;
+    lam[i] = 0;
+    if (!ok && anc_out) anc_out[i] = -1;
+    if (!ok && w_out) w_out[i] = 0.0;
 }
 
-__global__ void scatter_kernel(const double *Wg, const int *perm, int n, double *W) {
+// perm lists the grouped particles only (off[M] of them, fewer than n when
+// some ids were out of range)
+__global__ void scatter_kernel(const double *Wg, const int *perm, const int *off, int M, double *W) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) W[perm[i]] = Wg[i];
+    if (i < off[M]) W[perm[i]] = Wg[i];
 }
 
-__global__ void gather_weights_kernel(const double *W, const int *perm, int n, double *Wg) {
+__global__ void gather_weights_kernel(const double *W, const int *perm, const int *off, int M, double *Wg) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) Wg[i] = W[perm[i]];
+    if (i < off[M]) Wg[i] = W[perm[i]];
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -2724,13 +2733,13 @@ extern "C" int aem_reweight(const double *ll, const int *model, int n, int n_mod
         return fail(AEM_ERR_INVALID_ARG, "aem_reweight: NULL pointer or value out of range");
     cudaStream_t s = (cudaStream_t)stream;
     Workspace w = carve(work, n, n_models);
-    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, 1, w.kappa, w.lam);
+    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, n_models, w.kappa, w.lam, nullptr, W);
     group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
     AEM_CUDA_TRY(cudaMemcpyAsync(w.gamma, &gamma_prev, sizeof(double), cudaMemcpyHostToDevice, s));
     AEM_CUDA_TRY(cudaMemsetAsync(logz_inc, 0, sizeof(double) * n_models, s));
     reweight_kernel<<<1, kGroupThreads, 0, s>>>(ll, w.perm, w.off, w.counts, n, n_models, alpha, bisect_iters,
                                                 w.gamma, logz_inc, w.Wg, dgamma, reached_one);
-    scatter_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.Wg, w.perm, n, W);
+    scatter_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.Wg, w.perm, w.off, n_models, W);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -2743,9 +2752,9 @@ extern "C" int aem_resample_systematic(const double *W, const int *model, int n,
     if (!W || !model || !u40 || !ancestor) return fail(AEM_ERR_INVALID_ARG, "aem_resample_systematic: NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     Workspace w = carve(work, n, n_models);
-    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, 1, w.kappa, w.lam);
+    split_model_kernel<<<blocks_for(n, 256), 256, 0, s>>>(model, n, n_models, w.kappa, w.lam, ancestor, nullptr);
     group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
-    gather_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(W, w.perm, n, w.Wg);
+    gather_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(W, w.perm, w.off, n_models, w.Wg);
     resample_kernel<<<1, kGroupThreads, 0, s>>>(w.Wg, w.perm, w.off, w.counts, n, n_models, u40, 0ull, 0, nullptr,
                                                 w.C, ancestor);
     AEM_CUDA_TRY(cudaGetLastError());

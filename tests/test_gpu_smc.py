@@ -99,6 +99,40 @@ def test_resample_bit_exact(torch, S, case):
     assert np.array_equal(got.cpu().numpy(), ref)
 
 
+def test_out_of_range_model_ids_take_no_part(torch, S):
+    """Standalone a7 / a8 with model ids outside [0, n_models) (negative, just
+    past the range, past 255): those particles get ancestor -1 and weight 0,
+    and the others are resampled exactly as without them."""
+    rng = np.random.default_rng(9)
+    N, K = 500, 7
+    model = rng.integers(0, K, N)
+    bad = rng.choice(N, 40, replace=False)
+    model[bad[:10]] = -1
+    model[bad[10:20]] = K
+    model[bad[20:30]] = 300
+    model[bad[30:]] = 256 + 3  # would alias model 3 in an 8-bit key
+    good = np.ones(N, bool)
+    good[bad] = False
+    W = np.zeros(N)
+    for k in range(K):
+        idx = np.nonzero((model == k) & good)[0]
+        w = rng.exponential(1.0, idx.size)
+        W[idx] = w / w.sum()
+    u40 = rng.integers(0, 1 << 40, K, dtype=np.uint64)
+    mt = torch.as_tensor(model.astype(np.int32), device="cuda")
+    got = S.resample_systematic(torch.as_tensor(W, device="cuda"), mt, K,
+                                torch.as_tensor(u40.astype(np.int64), device="cuda")).cpu().numpy()
+    keep = np.nonzero(good)[0]
+    ref = R.resample_systematic(W[keep], model[keep], K, u40)
+    assert np.all(got[bad] == -1)
+    assert np.array_equal(got[keep], keep[ref])
+    ll = rng.normal(-30.0, 5.0, N)
+    _, _, _, Wr = S.reweight(torch.as_tensor(ll, device="cuda"), mt, K, 0.2, 0.5)
+    _, _, _, W_ref = R.reweight(ll[keep], model[keep], K, 0.2, 0.5)
+    Wr = Wr.cpu().numpy()
+    assert np.all(Wr[bad] == 0.0) and np.allclose(Wr[keep], W_ref, rtol=1e-8, atol=1e-14)
+
+
 def settings(**kw):
     base = dict(n_particles=128, kappa_max=3, lambda_max=4, n_sweeps=10, seed=11)
     base.update(kw)
