@@ -516,14 +516,30 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
     out1 = n1 * rcp_approx(d1);
 }
 
+// The per-item value buffer: kValsWords floats (24 KB), the same for every
+// launch shape, so that the Hankel sums come out identical whatever the
+// shape, the scheduling or the row stride (lmax) of the models.
+constexpr int kValsWords = 6144;
+static_assert(kValsWords % 512 == 0, "rounds must end on a multiple of every launch shape's thread count");
+
+// Words (floats) of the forward kernel's value region: the value buffer, or
+// the prologue's stmp[F*LS] (float2) that shares it, whichever is larger.
+__host__ __device__ inline size_t value_words(int F, int LS) {
+    const size_t st = (size_t)2 * F * LS;
+    return st > (size_t)kValsWords ? st : (size_t)kValsWords;
+}
+
 // Shared memory (dynamic), in order: RS[F*LS], RB[F*LS], RC[F*LS], RAB[F],
-// RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), stmp[F*LS], hwp[K2] (float2),
-// imh_w[NW*F], imh[F], T[G*F] (float).
-// NT threads per CTA; MINB resident CTAs per SM the register allocation must
-// allow; DYN: models are handed out by a global counter (each CTA takes the
-// next unclaimed model when it finishes one) instead of the fixed grid stride,
-// which evens out CTAs that draw many deep models (the launch shapes the
-// autotuner chooses between).
+// RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), hwp[K2] (float2), the value
+// region (value_words floats), imh[F], T[G*F] (float).  The items (frequency
+// major, F*K2 of them) are taken in rounds of kValsWords: every item stores
+// its weighted pair value at its own index in the buffer; after the round
+// each frequency the round touched is summed by one warp (lane l takes the
+// round's values k = l, l + 32, ... of that frequency, then a warp tree) and
+// added to imh[f], rounds in order.  The order of every sum is fixed by the
+// item indices alone.  (The throughput system's 60 x 100 items take one
+// round.)  Before the item loop the value region holds the prologue's
+// stmp[F*LS] (float2).
 template <int NT, int MINB, bool DYN>
 __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Ops> mv, int F, int G, int K,
                                                                int cc_form, int LS,
@@ -549,10 +565,10 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     ulonglong2 *RAC = RAB + F;
     ulonglong2 *lamp = RAC + F;
     u64 *RY = reinterpret_cast<u64 *>(lamp + K2);
-    float2 *stmp = reinterpret_cast<float2 *>(RY + (size_t)F * LS);
-    float2 *hwp = stmp + (size_t)F * LS;
-    float *imh_w = reinterpret_cast<float *>(hwp + K2);
-    float *imh = imh_w + (size_t)NW * F;
+    float2 *hwp = reinterpret_cast<float2 *>(RY + (size_t)F * LS);
+    float *vals = reinterpret_cast<float *>(hwp + K2);
+    float2 *stmp = reinterpret_cast<float2 *>(vals);  // prologue only: the item loop overwrites it
+    float *imh = vals + value_words(F, LS);
     float *Ts = imh + F;
     __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
     __shared__ float lsig[AEM_MAX_LAYERS], lm[AEM_MAX_LAYERS], ltau[AEM_MAX_LAYERS], lc[AEM_MAX_LAYERS];
@@ -586,7 +602,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             ltau[tid] = exp10f(mv.logtau[o]);
             lc[tid] = mv.c[o];
         }
-        for (int i = tid; i < NW * F; i += blockDim.x) imh_w[i] = 0.f;
+        for (int j = tid; j < F; j += blockDim.x) imh[j] = 0.f;
         __syncthreads();
         // Cole-Cole per (frequency, layer): x = (w tau)^c e^{i pi c / 2}, s = i w mu0 sigma
         for (int i = tid; i < F * L; i += blockDim.x) {
@@ -647,59 +663,51 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         __syncthreads();
 
         int f = tid / K2, k = tid - (tid / K2) * K2;
-        // the item loop, specialised on the model's layer count up to 10
-        auto items = [&](auto lt) {
-            constexpr int LT = decltype(lt)::value;
-            for (int base = 0; base < FK2; base += blockDim.x) {
-                const int item = base + tid;
-                float val = 0.f;
-                int fl = -1;
-                if (item < FK2) {
-                    fl = f;
+        // the item loop, specialised on the model's layer count up to 10, in
+        // rounds of kValsWords items
+        for (int r0 = 0; r0 < FK2; r0 += kValsWords) {
+            const int r1 = r0 + kValsWords < FK2 ? r0 + kValsWords : FK2;
+            auto items = [&](auto lt) {
+                constexpr int LT = decltype(lt)::value;
+                for (int item = r0 + tid; item < r1; item += blockDim.x) {
                     const ulonglong2 lw = lamp[k];
-                    float r0, r1;
+                    float v0, v1;
                     const size_t o = (size_t)f * LS;
-                    im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, r0, r1);
+                    im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, v0, v1);
                     const float2 hw = hwp[k];
-                    val = fmaf(hw.x, r0, hw.y * r1);
+                    vals[item - r0] = fmaf(hw.x, v0, hw.y * v1);
+                    k += blockDim.x;
+                    while (k >= K2) {
+                        k -= K2;
+                        ++f;
+                    }
                 }
-                // segmented warp reduction over lanes that share a frequency
-                unsigned pending = __ballot_sync(kFull, fl >= 0);
-                while (pending) {
-                    const int leader = __ffs(pending) - 1;
-                    const int fsel = __shfl_sync(kFull, fl, leader);
-                    const float part = warp_sum<float>(fl == fsel ? val : 0.f);
-                    if (lane == leader) imh_w[warp * F + fsel] += part;
-                    pending &= ~__ballot_sync(kFull, fl == fsel);
-                }
-                k += blockDim.x;
-                while (k >= K2) {
-                    k -= K2;
-                    ++f;
-                }
+            };
+            switch (L) {
+                case 1: items(std::integral_constant<int, 1>{}); break;
+                case 2: items(std::integral_constant<int, 2>{}); break;
+                case 3: items(std::integral_constant<int, 3>{}); break;
+                case 4: items(std::integral_constant<int, 4>{}); break;
+                case 5: items(std::integral_constant<int, 5>{}); break;
+                case 6: items(std::integral_constant<int, 6>{}); break;
+                case 7: items(std::integral_constant<int, 7>{}); break;
+                case 8: items(std::integral_constant<int, 8>{}); break;
+                case 9: items(std::integral_constant<int, 9>{}); break;
+                case 10: items(std::integral_constant<int, 10>{}); break;
+                default: items(std::integral_constant<int, 0>{}); break;
             }
-        };
-        switch (L) {
-            case 1: items(std::integral_constant<int, 1>{}); break;
-            case 2: items(std::integral_constant<int, 2>{}); break;
-            case 3: items(std::integral_constant<int, 3>{}); break;
-            case 4: items(std::integral_constant<int, 4>{}); break;
-            case 5: items(std::integral_constant<int, 5>{}); break;
-            case 6: items(std::integral_constant<int, 6>{}); break;
-            case 7: items(std::integral_constant<int, 7>{}); break;
-            case 8: items(std::integral_constant<int, 8>{}); break;
-            case 9: items(std::integral_constant<int, 9>{}); break;
-            case 10: items(std::integral_constant<int, 10>{}); break;
-            default: items(std::integral_constant<int, 0>{}); break;
+            __syncthreads();
+            // the round's share of each frequency's Hankel sum, in a fixed order
+            const int fa = r0 / K2, fb = (r1 - 1) / K2;
+            for (int j = fa + warp; j <= fb; j += NW) {
+                const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
+                float acc = 0.f;
+                for (int q = a + lane; q < b; q += 32) acc += vals[q - r0];
+                acc = warp_sum<float>(acc);
+                if (lane == 0) imh[j] += acc;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int j = tid; j < F; j += blockDim.x) {
-            float acc = 0.f;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) acc += imh_w[w * F + j];
-            imh[j] = acc;
-        }
-        __syncthreads();
 
         double term = 0.0;
         if (tid < G) {
@@ -734,10 +742,10 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     }
 }
 
-size_t smem_bytes_f32(int F, int G, int K, int LS, int NW) {
-    const size_t K2 = (K + 1) / 2;
+size_t smem_bytes_f32(int F, int G, int K, int LS) {
+    const int K2 = (K + 1) / 2;
     return sizeof(ulonglong2) * ((size_t)3 * F * LS + 2 * (size_t)F + K2) + sizeof(u64) * (size_t)F * LS +
-           sizeof(float2) * ((size_t)F * LS + K2) + sizeof(float) * ((size_t)NW * F + F + (size_t)G * F);
+           sizeof(float2) * K2 + sizeof(float) * (value_words(F, LS) + F + (size_t)G * F);
 }
 
 // Launch shapes of forward_f32_kernel: (threads per CTA, resident CTAs per SM
@@ -755,8 +763,8 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
                  cudaStream_t stream, int *counter_ext, const int *active) {
     const SystemTables &h = sys->host;
-    const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS, NT / 32);
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
+    const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
     if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the kernel reads its tables from shared memory only: give the SM's
     // unified L1/shared storage to shared memory so more CTAs stay resident

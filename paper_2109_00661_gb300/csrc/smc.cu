@@ -14,6 +14,7 @@
 // per-particle kernels one thread per particle.  Random numbers come from
 // Philox4x32-10 keyed by (seed, sounding) and counted by (particle, purpose,
 // stage, sweep), so every draw is reproducible and independent of scheduling.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,6 +32,7 @@ namespace {
 constexpr int KS = AEM_SMC_SLOTS;  // interface slots per profile
 constexpr int kMoves = 6;
 constexpr int kGroupThreads = 1024;
+constexpr int kClusterThreads = 512;  // per CTA of the cluster-split reweight step
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kPurposeMove = 64, kPurposeValue = 65, kPurposeAccept = 66, kPurposeResample = 67;
 // Langevin: acceptance uniform, and normal j of the proposal from words
@@ -408,6 +410,162 @@ __global__ void __launch_bounds__(kGroupThreads)
         dgamma_out[s] = dg;
         done_out[s] = done;
     }
+}
+
+// The same reweight step split over a thread-block cluster of C CTAs per
+// sounding, for samplers with few soundings and many particles (one CTA per
+// sounding would leave most SMs idle while its FP64 sums run 60 bisection
+// passes).  CTA r of the cluster takes the r-th of C equal slices of the
+// sounding's model-grouped particle positions; every evaluation forms, per
+// model, the partial sums S1, S2 (and once the maximum) over its slice, then
+// after one cluster barrier every CTA adds the C partials of each model in
+// rank order through distributed shared memory, so all CTAs evaluate TESS
+// identically and take the same bisection decisions.  The partials are
+// double-buffered: evaluation e writes buffer e mod 2, and the barrier of
+// evaluation e + 1 is passed only after every CTA has read evaluation e's.
+__global__ void __launch_bounds__(kClusterThreads)
+    reweight_cluster_kernel(const double *ll, const int *perm, const int *off, const int *counts, int N, int M,
+                            double alpha, int iters, double *gamma, double *logz, double *Wg, double *dgamma_out,
+                            int *done_out, int *status) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double p_s1[2][AEM_SMC_MAX_MODELS], p_s2[2][AEM_SMC_MAX_MODELS], p_max[AEM_SMC_MAX_MODELS];
+    __shared__ double s_max[AEM_SMC_MAX_MODELS], s_s1[AEM_SMC_MAX_MODELS], s_ess[AEM_SMC_MAX_MODELS];
+    __shared__ double s_tess;
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int s = blockIdx.x / C, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int *o = off + s * (M + 1);
+    const int *cnt = counts + s * M;
+    const double g0 = gamma[s];
+    if (g0 >= 1.0) {  // the same for every CTA of the cluster: none reaches a barrier
+        if (tid == 0 && rank == 0) {
+            dgamma_out[s] = 0.0;
+            done_out[s] = 1;
+        }
+        return;
+    }
+    const int total = o[M];
+    const int lo_pos = (int)((long long)total * rank / C), hi_pos = (int)((long long)total * (rank + 1) / C);
+    // positions of model k inside this CTA's slice
+    auto span = [&](int k, int &a, int &b) {
+        a = o[k] > lo_pos ? o[k] : lo_pos;
+        b = o[k + 1] < hi_pos ? o[k + 1] : hi_pos;
+    };
+    for (int k = warp; k < M; k += nw) {
+        int a, b;
+        span(k, a, b);
+        double mx = -INFINITY;
+        for (int q = a + lane; q < b; q += 32) mx = fmax(mx, ll[perm[s * N + q]]);
+        mx = warp_max(mx);
+        if (lane == 0) p_max[k] = mx;
+    }
+    cl.sync();
+    for (int k = tid; k < M; k += blockDim.x) {
+        double mx = -INFINITY;
+        for (int q = 0; q < C; ++q) mx = fmax(mx, *cl.map_shared_rank(&p_max[k], q));
+        s_max[k] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        bool any = false;
+        for (int k = 0; k < M; ++k) any = any || s_max[k] > -INFINITY;
+        s_tess = any ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (s_tess == 0.0) {  // no finite log-likelihood in the sounding (see reweight_kernel)
+        for (int k = warp; k < M; k += nw) {
+            int a, b;
+            span(k, a, b);
+            for (int q = a + lane; q < b; q += 32) Wg[s * N + q] = 1.0 / (double)cnt[k];
+        }
+        if (tid == 0 && rank == 0) {
+            dgamma_out[s] = 0.0;
+            done_out[s] = 0;
+            if (status) atomicExch(status, (int)AEM_ERR_NONFINITE);
+        }
+        cl.sync();  // no CTA leaves while another may still read its p_max
+        return;
+    }
+    int buf = 0;
+    auto evaluate = [&](double dg) {
+        for (int k = warp; k < M; k += nw) {
+            int a, b;
+            span(k, a, b);
+            double s1 = 0.0, s2 = 0.0;
+            const double mk = s_max[k];
+            for (int q = a + lane; q < b; q += 32) {
+                const double v = ll[perm[s * N + q]];
+                const double e = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk));
+                s1 += e;
+                s2 += e * e;
+            }
+            s1 = warp_sum_t(s1);
+            s2 = warp_sum_t(s2);
+            if (lane == 0) {
+                p_s1[buf][k] = s1;
+                p_s2[buf][k] = s2;
+            }
+        }
+        cl.sync();
+        for (int k = tid; k < M; k += blockDim.x) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int q = 0; q < C; ++q) {
+                s1 += *cl.map_shared_rank(&p_s1[buf][k], q);
+                s2 += *cl.map_shared_rank(&p_s2[buf][k], q);
+            }
+            s_s1[k] = s1;
+            s_ess[k] = (cnt[k] > 0 && s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double t = 0.0;
+            for (int k = lane; k < M; k += 32) t += s_ess[k];
+            t = warp_sum_t(t);
+            if (lane == 0) s_tess = t;
+        }
+        __syncthreads();
+        buf ^= 1;
+        return s_tess;
+    };
+    const double target = alpha * (double)total;
+    double hi = 1.0 - g0, dg;
+    int done;
+    if (evaluate(hi) >= target) {
+        dg = hi;
+        done = 1;
+    } else {
+        double lo = 0.0;
+        for (int it = 0; it < iters; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (evaluate(mid) >= target)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        if (lo == 0.0 && status && tid == 0 && rank == 0) atomicExch(status, (int)AEM_ERR_NO_BRACKET);
+        dg = lo > 0.0 ? lo : hi;
+        done = 0;
+        evaluate(dg);
+    }
+    for (int k = warp; k < M; k += nw) {
+        int a, b;
+        span(k, a, b);
+        const double mk = s_max[k], s1 = s_s1[k];
+        for (int q = a + lane; q < b; q += 32) {
+            const double v = ll[perm[s * N + q]];
+            Wg[s * N + q] = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk)) / s1;
+        }
+    }
+    if (rank == 0) {
+        for (int k = tid; k < M; k += blockDim.x)
+            if (cnt[k] > 0) logz[s * M + k] += dg * s_max[k] + log(s_s1[k]) - log((double)cnt[k]);
+        if (tid == 0) {
+            gamma[s] = done ? 1.0 : g0 + dg;
+            dgamma_out[s] = dg;
+            done_out[s] = done;
+        }
+    }
+    cl.sync();  // every CTA's partials stay readable until all have finished
 }
 
 // Non-finite log-likelihoods (NaN, or +inf, which no Gaussian likelihood can
@@ -1943,6 +2101,39 @@ static int take_status(smc_state *st) {
                        : "reweight: a sounding has no particle with a finite log-likelihood");
 }
 
+// The reweight step of every sounding: one CTA per sounding, or, when the
+// soundings are few (the cluster of C CTAs per sounding still fits the SMs,
+// C <= 8) and large (N >= 1024), the cluster-split form.
+static int launch_reweight(smc_state *st, cudaStream_t stream) {
+    int C = 1;
+    if (st->N >= 1024)
+        while (C < 8 && (long long)st->S * C * 2 <= st->sys->num_sms) C *= 2;
+    if (C == 1) {
+        reweight_kernel<<<st->S, kGroupThreads, 0, stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
+                                                             st->d.alpha, st->d.bisect_iters, st->gamma, st->logz,
+                                                             st->Wg, st->dgamma, st->done, st->d_status);
+        AEM_CUDA_TRY(cudaGetLastError());
+        return AEM_OK;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(st->S * C), 1, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, reweight_cluster_kernel, (const double *)st->cur.ll, (const int *)st->perm,
+                                    (const int *)st->off, (const int *)st->counts, st->N, st->M, st->d.alpha,
+                                    st->d.bisect_iters, st->gamma, st->logz, st->Wg, st->dgamma, st->done,
+                                    st->d_status));
+    return AEM_OK;
+}
+
 static int launch_group(smc_state *st) {
     group_kernel<<<st->S, kGroupThreads, st->N, st->stream>>>(st->cur.kappa, st->cur.lam, st->N,
                                                               st->d.lambda_max + 1, st->M, st->perm, st->off,
@@ -1956,10 +2147,7 @@ extern "C" int smc_reweight(smc_state *st, double *gamma_out) {
     int rc = launch_group(st);
     if (rc) return rc;
     st->stage += 1;
-    reweight_kernel<<<st->S, kGroupThreads, 0, st->stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
-                                                             st->d.alpha, st->d.bisect_iters, st->gamma, st->logz,
-                                                             st->Wg, st->dgamma, st->done, st->d_status);
-    AEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = launch_reweight(st, st->stream))) return rc;
     if (gamma_out) {
         AEM_CUDA_TRY(cudaMemcpyAsync(gamma_out, st->gamma, sizeof(double) * st->S, cudaMemcpyDeviceToHost, st->stream));
         return take_status(st);  // synchronises
@@ -2178,10 +2366,7 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
     AEM_CUDA_TRY(cudaGetLastError());
     int rc = launch_group(st);
     if (rc) return rc;
-    reweight_kernel<<<st->S, kGroupThreads, 0, s>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
-                                                    st->d.alpha, st->d.bisect_iters, st->gamma, st->logz, st->Wg,
-                                                    st->dgamma, st->done, st->d_status);
-    AEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = launch_reweight(st, s))) return rc;
     resample_kernel<<<st->S, kGroupThreads, 0, s>>>(st->Wg, st->perm, st->off, st->counts, st->N, st->M, nullptr,
                                                     st->d.seed, 0, st->d_stage, st->C, st->anc);
     AEM_CUDA_TRY(cudaGetLastError());

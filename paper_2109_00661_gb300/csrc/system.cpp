@@ -22,6 +22,10 @@ int fail(int code, const std::string &msg) {
 
 int cuda_fail(cudaError_t err, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+    // a failed runtime call leaves its error as the thread's last error; read
+    // it off here so that a later call's cudaGetLastError() does not report it
+    // again (a sticky error stays set for the context all the same)
+    (void)cudaGetLastError();
     return AEM_ERR_CUDA;
 }
 

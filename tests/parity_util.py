@@ -114,3 +114,13 @@ def gradient_bound(y_model, jac, y_obs, gate_bound, eps_an=EPS_AN, eps_mn=I.EPS_
                     np.abs(dll_dy(y_model - dy, y_obs, eps_an, eps_mn) - d0))
     w = dd + np.abs(d0) * gate_bound
     return np.einsum("pg,pgnk->pnk", w, np.abs(jac))
+
+
+def ll_terms32_tol(y_model, y_obs, eps_an=EPS_AN, eps_mn=I.EPS_MN):
+    """Rounding of the FP32 likelihood terms r^2 / v + ln v (r from an FP64
+    difference rounded to FP32, v, the division and the logarithm in FP32):
+    each term within 16 units of 2^-24 of r^2 / v + |ln v| + 1, their sum in
+    FP64 (or compensated) adding nothing at this level; ll = -1/2 the sum."""
+    v = eps_an ** 2 + (eps_mn * y_model) ** 2
+    t1 = (y_obs - y_model) ** 2 / v
+    return 0.5 * 16 * 2.0 ** -24 * np.sum(t1 + np.abs(np.log(v)) + 1.0, axis=1)

@@ -82,23 +82,25 @@ def test_sampler_maps_nonfinite_to_minus_inf(env):
     assert sm.status()[0] == 0
 
 
-def minus_inf_population(S, gsys, data, frac, soundings=1):
-    sm = sampler(S, gsys, data, N=200, soundings=soundings)
+def minus_inf_population(S, gsys, data, frac, soundings=1, N=200):
+    sm = sampler(S, gsys, data, N=N, soundings=soundings)
     sm.init()
     p = sm.get_particles(0)
     rng = np.random.default_rng(0)
     for s in range(soundings):
-        idx = s * 200 + rng.choice(200, int(round(frac * 200)), replace=False)
+        idx = s * N + rng.choice(N, int(round(frac * N)), replace=False)
         p.ll[idx] = -np.inf
     sm.set_particles(p)
     return sm
 
 
-def test_unbracketable_step_reports_no_bracket(env):
+# N = 200: one CTA per sounding; N = 2048: the cluster-split reweight step
+@pytest.mark.parametrize("N", [200, 2048])
+def test_unbracketable_step_reports_no_bracket(env, N):
     """60 % of the particles at ll = -inf: TESS(dgamma) <= 0.4 N < alpha N for
     every dgamma > 0."""
     torch, L, S, gsys, data = env
-    sm = minus_inf_population(S, gsys, data, 0.6)
+    sm = minus_inf_population(S, gsys, data, 0.6, N=N)
     with pytest.raises(L.AEMError) as ei:
         sm.reweight()
     assert ei.value.code == ERR_NO_BRACKET
@@ -106,7 +108,7 @@ def test_unbracketable_step_reports_no_bracket(env):
     assert 0.0 < g < 1e-15  # the smallest probed step, (1 - gamma) 2^-60
     assert sm.status()[0] == 0  # reported once, then cleared
     # 40 % at -inf is still bracketable
-    ok = minus_inf_population(S, gsys, data, 0.4)
+    ok = minus_inf_population(S, gsys, data, 0.4, N=N)
     assert ok.reweight()[0] > 0.0
 
 
@@ -123,11 +125,12 @@ def test_run_stops_on_no_bracket(env, graph):
     assert sm.stats()["stage"] == 1
 
 
-def test_sounding_without_finite_likelihood_reports_nonfinite(env):
+@pytest.mark.parametrize("N", [200, 2048])
+def test_sounding_without_finite_likelihood_reports_nonfinite(env, N):
     torch, L, S, gsys, data = env
-    sm = minus_inf_population(S, gsys, data, 1.0, soundings=2)
+    sm = minus_inf_population(S, gsys, data, 1.0, soundings=2, N=N)
     p = sm.get_particles(0)
-    p.ll[200:] = np.random.default_rng(1).normal(-100.0, 5.0, 200)  # sounding 1 is healthy
+    p.ll[N:] = np.random.default_rng(1).normal(-100.0, 5.0, N)  # sounding 1 is healthy
     sm.set_particles(p)
     with pytest.raises(L.AEMError) as ei:
         sm.reweight()

@@ -16,7 +16,7 @@ import pytest
 
 import oracle as O
 from paper_2109_00661_gb300 import inputs as I
-from parity_util import DELTA_S32, DELTA_T, oracle_ref, oracle_system
+from parity_util import DELTA_S32, DELTA_T, ll_terms32_tol, oracle_ref, oracle_system
 
 pytestmark = pytest.mark.gpu
 
@@ -81,12 +81,8 @@ def test_likelihood_epilogue(env, mode):
     g, ll = L.gates_from_spectrum(sysg, imh, MODES[mode], y_obs, I.EPS_AN, I.EPS_MN)
     yh = g.cpu().numpy().astype(np.float64)
     ref = O.loglik(yh, y_obs, I.EPS_AN, I.EPS_MN)
-    # FP32 terms r^2 / v + ln v (r from the datum's float pair, v and the
-    # division and logarithm in FP32: each term within 16 units of 2^-24 of
-    # r^2 / v + |ln v| + 1), summed exactly enough (TwoSum) to add nothing
-    v = I.EPS_AN ** 2 + (I.EPS_MN * yh) ** 2
-    t1 = (y_obs - yh) ** 2 / v
-    tol = 0.5 * 16 * 2.0 ** -24 * np.sum(t1 + np.abs(np.log(v)) + 1.0, axis=1)
+    # FP32 terms (r from the datum's float pair), summed by TwoSum
+    tol = ll_terms32_tol(yh, y_obs)
     err = np.abs(ll.cpu().numpy() - ref)
     print(f"\n{mode}: ll error max {err.max():.2e}, max error / tolerance {np.max(err / tol):.3f}")
     assert np.all(err <= tol)

@@ -206,20 +206,25 @@ def test_proposals_match_oracle(S, gsys, data, stage, sweep):
     assert np.all(moves > 0)
 
 
-def test_stage_reweight_through_state_api(S, gsys, data):
+@pytest.mark.parametrize("N,km,lm,soundings", [(256, 3, 4, 1), (1024, 3, 4, 1), (4096, 9, 9, 3)])
+def test_stage_reweight_through_state_api(S, gsys, data, N, km, lm, soundings):
     """smc_reweight on the sampler's own particles equals the oracle step on
-    the same log-likelihoods and model ids."""
-    st = settings(n_particles=1024)
-    sm = gpu_smc(S, gsys, data, st)
+    the same log-likelihoods and model ids, per sounding: with one CTA per
+    sounding (N = 256) and with the cluster-split form that few, large
+    soundings take (N >= 1024)."""
+    st = settings(n_particles=N, kappa_max=km, lambda_max=lm)
+    sm = gpu_smc(S, gsys, data, st, soundings=soundings)
     sm.init()
     p = sm.get_particles(0)
-    model = p.kappa * (st.lambda_max + 1) + p.lam
     g = sm.reweight()
-    dg_ref, done_ref, inc_ref, _ = R.reweight(p.ll, model, st.n_models, 0.0, 0.5)
-    assert abs(g[0] - (1.0 if done_ref else dg_ref)) <= 1e-10 * max(dg_ref, 1e-300)
     _, _, lz = sm.model_odds()
-    present = np.bincount(model, minlength=st.n_models) > 0
-    assert np.allclose(lz[0][present], inc_ref[present], rtol=1e-9, atol=1e-9)
+    for s_ in range(soundings):
+        sl = slice(s_ * N, (s_ + 1) * N)
+        model = p.kappa[sl] * (st.lambda_max + 1) + p.lam[sl]
+        dg_ref, done_ref, inc_ref, _ = R.reweight(p.ll[sl], model, st.n_models, 0.0, 0.5)
+        assert abs(g[s_] - (1.0 if done_ref else dg_ref)) <= 1e-10 * max(dg_ref, 1e-300)
+        present = np.bincount(model, minlength=st.n_models) > 0
+        assert np.allclose(lz[s_][present], inc_ref[present], rtol=1e-9, atol=1e-9)
 
 
 def test_model_odds_consistent_with_counts(S, gsys, data):
@@ -350,6 +355,25 @@ def test_graph_captured_run_equals_host_loop(S, gsys, data, mode):
     assert s0 == s1 and np.all(g1 == 1.0)
     assert np.array_equal(g0, g1) and np.array_equal(z0, z1)
     assert np.array_equal(e0, e1)
+    for name in ("kappa", "lam", "phib", "tau", "c", "zc", "phic", "zm", "mv", "ll"):
+        assert np.array_equal(getattr(p0, name), getattr(p1, name)), name
+
+
+def test_graph_equals_host_loop_with_cluster_reweight(S, gsys, data):
+    """Few large soundings take the cluster-split reweight step: captured in
+    the graph it gives the host loop's results bit for bit."""
+    runs = []
+    for graph in (False, True):
+        st = settings(n_particles=2048, seed=31)
+        sm = S.SMC(gsys, np.tile(data, (2, 1)), I.EPS_AN, I.EPS_MN, n_particles=st.n_particles, n_soundings=2,
+                   kappa_max=st.kappa_max, lambda_max=st.lambda_max, zmax=st.zmax, seed=st.seed, r_max=st.r_max)
+        sm.init()
+        stages = sm.run_graph(max_stages=6, n_sweeps=2) if graph else sm.run(max_stages=6, n_sweeps=2)
+        p = sm.get_particles(0)
+        runs.append((stages, p, sm.stats()["gamma"], sm.model_odds()[2]))
+    (s0, p0, g0, z0), (s1, p1, g1, z1) = runs
+    assert s0 == s1 == 6
+    assert np.array_equal(g0, g1) and np.array_equal(z0, z1)
     for name in ("kappa", "lam", "phib", "tau", "c", "zc", "phic", "zm", "mv", "ll"):
         assert np.array_equal(getattr(p0, name), getattr(p1, name)), name
 
