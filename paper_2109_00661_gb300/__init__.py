@@ -145,9 +145,18 @@ def forward_f64(system, models, want_imh=False, stream=None):
     return (g, i) if want_imh else g
 
 
-def spectrum_f32(system, models, stream=None):
-    """aem_forward_f32 with the spectrum only: Im Hz_s [P, F] (float32)."""
-    return _forward(_lib.load().aem_forward_f32, models, _torch().float32, False, True, system, stream)[1]
+def spectrum_f32(system, models, stream=None, out=None):
+    """aem_forward_f32 with the spectrum only: Im Hz_s [P, F] (float32), into
+    out (a contiguous [P, F] CUDA float32 tensor) when given."""
+    if out is None:
+        return _forward(_lib.load().aem_forward_f32, models, _torch().float32, False, True, system, stream)[1]
+    torch = _torch()
+    ms = _models_struct(models, torch.float32)
+    if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (ms.n_models, system.F):
+        raise AEMError("out must be a contiguous [P, F] float32 CUDA tensor")
+    check(_lib.load().aem_forward_f32(system.handle, ctypes.byref(ms), None, _dptr(out), _stream_ptr(stream)),
+          "aem_forward_f32")
+    return out
 
 
 def _obs(y_obs, eps_an, system, dev):
@@ -158,9 +167,10 @@ def _obs(y_obs, eps_an, system, dev):
 
 
 def gates_from_spectrum(system, imh, mode=GATES_TF32_SPLIT, y_obs=None, eps_an=None, eps_mn=0.0, want_gates=True,
-                        stream=None):
+                        stream=None, ll_out=None):
     """aem_gates_from_spectrum: gates [P, G] (float32, or None) and, when y_obs
-    is given, ll [P] (float64, else None) from spectra imh [P, F] (float32)."""
+    is given, ll [P] (float64, else None; into ll_out when given) from spectra
+    imh [P, F] (float32)."""
     torch = _torch()
     if imh.dtype != torch.float32 or not imh.is_cuda or not imh.is_contiguous() or imh.dim() != 2:
         raise AEMError("imh must be a contiguous 2-D CUDA float32 tensor")
@@ -169,7 +179,9 @@ def gates_from_spectrum(system, imh, mode=GATES_TF32_SPLIT, y_obs=None, eps_an=N
     ll = y = e = None
     if y_obs is not None:
         y, e = _obs(y_obs, eps_an, system, imh.device)
-        ll = torch.empty(P, dtype=torch.float64, device=imh.device)
+        ll = ll_out if ll_out is not None else torch.empty(P, dtype=torch.float64, device=imh.device)
+        if ll.dtype != torch.float64 or not ll.is_contiguous() or ll.numel() != P:
+            raise AEMError("ll_out must be a contiguous float64 CUDA tensor of P elements")
     check(_lib.load().aem_gates_from_spectrum(system.handle, _dptr(imh), P, int(mode), _dptr(y), _dptr(e),
                                               float(eps_mn), _dptr(gates), _dptr(ll), _stream_ptr(stream)),
           "aem_gates_from_spectrum")

@@ -424,7 +424,8 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     const int LS = models->lmax;
     const size_t smem = grad_smem_bytes(h.F, h.G, h.K, LS);
     auto kern = LS <= 10 ? loglik_grad_kernel<10> : loglik_grad_kernel<AEM_MAX_LAYERS>;
-    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // always: the static shared memory counts against the 48 KB default too
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGT, smem));
     if (per_sm < 1) per_sm = 1;

@@ -333,7 +333,8 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
                        models->m, models->logtau, models->c};
     size_t smem = smem_bytes<Ops>(h.F, h.G, h.K);
     auto kern = forward_kernel<Ops>;
-    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // always: the static shared memory counts against the 48 KB default too
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     AEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
@@ -405,15 +406,30 @@ __device__ __forceinline__ C2x2 rcoef2(ulonglong2 Bv, ulonglong2 Cv, C2x2 a, C2x
 }
 
 // he = ((e, e), (e ln2, e ln2)) of the layer below the interface.
-__device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
-    float a0, a1, f0, f1;
+// E = exp(-2 u h) of both abscissae as (Re, Im) pairs.
+__device__ __forceinline__ void expm2(C2x2 wb, ulonglong2 he, u64 &Ex, u64 &Ey) {
+    float a0, a1;
     up2(mul2(he.x, wb.re), a0, a1);
+    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
+#if AEM_F32_POLY_SINCOS
+    u64 sn, cs;
+    sincos2_poly(mul2(he.y, wb.im), sn, cs);
+    Ex = mul2(e, cs);
+    Ey = mul2(e, sn);
+#else
+    float f0, f1;
     up2(reduce_2pi2(mul2(he.y, wb.im)), f0, f1);
     float s0, c0, s1, c1;
     sincos_approx(f0, &s0, &c0);
     sincos_approx(f1, &s1, &c1);
-    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
-    const u64 Ex = mul2(e, pk2(c0, c1)), Ey = mul2(e, pk2(s0, s1));
+    Ex = mul2(e, pk2(c0, c1));
+    Ey = mul2(e, pk2(s0, s1));
+#endif
+}
+
+__device__ __forceinline__ void mobius2(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
+    u64 Ex, Ey;
+    expm2(wb, he, Ex, Ey);
     const u64 Px = sub2(mul2(N.re, Ex), mul2(N.im, Ey));
     const u64 Py = fma2(N.re, Ey, mul2(N.im, Ex));
     const u64 Nx = sub2(fma2(r.re, D.re, Px), mul2(r.im, D.im));
@@ -443,14 +459,8 @@ __device__ __forceinline__ C2x2 rcoef2_air(ulonglong2 Bv, ulonglong2 Cv, u64 wai
 
 // The first Moebius step, where D = 1: (N, D) <- (r + N E, 1 + r N E).
 __device__ __forceinline__ void mobius2_d1(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ulonglong2 he) {
-    float a0, a1, f0, f1;
-    up2(mul2(he.x, wb.re), a0, a1);
-    up2(reduce_2pi2(mul2(he.y, wb.im)), f0, f1);
-    float s0, c0, s1, c1;
-    sincos_approx(f0, &s0, &c0);
-    sincos_approx(f1, &s1, &c1);
-    const u64 e = pk2(ex2_approx(a0), ex2_approx(a1));
-    const u64 Ex = mul2(e, pk2(c0, c1)), Ey = mul2(e, pk2(s0, s1));
+    u64 Ex, Ey;
+    expm2(wb, he, Ex, Ey);
     const u64 Px = sub2(mul2(N.re, Ex), mul2(N.im, Ey));
     const u64 Py = fma2(N.re, Ey, mul2(N.im, Ex));
     N.re = add2(r.re, Px);
@@ -765,7 +775,8 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     const SystemTables &h = sys->host;
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
-    if (smem > 48 * 1024) AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // always: the static shared memory counts against the 48 KB default too
+    AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the kernel reads its tables from shared memory only: give the SM's
     // unified L1/shared storage to shared memory so more CTAs stay resident
     AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

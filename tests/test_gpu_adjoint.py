@@ -235,6 +235,24 @@ def test_autograd_function(setup):
         assert torch.allclose(tm[k].grad, w.float()[:, None] * g[:, :, i], rtol=1e-6, atol=0)
 
 
+def test_autograd_without_gradient_is_the_plain_likelihood(setup):
+    """With grad mode off, or no parameter tensor requiring grad, the
+    differentiable entry is the plain aem_loglik_f32 launch (no adjoint)."""
+    torch, L, sysg, s, y_obs = setup
+    models = near_truth(6, seed=7, L=3)
+    plain = L.loglik_f32(sysg, I.to_torch(models, torch.float32), y_obs, I.EPS_AN, I.EPS_MN)
+    tm = I.to_torch(models, torch.float32)
+    ll = L.loglik(sysg, tm, y_obs, I.EPS_AN, I.EPS_MN)  # nothing requires grad
+    assert not ll.requires_grad and torch.equal(ll, plain)
+    for k in L.PARAMS:
+        tm[k].requires_grad_(True)
+    with torch.no_grad():
+        ll2 = L.loglik(sysg, tm, y_obs, I.EPS_AN, I.EPS_MN)
+    assert not ll2.requires_grad and torch.equal(ll2, plain)
+    ll3 = L.loglik(sysg, tm, y_obs, I.EPS_AN, I.EPS_MN)  # the adjoint path, same likelihood
+    assert ll3.requires_grad and torch.equal(ll3.detach(), plain)
+
+
 def test_full_size_sampled_gradient(setup):
     """65,536 random models (1..10 layers, the throughput workload's
     distribution) on the 30-gate / 60-frequency / 200-point system, in the
