@@ -46,9 +46,12 @@ MUFU_PER_LAYER_STEP = 6    # sqrt(|w|), rsqrt, rcp, ex2, sin, cos
 ADJ_FLOPS_PER_LAYER_STEP = 230
 ACCURACY_MODELS = 4096     # subset of the batch on which each variant's per-gate error is measured
 K_PARAM_BYTES = 201        # per model in: 5 float parameters x 10 layers + the int8 layer count
-# DRAM bytes (read + write) of one spectrum-writing forward launch on 65,536
-# models of the workload, from an ncu capture; None until recorded
-SPECTRUM_LAUNCH_BYTES_64K = None
+# DRAM bytes (read 219.63 MB + write 211.21 MB) of one spectrum-writing
+# forward launch of the 256 x 3 dynamic-scheduled shape on 1,048,576 models of
+# this workload, from an ncu capture (dram__bytes_read.sum and
+# dram__bytes_write.sum, one pass); spectra still dirty in L2 when the launch
+# ends are written back after it and are not counted
+SPECTRUM_LAUNCH_BYTES_1M = 219.63e6 + 211.21e6
 METRIC = "forward+loglik evals/s"
 UNIT = "evals/s"
 
@@ -552,33 +555,50 @@ def main():
     ms_max = float(t.item())
     value = job_throughput([P] * world, [ms_max * 1e-3] * world)
 
-    # end to end through the public API: pinned host inputs -> device -> loglik -> host
+    # end to end through the public API: pinned host inputs -> device ->
+    # forward + transform -> host, every step.  The inputs are double-buffered
+    # on the device: the host-to-device copy of the next step's inputs (its
+    # own stream) overlaps this step's kernels, and the first step's copy is
+    # inside the timed region like every other; each step's log-likelihoods
+    # are copied back to pinned host memory.
     e2e = None
     if not args.no_e2e:
         host = {k: torch.as_tensor(np.ascontiguousarray(v, dtype=np.int8 if k == "nlayers" else np.float32)).pin_memory()
                 for k, v in models_np.items()}
         ll_host = torch.empty(P, dtype=torch.float64).pin_memory()
-        dev = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+        bufs = [{k: torch.empty_like(v, device="cuda") for k, v in host.items()} for _ in range(2)]
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         d2h = ll_host.numel() * ll_host.element_size()
+        copy_stream = torch.cuda.Stream()
 
-        def e2e_step():
-            for k in host:
-                dev[k].copy_(host[k], non_blocking=True)
-            L.spectrum_f32(sysg, dev, stream=stream, out=imh_buf)
-            _, out = L.gates_from_spectrum(sysg, imh_buf, L.GATES_TF32_SPLIT, y_obs, eps_an, I.EPS_MN,
-                                           want_gates=False, stream=stream, ll_out=ll_buf)
-            ll_host.copy_(out, non_blocking=True)
+        def h2d_copy(buf):
+            # the copy may start once the kernels that last read this buffer are done
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                for k in host:
+                    buf[k].copy_(host[k], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            return ev
 
-        for _ in range(2):
-            e2e_step()
+        def e2e_run(n_steps):
+            ready = h2d_copy(bufs[0])
+            for i in range(n_steps):
+                nxt = h2d_copy(bufs[(i + 1) % 2]) if i + 1 < n_steps else None
+                stream.wait_event(ready)
+                L.spectrum_f32(sysg, bufs[i % 2], stream=stream, out=imh_buf)
+                L.gates_from_spectrum(sysg, imh_buf, L.GATES_TF32_SPLIT, y_obs, eps_an, I.EPS_MN,
+                                      want_gates=False, stream=stream, ll_out=ll_buf)
+                ll_host.copy_(ll_buf, non_blocking=True)
+                ready = nxt
+
+        e2e_run(2)
         torch.cuda.synchronize()
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         f1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -587,7 +607,8 @@ def main():
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": world * P / (float(te.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "overlap": "double-buffered inputs: the next step's copy runs "
+                                                         "during this step's kernels"}
 
     # the plain double-precision form of the same kernel on a 65,536-model block
     fp64 = None
@@ -787,11 +808,10 @@ def main():
             "roofline": {"bound": "alu", "kernel": "forward_f32_kernel", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": fwd_ms,
                          # DRAM bytes of one spectrum-writing launch from an ncu
-                         # capture of the dynamic-scheduled 256 x 3 shape on 65,536
+                         # capture of the dynamic-scheduled 256 x 3 shape on 2^20
                          # models of this workload, scaled by the model count; null
-                         # when the autotuner picks another shape or none is recorded
-                         "traffic": (SPECTRUM_LAUNCH_BYTES_64K / 65536 * P)
-                         if (shape == 8 and SPECTRUM_LAUNCH_BYTES_64K) else None,
+                         # when the autotuner picks another shape
+                         "traffic": (SPECTRUM_LAUNCH_BYTES_1M / 1048576 * P) if shape == 8 else None,
                          "traffic_unit": "bytes per launch",
                          "algorithmic_bytes": float(P) * (K_PARAM_BYTES + 4 * F),
                          "peak_source": "FP32 FMA rate measured live by aem_probe_peaks (x2 flops)",

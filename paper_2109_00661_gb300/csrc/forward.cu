@@ -674,23 +674,25 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
 
         int f = tid / K2, k = tid - (tid / K2) * K2;
         // the item loop, specialised on the model's layer count up to 10, in
-        // rounds of kValsWords items
+        // rounds of kValsWords items; (f, k) advance by NT items at a time:
+        // NT = dF K2 + dK with 0 <= dK < K2, so one compare carries into f
+        const int dF = NT / K2, dK = NT - (NT / K2) * K2;
         for (int r0 = 0; r0 < FK2; r0 += kValsWords) {
             const int r1 = r0 + kValsWords < FK2 ? r0 + kValsWords : FK2;
             auto items = [&](auto lt) {
                 constexpr int LT = decltype(lt)::value;
-                for (int item = r0 + tid; item < r1; item += blockDim.x) {
+                for (int item = r0 + tid; item < r1; item += NT) {
                     const ulonglong2 lw = lamp[k];
                     float v0, v1;
                     const size_t o = (size_t)f * LS;
                     im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, v0, v1);
                     const float2 hw = hwp[k];
                     vals[item - r0] = fmaf(hw.x, v0, hw.y * v1);
-                    k += blockDim.x;
-                    while (k >= K2) {
-                        k -= K2;
-                        ++f;
-                    }
+                    k += dK;
+                    f += dF;
+                    const bool carry = k >= K2;
+                    k -= carry ? K2 : 0;
+                    f += carry ? 1 : 0;
                 }
             };
             switch (L) {

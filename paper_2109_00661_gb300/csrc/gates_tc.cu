@@ -12,7 +12,7 @@
 // (11-bit significand) leaves a relative residual near 2^-22 per term, BF16
 // (8-bit) near 2^-17.
 //
-// One CTA of four warps per 128-model tile (persistent over tiles, several
+// One CTA of eight warps per 128-model tile (persistent over tiles, several
 // CTAs per SM so that one CTA's staging overlaps another's MMA and epilogue):
 // the threads stage A_hi / A_lo of the tile and, once per CTA, B_hi / B_lo in
 // shared memory in the canonical K-major layout without swizzle (core
@@ -20,8 +20,9 @@
 // row so that a warp's stores cover 512 contiguous bytes; one thread issues
 // the tcgen05.mma chain into a TMEM accumulator (row m of the tile in TMEM
 // lane m, gate n in column n) and commits it to an mbarrier; every warp then
-// reads its 32 lanes with tcgen05.ld and forms the gates and the likelihood
-// of its 32 models.  The likelihood terms are FP32 (Section 2.3.2's Gaussian:
+// reads its 32 lanes (warps w and w + 4 the same lanes, each half of the
+// columns) with tcgen05.ld and forms the gates and the likelihood terms of
+// its 32 models, the two halves' sums meeting in shared memory.  The likelihood terms are FP32 (Section 2.3.2's Gaussian:
 // the residual from a float pair holding the FP64 datum, the variance, one
 // logarithm and one division per gate) and their sum is carried as an
 // unevaluated FP32 pair (Knuth's TwoSum), exact to about 2^-48 of the sum of
@@ -43,7 +44,7 @@ namespace aem {
 namespace {
 
 constexpr int kTM = 128;       // models per tile = MMA M
-constexpr int kThreads = 128;  // warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int kThreads = 256;  // warps w and w + 4 read TMEM lanes 32 (w mod 4) .., one half of the columns each
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr double kLn2Pi = 1.83787706640934548356;  // ln(2 pi)
 
@@ -241,11 +242,12 @@ __device__ __forceinline__ void stage_chunk(const float *__restrict__ src, int F
 }
 
 // Register prefetch of a tile's spectra: thread tid owns chunks
-// c = tid + j kThreads (j < NKC), each chunk KC / 4 float4 loads; a tile needs
-// NKC KC / 4 <= kPF of them per thread (F <= 64 for both splits) and F a
-// multiple of 4 (16-byte rows).  The next tile's loads are issued before the
-// current tile's MMA wait and epilogue, so their latency overlaps both.
-constexpr int kPF = 16;
+// c = tid + j kThreads (j < JC = kTM NKC / kThreads), each chunk KC / 4 float4
+// loads; a tile needs JC KC / 4 <= kPF of them per thread (F <= 64 for both
+// splits) and F a multiple of 4 (16-byte rows).  The next tile's loads are
+// issued before the current tile's MMA wait and epilogue, so their latency
+// overlaps both.
+constexpr int kPF = 8;
 
 template <int KIND>
 struct TilePrefetch {
@@ -258,7 +260,7 @@ struct TilePrefetch {
         for (int q = 0; q < kPF; ++q) {
             const int j = q / Q, part = q - (q / Q) * Q;
             v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < NKC) {
+            if (j < NKC * kTM / kThreads) {
                 const int c = tid + j * kThreads;
                 const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
                 const size_t m = row0 + r;
@@ -272,7 +274,7 @@ struct TilePrefetch {
         using S = Split<KIND>;
 #pragma unroll
         for (int j = 0; j < kPF / Q; ++j) {
-            if (j < NKC) {
+            if (j < NKC * kTM / kThreads) {
                 const int c = tid + j * kThreads;
                 const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
                 const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
@@ -310,7 +312,8 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     unsigned char *Ahi = base, *Alo = base + a_bytes, *Bhi = base + 2 * a_bytes, *Blo = Bhi + b_bytes;
     float2 *ysplit = reinterpret_cast<float2 *>(Blo + b_bytes);  // [2][G]: the datum rows of this tile
     float *ea2 = reinterpret_cast<float *>(ysplit + 2 * AEM_MAX_GATES);
-    uint64_t *mbar_p = reinterpret_cast<uint64_t *>(ea2 + AEM_MAX_GATES);
+    float2 *llp = reinterpret_cast<float2 *>(ea2 + AEM_MAX_GATES);  // [kTM]: the second column half's sums
+    uint64_t *mbar_p = reinterpret_cast<uint64_t *>(llp + kTM);
     uint32_t *slot_p = reinterpret_cast<uint32_t *>(mbar_p + 1);
     int *abort_p = reinterpret_cast<int *>(slot_p + 1);
     const uint32_t mbar = smem_u32(mbar_p);
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     uint32_t phase = 0;
     bool pending = false;  // an MMA chain committed and not yet observed complete
     bool first = true;
-    const bool pf_ok = vec4 && NKC * TilePrefetch<KIND>::Q <= kPF;
+    const bool pf_ok = vec4 && NKC * kTM / kThreads * TilePrefetch<KIND>::Q <= kPF;
     TilePrefetch<KIND> pf;
     if (pf_ok && (int)blockIdx.x < ntiles) pf.load(a.imh, a.P, a.F, NKC, (size_t)blockIdx.x * kTM, tid);
 
@@ -400,16 +403,20 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
         pending = false;
         phase ^= 1u;
         tc_after_sync();
-        // epilogue: this thread's model is row 32 warp + lane of the tile
-        const size_t m = row0 + (size_t)warp * 32 + lane;
+        // epilogue: this thread's model is row 32 (warp mod 4) + lane of the
+        // tile; warps 0-3 take the first half of the gate columns, 4-7 the second
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const size_t m = row0 + (size_t)row;
         const bool valid = m < (size_t)a.P;
         const size_t srow = valid ? m / (size_t)a.obs_per : 0;
         const float2 *yrow = split_rows ? ysplit + (srow - s0) * a.G : nullptr;
         const double *yd = (a.y_obs && !split_rows) ? a.y_obs + srow * a.G : nullptr;
         LlAcc acc;
-        for (int c = 0; c < a.N; c += 8) {
+        const int c_lo = half * (a.N / 2), c_hi = c_lo + a.N / 2;
+        for (int c = c_lo; c < c_hi; c += 8) {
             float v[8];
-            tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int g = c + q;
@@ -429,7 +436,20 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
                 }
             }
         }
-        if (valid && a.ll) a.ll[m] = acc.ll(a.G);
+        if (a.ll) {
+            // the two halves' (sum, error) pairs meet in shared memory, added
+            // in a fixed order by the first half's thread
+            if (half == 1) llp[row] = make_float2(acc.s, acc.e);
+            __syncthreads();
+            if (half == 0 && valid) {
+                const float2 o = llp[row];
+                float s1, e1;
+                two_sum(acc.s, o.x, s1, e1);
+                acc.s = s1;
+                acc.e = (acc.e + o.y) + e1;
+                a.ll[m] = acc.ll(a.G);
+            }
+        }
         tc_before_sync();
         __syncthreads();  // every lane read before the next chain overwrites the accumulator
     }
@@ -494,7 +514,7 @@ int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode
     a.N = round_up(h.G, 16);
     a.ncols = a.N <= 32 ? 32 : 64;
     const size_t smem = (size_t)2 * (kTM + a.N) * a.KP * ES + 1024 + sizeof(float2) * 2 * AEM_MAX_GATES +
-                        sizeof(float) * AEM_MAX_GATES + 64;
+                        sizeof(float) * AEM_MAX_GATES + sizeof(float2) * kTM + 64;
     auto kern = tf32 ? gates_tc_kernel<0> : gates_tc_kernel<1>;
     AEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // all of the SM's unified storage to shared memory, so that several CTAs
@@ -506,16 +526,18 @@ int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode
     if (per_sm < 1) return fail(AEM_ERR_UNSUPPORTED, "aem_gates_from_spectrum: tile does not fit in shared memory");
     // the occupancy query has reported one CTA per SM for the TF32 tile where
     // two fit (the profiler's shared-memory limit says two); take the count
-    // the SM's shared memory allows when it is larger (registers allow four,
-    // warps sixteen, the tensor memory 512 / ncols)
+    // the SM's shared memory, registers and tensor memory allow when it is larger
     {
         int smem_sm = 0, reserved = 0;
         AEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sys->device));
         AEM_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, sys->device));
+        cudaFuncAttributes fa{};
+        AEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
         int by_smem = smem_sm / (int)(smem + (size_t)reserved);
+        const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * kThreads) : 1;
         const int by_tmem = 512 / a.ncols;
+        if (by_smem > by_regs) by_smem = by_regs;
         if (by_smem > by_tmem) by_smem = by_tmem;
-        if (by_smem > 4) by_smem = 4;
         if (by_smem > per_sm) per_sm = by_smem;
     }
     const int ntiles = (P + kTM - 1) / kTM;

@@ -109,3 +109,23 @@ def test_against_oracle_4096(env, mode):
     print(f"\n{mode}: per-gate error max {e.max():.2e} median {np.median(e):.2e}; "
           f"within {floor:g}: {np.mean(e <= floor):.4f}; max error / bound {np.max(e / bound):.3f}")
     assert np.all(e <= bound)
+
+
+def test_benchmark_step_equals_loglik_tc(env):
+    """The benchmark's step (spectra into a caller's buffer, then the TF32-split
+    transform writing the likelihood into a caller's buffer) equals
+    aem_loglik_f32_tc bit for bit."""
+    torch, L, sysg, _ = env
+    s = oracle_system(NAME)
+    y_obs = I.noisy(O.forward(I.truth_3layer(), s, mode=O.HANKEL_RULE)[0], seed=0)
+    models = I.to_torch(I.random_models(2000, seed=41), torch.float32)
+    imh = torch.empty((2000, sysg.F), dtype=torch.float32, device="cuda")
+    ll = torch.empty(2000, dtype=torch.float64, device="cuda")
+    assert L.spectrum_f32(sysg, models, out=imh) is imh
+    _, ll2 = L.gates_from_spectrum(sysg, imh, L.GATES_TF32_SPLIT, y_obs, I.EPS_AN, I.EPS_MN, want_gates=False,
+                                   ll_out=ll)
+    assert ll2 is ll
+    ref = L.loglik_f32_tc(sysg, models, y_obs, I.EPS_AN, I.EPS_MN, L.GATES_TF32_SPLIT)
+    assert torch.equal(ll, ref)
+    with pytest.raises(L.AEMError):
+        L.spectrum_f32(sysg, models, out=imh[:10])
