@@ -45,13 +45,14 @@ MUFU_PER_LAYER_STEP = 6    # sqrt(|w|), rsqrt, rcp, ex2, sin, cos
 # adjoint recursion and the per-layer accumulation)
 ADJ_FLOPS_PER_LAYER_STEP = 230
 ACCURACY_MODELS = 4096     # subset of the batch on which each variant's per-gate error is measured
+DEPTH_CUTOFF = 20.0        # the forward kernel's default (aem_system_set_depth_cutoff)
 K_PARAM_BYTES = 201        # per model in: 5 float parameters x 10 layers + the int8 layer count
-# DRAM bytes (read 219.63 MB + write 211.21 MB) of one spectrum-writing
+# DRAM bytes (read 219.66 MB + write 211.05 MB) of one spectrum-writing
 # forward launch of the 256 x 3 dynamic-scheduled shape on 1,048,576 models of
 # this workload, from an ncu capture (dram__bytes_read.sum and
 # dram__bytes_write.sum, one pass); spectra still dirty in L2 when the launch
 # ends are written back after it and are not counted
-SPECTRUM_LAUNCH_BYTES_1M = 219.63e6 + 211.21e6
+SPECTRUM_LAUNCH_BYTES_1M = 219.66e6 + 211.05e6
 METRIC = "forward+loglik evals/s"
 UNIT = "evals/s"
 
@@ -505,6 +506,11 @@ def main():
     # launch shape of the forward kernel, picked by the project's autotuner
     # on a 65,536-model sample of the workload before any timing
     shape, shape_ms = sysg.autotune(I.to_torch(I.subset(models_np, np.arange(min(P, 1 << 16))), torch.float32))
+    # the layer-steps the recursion runs on this batch with the depth cutoff
+    # (counted by the kernel, one untimed launch): the roofline's algorithmic
+    # work; the whole stack's F K L count is reported beside it
+    steps_run, kept_frac = L.forward_layer_steps(sysg, models)
+    steps_exec = steps_work * kept_frac
 
     stream = torch.cuda.current_stream()
     # One step: the forward model (Cole-Cole, TE recursion, Hankel sums) writes
@@ -646,7 +652,7 @@ def main():
         torch.cuda.synchronize()
         fused_ms = t0_.elapsed_time(t1_) / args.steps
         transforms["fp32_fused_epilogue"] = {"evals_per_s": P / (fused_ms * 1e-3), "ms_per_step": fused_ms,
-                                             "roofline_frac": steps_work * FLOPS_PER_LAYER_STEP / (fused_ms * 1e-3)
+                                             "roofline_frac": steps_exec * FLOPS_PER_LAYER_STEP / (fused_ms * 1e-3)
                                              / (2.0 * peaks["fp32_fma_per_s"])}
         imh = imh_buf
         for name, mode in (("fp32", L.GATES_FP32), ("tf32_split", L.GATES_TF32_SPLIT),
@@ -788,12 +794,14 @@ def main():
     if rank == 0:
         # the dominant kernel (the forward model, 98 % of the step): its
         # algorithmic flops per launch over its own event-timed duration
-        flops = steps_work * FLOPS_PER_LAYER_STEP
+        # the layer-steps the kernel runs: the whole stack less the layers the
+        # depth cutoff drops (aem_system_set_depth_cutoff), counted on the batch
+        flops = steps_exec * FLOPS_PER_LAYER_STEP
         achieved = flops / (fwd_ms * 1e-3) / 1e12
         peak = 2.0 * peaks["fp32_fma_per_s"] / 1e12
         # the special-function unit: layer-steps x 6 MUFU ops against the
         # measured rate of the same mix (rsqrt, rsqrt, rcp, ex2, sin, cos)
-        mufu_frac = steps_work * MUFU_PER_LAYER_STEP / (fwd_ms * 1e-3) / peaks["mufu_mix_per_s"]
+        mufu_frac = steps_exec * MUFU_PER_LAYER_STEP / (fwd_ms * 1e-3) / peaks["mufu_mix_per_s"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -821,7 +829,12 @@ def main():
                          # fraction of that bound the launch reaches, and its pipe
                          "roofline_time_frac": max(achieved / peak, mufu_frac),
                          "binding_pipe": "mufu" if mufu_frac > achieved / peak else "fp32",
-                         "layer_steps_per_s": steps_work / (ms * 1e-3)},
+                         "layer_steps_per_s": steps_exec / (ms * 1e-3),
+                         # the depth cutoff: attenuation exponent, the share of
+                         # the whole stack's F K L layer-steps it kept on this
+                         # batch, and the FP32 fraction counted on the whole stack
+                         "depth_cutoff": DEPTH_CUTOFF, "layer_steps_kept_frac": kept_frac,
+                         "frac_whole_stack": steps_work * FLOPS_PER_LAYER_STEP / (fwd_ms * 1e-3) / 1e12 / peak},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "peaks_measured": peaks,

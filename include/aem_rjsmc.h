@@ -127,6 +127,13 @@ typedef struct {
  * layer recursion, Hankel sum and gate transform in FP32; the f64 entry is
  * the plain double-precision form of the same arithmetic. */
 int aem_forward_f32(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh, void *stream);
+/* aem_forward_f32 that also adds to *layer_steps ([device] unsigned long
+ * long, caller-initialised) the number of (layer, abscissa pair) steps its
+ * recursion ran: with the depth cutoff off this is P x F x ceil(K/2) x the
+ * mean layer count; the ratio is the fraction of the stack the cutoff kept
+ * (aem_system_set_depth_cutoff).  A diagnostic for the throughput figures. */
+int aem_forward_f32_count(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh,
+                          unsigned long long *layer_steps, void *stream);
 int aem_forward_f64(const aem_system *sys, const aem_models_f64 *models, double *gates, double *imh,
                     void *stream);
 
@@ -163,6 +170,25 @@ int aem_loglik_f64(const aem_system *sys, const aem_models_f64 *models, const do
 int aem_autotune_forward(aem_system *sys, const aem_models_f32 *sample, int repeats, void *stream, int *shape_out,
                          float *ms_out);
 int aem_forward_shape(aem_system *sys, int lmax, int shape);
+
+/* Depth cutoff of the FP32 forward kernel (aem_forward_f32, aem_loglik_f32,
+ * the tensor-core and gradient entries' forward pass and every sampler call
+ * that evaluates the FP32 forward model; the FP64 form always takes the whole
+ * stack).  The TE recursion of Section 2 (Ward & Hohmann's reflection form)
+ * runs bottom-up through every layer, but a layer below a depth where the
+ * round-trip attenuation exp(-2 sum Re(u_i) h_i) of the layers above is under
+ * exp(-a) changes R_0 by less than exp(-a) times the largest reflection
+ * coefficient below it; the kernel then treats that layer as the half-space.
+ * a = attenuation + ln(max_n |s_n| / |s_0|) per model and frequency (s_n =
+ * i omega mu0 sigma_n), so a large conductivity contrast below a resistive top
+ * keeps more layers.  The depth is found from a lower bound of the attenuation
+ * (Re u_i >= Re sqrt(s_i) and Re u_i >= sqrt(lambda^2 - max_n(-Re s_n))) and
+ * taken per group of 32 (frequency, abscissa-pair) items as the largest any of
+ * them needs, so the results do not depend on the launch shape.  attenuation:
+ * >= 0 and finite; 0 turns the cutoff off (every layer always).  Default 20
+ * (exp(-20) = 2.1e-9, under FP32 resolution).  Synchronous; applies to later
+ * launches. */
+int aem_system_set_depth_cutoff(aem_system *sys, double attenuation);
 
 /* Gate transform and likelihood from a batch of spectra (the a5 + a6 steps on
  * their own; Section 2.3.2).  imh: [device] n_models x F Im Hz_s at the

@@ -97,6 +97,13 @@ class System:
         """aem_forward_shape: the FP32 forward kernel's launch shape for lmax."""
         check(_lib.load().aem_forward_shape(self._h, int(lmax), int(shape)), "aem_forward_shape")
 
+    def set_depth_cutoff(self, attenuation):
+        """aem_system_set_depth_cutoff: the FP32 forward kernel drops the layers
+        below the depth where the round-trip attenuation exceeds
+        exp(-attenuation) (times the model's conductivity contrast); 0 keeps
+        every layer.  Default 20."""
+        check(_lib.load().aem_system_set_depth_cutoff(self._h, float(attenuation)), "aem_system_set_depth_cutoff")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().aem_system_destroy(self._h)
@@ -157,6 +164,22 @@ def spectrum_f32(system, models, stream=None, out=None):
     check(_lib.load().aem_forward_f32(system.handle, ctypes.byref(ms), None, _dptr(out), _stream_ptr(stream)),
           "aem_forward_f32")
     return out
+
+
+def forward_layer_steps(system, models, stream=None):
+    """aem_forward_f32_count: the (layer, abscissa pair) steps the FP32
+    recursion runs on this batch (an int), and the fraction of the whole
+    stack, P F ceil(K/2) sum(L) / P, that it is (the depth cutoff's share)."""
+    torch = _torch()
+    ms = _models_struct(models, torch.float32)
+    dev = models["logsig"].device
+    steps = torch.zeros(1, dtype=torch.int64, device=dev)
+    scratch = torch.empty((max(ms.n_models, 1), system.F), dtype=torch.float32, device=dev)
+    check(_lib.load().aem_forward_f32_count(system.handle, ctypes.byref(ms), None, _dptr(scratch), _dptr(steps),
+                                            _stream_ptr(stream)), "aem_forward_f32_count")
+    n = int(steps.item())
+    full = int(models["nlayers"].to(torch.int64).sum().item()) * system.F * ((system.K + 1) // 2)
+    return n, (n / full if full else 1.0)
 
 
 def _obs(y_obs, eps_an, system, dev):

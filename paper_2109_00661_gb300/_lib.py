@@ -100,6 +100,8 @@ SIGNATURES = {
     "aem_probe_peaks": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "aem_autotune_forward": ([c_void_p, ctypes.POINTER(Models), c_int, c_void_p, c_void_p, c_void_p], c_int),
     "aem_forward_shape": ([c_void_p, c_int, c_int], c_int),
+    "aem_system_set_depth_cutoff": ([c_void_p, ctypes.c_double], c_int),
+    "aem_forward_f32_count": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     "aem_gates_from_spectrum": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                                  c_void_p], c_int),
     "aem_loglik_f32_tc": ([c_void_p, ctypes.POINTER(Models), c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,

@@ -54,6 +54,9 @@ struct aem_system {
     // launch shape of the FP32 forward kernel per lmax (index into its shape
     // table, 0 = default), set by aem_autotune_forward / aem_forward_shape
     int f32_shape[AEM_MAX_LAYERS + 1] = {};
+    // the FP32 forward kernel's depth cutoff (aem_system_set_depth_cutoff):
+    // attenuation exponent, 0 = the whole stack always
+    float depth_att = 20.f;
 };
 
 namespace aem {

@@ -4,7 +4,7 @@
 // Two values (two Hankel abscissae of one frequency in both kernels) travel
 // in one 64-bit register pair and are advanced with the sm_100+ paired FP32
 // instructions (add/sub/mul/fma .rn.f32x2): one issue slot per operation on
-// both.  The special functions (rsqrt, rcp, ex2, sin, cos) are the hardware
+// both.  The special functions (sqrt, rsqrt, rcp, ex2, sin, cos) are the hardware
 // approximations, one scalar instruction per value (relative error about
 // 2^-22; sin and cos have an absolute error of the same size on the phases
 // both kernels pass them).
@@ -23,8 +23,8 @@ constexpr u64 kHalf2 = 0x3f0000003f000000ull;  // (0.5, 0.5)
 
 // Measurement builds (off by default; build.py passes them through its
 // AEM_NVCC_DEFINES environment variable):
-//   AEM_F32_ACCURATE_MATH=1  the round-to-nearest reciprocal and reciprocal
-//     square root and the library's exp2f / sincosf (full range reduction) in
+//   AEM_F32_ACCURATE_MATH=1  the round-to-nearest square root, reciprocal and
+//     reciprocal square root and the library's exp2f / sincosf (full range reduction) in
 //     place of the hardware approximations, to separate the approximations'
 //     share of the FP32 error from the FP32 arithmetic's;
 //   AEM_F32_REDUCE_PHASE=1   the Moebius step's phase reduced modulo 2 pi
@@ -54,6 +54,15 @@ __device__ __forceinline__ float rsqrt_approx(float v) {
 #else
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+#endif
+}
+__device__ __forceinline__ float sqrt_approx(float v) {
+#if AEM_F32_ACCURATE_MATH
+    return __fsqrt_rn(v);
+#else
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 #endif
 }

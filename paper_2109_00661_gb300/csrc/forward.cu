@@ -353,14 +353,14 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
 // frequency (k and k + K/2) through the layer recursion together, packed in
 // 64-bit register pairs and advanced with the sm_100+ paired FP32 instructions
 // (add/sub/mul/fma .f32x2): one issue slot per operation on both abscissae.
-// The special functions (rsqrt, rcp, ex2, sin, cos) stay scalar.
+// The special functions (sqrt, rsqrt, rcp, ex2, sin, cos) stay scalar.
 //
 // The recursion is carried in w = sqrt(2) u, which folds the constants:
 //   r = (s_a - s_b) / (u_a + u_b)^2 = B / (w_a + w_b)^2,  B = 2 (s_a - s_b)
 //   E = exp(-2 u h) = exp2(e w.x) (cos(e ln2 w.y) + i sin(e ln2 w.y)),
 //   e = -sqrt(2) h log2(e).
 // Principal root of 2 (lambda^2 + s) with x = lambda^2 + Re s, y = Im s > 0:
-//   t = |x + i y| + |x|, rr = rsqrt(t); (t rr, y rr) is (Re w, Im w) when
+//   t = sqrt(x^2 + y^2) + |x|, rr = rsqrt(t); (t rr, y rr) is (Re w, Im w) when
 //   x >= 0 and (Im w, Re w) otherwise.
 // The Moebius step (N, D) <- (r D + N E, D + r N E) keeps R_0 = N / D.
 using namespace f32x2;  // paired FP32 helpers and the hardware approximations (f32x2.h)
@@ -374,10 +374,7 @@ __device__ __forceinline__ C2x2 wroot2(u64 lam2, u64 sxx, u64 yyy, u64 syy) {
     float v0, v1, x0, x1;
     up2(v, v0, v1);
     up2(x, x0, x1);
-    const u64 mod = mul2(v, pk2(rsqrt_approx(v0), rsqrt_approx(v1)));
-    float m0, m1;
-    up2(mod, m0, m1);
-    const float t0 = m0 + fabsf(x0), t1 = m1 + fabsf(x1);
+    const float t0 = sqrt_approx(v0) + fabsf(x0), t1 = sqrt_approx(v1) + fabsf(x1);
     const u64 rr = pk2(rsqrt_approx(t0), rsqrt_approx(t1));
     const u64 p = mul2(pk2(t0, t1), rr), o = mul2(syy, rr);
     float p0, p1, o0, o1;
@@ -469,31 +466,36 @@ __device__ __forceinline__ void mobius2_d1(C2x2 &N, C2x2 &D, C2x2 r, C2x2 wb, ul
     D.im = fma2(r.re, Py, mul2(r.im, Px));
 }
 
+// Per frequency, a block of LS + 1 records of three ulonglong2: record 0 the
+// air interface (B, C in entries 1 and 2), record n + 1 layer n ((Re s,
+// (Im s)^2) in entry 0) and the interface below it (B, C in entries 1 and 2).
+constexpr int kRecWords = 3;
+
 // Im R_0 for the two abscissae of one work item.  LT > 0: the layer count is
 // the compile-time LT and the layer loop is unrolled completely (the record
-// offsets become immediates); LT = 0: the runtime L.
+// offsets become immediates); LT = 0: the runtime L.  R is the frequency's
+// record block, Y its (Im s) pairs.
 template <int LT>
-__device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 *__restrict__ RS,
-                                           const u64 *__restrict__ RY, const ulonglong2 *__restrict__ RB,
-                                           const ulonglong2 *__restrict__ RC, ulonglong2 RAB, ulonglong2 RAC,
-                                           const ulonglong2 *__restrict__ HE, int L_rt, float &out0, float &out1) {
+__device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 *__restrict__ R,
+                                           const u64 *__restrict__ Y, const ulonglong2 *__restrict__ HE, int L_rt,
+                                           float &out0, float &out1) {
     const int L = LT > 0 ? LT : L_rt;
-    ulonglong2 a = RS[L - 1];
-    C2x2 wb = wroot2(lam2, a.x, a.y, RY[L - 1]);
+    ulonglong2 a = R[kRecWords * L];
+    C2x2 wb = wroot2(lam2, a.x, a.y, Y[L - 1]);
     if (L == 1) {
-        up2(rcoef2_air(RAB, RAC, wair, wb).im, out0, out1);
+        up2(rcoef2_air(R[1], R[2], wair, wb).im, out0, out1);
         return;
     }
-    a = RS[L - 2];
-    C2x2 wn = wroot2(lam2, a.x, a.y, RY[L - 2]);
-    C2x2 N = rcoef2(RB[L - 2], RC[L - 2], wn, wb);
+    a = R[kRecWords * (L - 1)];
+    C2x2 wn = wroot2(lam2, a.x, a.y, Y[L - 2]);
+    C2x2 N = rcoef2(R[kRecWords * (L - 1) + 1], R[kRecWords * (L - 1) + 2], wn, wb);
     C2x2 D;  // 1 until the first Moebius step
     ulonglong2 he = HE[L - 2];
     wb = wn;
     auto step = [&](int n) {
-        a = RS[n];
-        wn = wroot2(lam2, a.x, a.y, RY[n]);
-        const C2x2 r = rcoef2(RB[n], RC[n], wn, wb);
+        a = R[kRecWords * (n + 1)];
+        wn = wroot2(lam2, a.x, a.y, Y[n]);
+        const C2x2 r = rcoef2(R[kRecWords * (n + 1) + 1], R[kRecWords * (n + 1) + 2], wn, wb);
         if (n == L - 3)
             mobius2_d1(N, D, r, wb, he);
         else
@@ -516,9 +518,9 @@ __device__ __forceinline__ void im_r0_pair(u64 lam2, u64 wair, const ulonglong2 
         for (int n = L - 3; n >= 0; --n) step(n);
     }
     if (L == 2)
-        mobius2_d1(N, D, rcoef2_air(RAB, RAC, wair, wb), wb, he);
+        mobius2_d1(N, D, rcoef2_air(R[1], R[2], wair, wb), wb, he);
     else
-        mobius2(N, D, rcoef2_air(RAB, RAC, wair, wb), wb, he);
+        mobius2(N, D, rcoef2_air(R[1], R[2], wair, wb), wb, he);
     float n0, n1, d0, d1;
     up2(sub2(mul2(N.im, D.re), mul2(N.re, D.im)), n0, n1);
     up2(fma2(D.re, D.re, mul2(D.im, D.im)), d0, d1);
@@ -533,16 +535,19 @@ constexpr int kValsWords = 6144;
 static_assert(kValsWords % 512 == 0, "rounds must end on a multiple of every launch shape's thread count");
 
 // Words (floats) of the forward kernel's value region: the value buffer, or
-// the prologue's stmp[F*LS] (float2) that shares it, whichever is larger.
+// the prologue's stmp[F*LS] (float2) and TH[F*LS] (float) that share it,
+// whichever is larger.
 __host__ __device__ inline size_t value_words(int F, int LS) {
-    const size_t st = (size_t)2 * F * LS;
+    const size_t st = (size_t)3 * F * LS;
     return st > (size_t)kValsWords ? st : (size_t)kValsWords;
 }
 
-// Shared memory (dynamic), in order: RS[F*LS], RB[F*LS], RC[F*LS], RAB[F],
-// RAC[F], lamp[K2] (ulonglong2), RY[F*LS] (u64), hwp[K2] (float2), the value
-// region (value_words floats), imh[F], T[G*F] (float).  The items (frequency
-// major, F*K2 of them) are taken in rounds of kValsWords: every item stores
+// Shared memory (dynamic), in order: REC[F*(LS+1)*kRecWords] (the record
+// blocks of im_r0_pair), KR[2*K2] (ulonglong2: per abscissa pair the
+// (lambda^2, sqrt(2) lambda) pairs, then the two Hankel weights), Y[F*LS]
+// (u64), the value region (value_words floats), imh[F], T[G*F] (float).  The
+// items (frequency major, F*K2 of them) are taken in rounds of kValsWords:
+// every item stores
 // its weighted pair value at its own index in the buffer; after the round
 // each frequency the round touched is summed by one warp (lane l takes the
 // round's values k = l, l + 32, ... of that frequency, then a warp tree) and
@@ -563,25 +568,28 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                                                                const double *__restrict__ eps_an, double eps_mn,
                                                                double *__restrict__ ll_out,
                                                                int *__restrict__ work_counter,
-                                                               const int *__restrict__ active) {
+                                                               const int *__restrict__ active, float att0,
+                                                               unsigned long long *__restrict__ steps_out) {
     if (active && *active == 0) return;  // a gated launch the caller switched off on the device
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
-    ulonglong2 *RS = reinterpret_cast<ulonglong2 *>(smem_raw);
-    ulonglong2 *RB = RS + (size_t)F * LS;
-    ulonglong2 *RC = RB + (size_t)F * LS;
-    ulonglong2 *RAB = RC + (size_t)F * LS;
-    ulonglong2 *RAC = RAB + F;
-    ulonglong2 *lamp = RAC + F;
-    u64 *RY = reinterpret_cast<u64 *>(lamp + K2);
-    float2 *hwp = reinterpret_cast<float2 *>(RY + (size_t)F * LS);
-    float *vals = reinterpret_cast<float *>(hwp + K2);
+    const int RB1 = (LS + 1) * kRecWords;  // ulonglong2 per frequency block
+    ulonglong2 *REC = reinterpret_cast<ulonglong2 *>(smem_raw);
+    ulonglong2 *KR = REC + (size_t)F * RB1;
+    u64 *Y = reinterpret_cast<u64 *>(KR + 2 * K2);
+    float *vals = reinterpret_cast<float *>(Y + (size_t)F * LS);
     float2 *stmp = reinterpret_cast<float2 *>(vals);  // prologue only: the item loop overwrites it
+    float *TH = vals + (size_t)2 * F * LS;            // prologue only, after stmp
     float *imh = vals + value_words(F, LS);
     float *Ts = imh + F;
+    const int ngroups = (F * K2 + 31) / 32;  // groups of 32 consecutive items
+    int *G0 = reinterpret_cast<int *>(Ts + (size_t)G * F);  // per group: (f << 16) | k of its first item
+    unsigned char *LPW = reinterpret_cast<unsigned char *>(G0 + ngroups);  // per group: its layer count
     __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
+    __shared__ float lh[AEM_MAX_LAYERS];
     __shared__ float lsig[AEM_MAX_LAYERS], lm[AEM_MAX_LAYERS], ltau[AEM_MAX_LAYERS], lc[AEM_MAX_LAYERS];
+    __shared__ float lsp[AEM_MAX_LAYERS], lcp[AEM_MAX_LAYERS];
     __shared__ double ll_part[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -590,14 +598,15 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     for (int k = tid; k < K2; k += blockDim.x) {
         const int kb = k + K2 < K ? k + K2 : K - 1;
         const float la = g_lam[k], lb = g_lam[kb];
-        lamp[k] = make_ulonglong2(pk2(la * la, lb * lb),
-                                  pk2(1.41421356237309505f * la, 1.41421356237309505f * lb));
-        hwp[k] = make_float2(g_hw[k], k + K2 < K ? g_hw[kb] : 0.f);
+        KR[2 * k] = make_ulonglong2(pk2(la * la, lb * lb),
+                                    pk2(1.41421356237309505f * la, 1.41421356237309505f * lb));
+        KR[2 * k + 1] = make_ulonglong2(pk2(g_hw[k], k + K2 < K ? g_hw[kb] : 0.f), 0ull);
     }
     const float mu0 = (float)kMu0;
     const int FK2 = F * K2;
 
     __shared__ int next_model;
+    unsigned int nsteps = 0;  // layer-steps of the groups this thread bucketed (steps_out)
     for (int p = blockIdx.x; p < mv.n; p = DYN ? next_model : p + gridDim.x) {
         const int L = mv.nlayers[p];
         __syncthreads();
@@ -606,11 +615,16 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             lsig[tid] = exp10f(mv.logsig[o]);
-            const float e = -1.41421356237309505f * 1.44269504088896341f * exp10f(mv.logh[o]);
+            lh[tid] = exp10f(mv.logh[o]);
+            const float e = -1.41421356237309505f * 1.44269504088896341f * lh[tid];
             HE[tid] = make_ulonglong2(pk2(e, e), pk2(e * 0.69314718055994531f, e * 0.69314718055994531f));
             lm[tid] = mv.m[o];
             ltau[tid] = exp10f(mv.logtau[o]);
             lc[tid] = mv.c[o];
+            float sp, cp;
+            sincospif(0.5f * mv.c[o], &sp, &cp);
+            lsp[tid] = sp;
+            lcp[tid] = cp;
         }
         for (int j = tid; j < F; j += blockDim.x) imh[j] = 0.f;
         __syncthreads();
@@ -623,8 +637,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             if (mm != 0.f) {
                 const float cc = lc[n];
                 const float mag = expf(cc * logf(w * ltau[n]));
-                float sp, cp;
-                sincospif(0.5f * cc, &sp, &cp);
+                const float sp = lsp[n], cp = lcp[n];
                 const float xr = 1.f + mag * cp, xi = mag * sp;
                 const float den = xr * xr + xi * xi;
                 // Each form is evaluated without cancellation.  The paper's
@@ -650,8 +663,8 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 }
             }
             const float sx = -w * mu0 * si, sy = w * mu0 * sr;
-            RS[(size_t)f * LS + n] = make_ulonglong2(pk2(sx, sx), pk2(sy * sy, sy * sy));
-            RY[(size_t)f * LS + n] = pk2(sy, sy);
+            REC[(size_t)f * RB1 + kRecWords * (n + 1)] = make_ulonglong2(pk2(sx, sx), pk2(sy * sy, sy * sy));
+            Y[(size_t)f * LS + n] = pk2(sy, sy);
             stmp[(size_t)f * LS + n] = make_float2(sx, sy);
         }
         __syncthreads();
@@ -661,52 +674,127 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             if (n + 1 < L) {
                 const float2 b = stmp[(size_t)f * LS + n + 1];
                 const float bx = 2.f * (a.x - b.x), by = 2.f * (a.y - b.y);
-                RB[(size_t)f * LS + n] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
-                RC[(size_t)f * LS + n] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
+                ulonglong2 *r = REC + (size_t)f * RB1 + kRecWords * (n + 1);
+                r[1] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
+                r[2] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
             }
             if (n == 0) {
                 const float bx = -2.f * a.x, by = -2.f * a.y;
-                RAB[f] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
-                RAC[f] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
+                ulonglong2 *r = REC + (size_t)f * RB1;
+                r[1] = make_ulonglong2(pk2(bx, bx), pk2(by, by));
+                r[2] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
             }
+        }
+        // The depth cutoff.  Below a depth where the round-trip attenuation
+        // exp(-2 sum_i Re(u_i) h_i) of the layers above has fallen under
+        // exp(-att) for att = att0 + ln(max_n |s_n| / |s_0|), the layers change
+        // R_0 by less than that factor of the largest reflection below, so the
+        // recursion may treat that layer as the half-space.  A lower bound of
+        // the attenuation suffices: Re u_i >= Re sqrt(s_i) and, as Re u grows
+        // with lambda^2, Re u_i >= sqrt(lambda^2 - ms) with ms = max_n(-Re s_n).
+        // TH[f][j] is the lambda^2 above which the bound through layers 0..j
+        // exceeds att (-1: every lambda), non-increasing in j.
+        const bool cut = att0 > 0.f && L > 1;
+        // (The hardware approximations suffice here: the thresholds only
+        // need to be right to well under the exp(-att0) margin.)
+        if (cut)
+            for (int f = tid; f < F; f += blockDim.x) {
+                const float2 *st = stmp + (size_t)f * LS;
+                float s2max = 0.f, ms = 0.f;
+                for (int n = 0; n < L; ++n) {
+                    s2max = fmaxf(s2max, fmaf(st[n].x, st[n].x, st[n].y * st[n].y));
+                    ms = fmaxf(ms, -st[n].x);
+                }
+                const float s02 = fmaf(st[0].x, st[0].x, st[0].y * st[0].y);
+                const float att = att0 + 0.5f * __logf(s2max * rcp_approx(s02));
+                float C = 0.f, H = 0.f;
+                for (int j = 0; j + 1 < L; ++j) {
+                    const float2 a = st[j];
+                    const float m = sqrt_approx(fmaf(a.x, a.x, a.y * a.y));
+                    // Re sqrt(s_j) without cancellation
+                    const float rs = a.x >= 0.f ? sqrt_approx(0.5f * (m + a.x))
+                                                : 0.5f * fabsf(a.y) * rsqrt_approx(0.5f * (m - a.x));
+                    C = fmaf(2.f * lh[j], rs, C);
+                    H += lh[j];
+                    const float q = 0.5f * att * rcp_approx(H);
+                    TH[(size_t)f * LS + j] = C > att ? -1.f : fmaf(q, q, ms);
+                }
+            }
+        __syncthreads();
+        // the layer count of each group of 32 consecutive items (the items
+        // one warp takes together in any launch shape): the largest count any
+        // of them needs, which within a frequency is that of its smallest
+        // lambda (the pair's first abscissa), so the group's first item and
+        // the first item of each later frequency it reaches
+        for (int g = tid; g < ngroups; g += blockDim.x) {
+            int lp = L;
+            if (cut) {
+                const int first = 32 * g, last = min(first + 31, FK2 - 1);
+                const int f0 = first / K2, f1 = last / K2;
+                lp = 1;
+                for (int ff = f0; ff <= f1; ++ff) {
+                    float l2, lb2;
+                    up2(KR[2 * (ff == f0 ? first - f0 * K2 : 0)].x, l2, lb2);
+                    int c = 1;
+                    for (int j = 0; j + 1 < L; ++j) c += l2 <= TH[(size_t)ff * LS + j] ? 1 : 0;
+                    lp = max(lp, c);
+                }
+            }
+            LPW[g] = (unsigned char)lp;
+            G0[g] = ((32 * g / K2) << 16) | (32 * g - (32 * g / K2) * K2);
+            if (steps_out) nsteps += (unsigned int)lp * (unsigned int)(min(32 * g + 32, FK2) - 32 * g);
         }
         __syncthreads();
 
-        int f = tid / K2, k = tid - (tid / K2) * K2;
-        // the item loop, specialised on the model's layer count up to 10, in
-        // rounds of kValsWords items; (f, k) advance by NT items at a time:
-        // NT = dF K2 + dK with 0 <= dK < K2, so one compare carries into f
-        const int dF = NT / K2, dK = NT - (NT / K2) * K2;
+        // The item loop in rounds of kValsWords items.  A warp takes whole
+        // groups (32 items, one per lane): its groups of the round are
+        // g = g0 + warp + j NW, read 32 at a time (one per lane), and each such
+        // chunk is taken bucket by bucket of layer count (a ballot per count),
+        // so every bucket runs the recursion specialised on its count.
         for (int r0 = 0; r0 < FK2; r0 += kValsWords) {
             const int r1 = r0 + kValsWords < FK2 ? r0 + kValsWords : FK2;
-            auto items = [&](auto lt) {
-                constexpr int LT = decltype(lt)::value;
-                for (int item = r0 + tid; item < r1; item += NT) {
-                    const ulonglong2 lw = lamp[k];
-                    float v0, v1;
-                    const size_t o = (size_t)f * LS;
-                    im_r0_pair<LT>(lw.x, lw.y, RS + o, RY + o, RB + o, RC + o, RAB[f], RAC[f], HE, L, v0, v1);
-                    const float2 hw = hwp[k];
-                    vals[item - r0] = fmaf(hw.x, v0, hw.y * v1);
-                    k += dK;
-                    f += dF;
-                    const bool carry = k >= K2;
-                    k -= carry ? K2 : 0;
-                    f += carry ? 1 : 0;
+            const int g0 = r0 >> 5, g1 = (r1 + 31) >> 5;
+            for (int gc = g0 + warp; gc < g1; gc += 32 * NW) {
+                const int gl = gc + lane * NW;
+                const int lpl = gl < g1 ? LPW[gl] : 0;
+                for (int v = __reduce_max_sync(kFull, lpl); v >= 1; --v) {
+                    unsigned int mask = __ballot_sync(kFull, lpl == v);
+                    auto run = [&](auto lt) {
+                        constexpr int LT = decltype(lt)::value;
+                        while (mask) {
+                            const int g = gc + (__ffs(mask) - 1) * NW;
+                            mask &= mask - 1;
+                            const int item = 32 * g + lane;
+                            if (item >= r1) continue;
+                            const int pk = G0[g];
+                            int f = pk >> 16, k = (pk & 0xffff) + lane;
+                            while (k >= K2) {
+                                k -= K2;
+                                ++f;
+                            }
+                            const ulonglong2 lw = KR[2 * k];
+                            float v0, v1;
+                            im_r0_pair<LT>(lw.x, lw.y, REC + f * RB1, Y + f * LS, HE, v, v0, v1);
+                            float h0, h1;
+                            up2(KR[2 * k + 1].x, h0, h1);
+                            vals[item - r0] = fmaf(h0, v0, h1 * v1);
+                        }
+                    };
+                    if (!mask) continue;
+                    switch (v) {
+                        case 1: run(std::integral_constant<int, 1>{}); break;
+                        case 2: run(std::integral_constant<int, 2>{}); break;
+                        case 3: run(std::integral_constant<int, 3>{}); break;
+                        case 4: run(std::integral_constant<int, 4>{}); break;
+                        case 5: run(std::integral_constant<int, 5>{}); break;
+                        case 6: run(std::integral_constant<int, 6>{}); break;
+                        case 7: run(std::integral_constant<int, 7>{}); break;
+                        case 8: run(std::integral_constant<int, 8>{}); break;
+                        case 9: run(std::integral_constant<int, 9>{}); break;
+                        case 10: run(std::integral_constant<int, 10>{}); break;
+                        default: run(std::integral_constant<int, 0>{}); break;
+                    }
                 }
-            };
-            switch (L) {
-                case 1: items(std::integral_constant<int, 1>{}); break;
-                case 2: items(std::integral_constant<int, 2>{}); break;
-                case 3: items(std::integral_constant<int, 3>{}); break;
-                case 4: items(std::integral_constant<int, 4>{}); break;
-                case 5: items(std::integral_constant<int, 5>{}); break;
-                case 6: items(std::integral_constant<int, 6>{}); break;
-                case 7: items(std::integral_constant<int, 7>{}); break;
-                case 8: items(std::integral_constant<int, 8>{}); break;
-                case 9: items(std::integral_constant<int, 9>{}); break;
-                case 10: items(std::integral_constant<int, 10>{}); break;
-                default: items(std::integral_constant<int, 0>{}); break;
             }
             __syncthreads();
             // the round's share of each frequency's Hankel sum, in a fixed order
@@ -752,12 +840,17 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             }
         }
     }
+    if (steps_out) {
+        const unsigned long long t = warp_sum<unsigned long long>(nsteps);
+        if (lane == 0) atomicAdd(steps_out, t);
+    }
 }
 
 size_t smem_bytes_f32(int F, int G, int K, int LS) {
     const int K2 = (K + 1) / 2;
-    return sizeof(ulonglong2) * ((size_t)3 * F * LS + 2 * (size_t)F + K2) + sizeof(u64) * (size_t)F * LS +
-           sizeof(float2) * K2 + sizeof(float) * (value_words(F, LS) + F + (size_t)G * F);
+    return sizeof(ulonglong2) * ((size_t)F * (LS + 1) * kRecWords + 2 * (size_t)K2) + sizeof(u64) * (size_t)F * LS +
+           sizeof(float) * (value_words(F, LS) + F + (size_t)G * F) + sizeof(int) * (((size_t)F * K2 + 31) / 32) +
+           (((size_t)F * K2 + 31) / 32 + 15) / 16 * 16;
 }
 
 // Launch shapes of forward_f32_kernel: (threads per CTA, resident CTAs per SM
@@ -773,7 +866,7 @@ constexpr int kNumF32Shapes = 2 * kNumBase;
 template <int NT, int MINB, bool DYN>
 int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                 cudaStream_t stream, int *counter_ext, const int *active) {
+                 cudaStream_t stream, int *counter_ext, const int *active, unsigned long long *steps) {
     const SystemTables &h = sys->host;
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
@@ -795,7 +888,7 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     if (DYN) AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
                                                sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
-                                               ll, counter, active);
+                                               ll, counter, active, sys->depth_att, steps);
     const cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(counter, stream);
     AEM_CUDA_TRY(e);
@@ -804,11 +897,12 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
 
 int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
                        float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                       cudaStream_t stream, int *counter_ext = nullptr, const int *active = nullptr) {
+                       cudaStream_t stream, int *counter_ext = nullptr, const int *active = nullptr,
+                       unsigned long long *steps = nullptr) {
 #define AEM_SHAPE(I, NT, MINB, DYN) \
     case I:                         \
         return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream, \
-                                           counter_ext, active);
+                                           counter_ext, active, steps);
     switch (idx) {
         AEM_SHAPE(1, 128, 8, false)
         AEM_SHAPE(2, 512, 2, false)
@@ -821,7 +915,7 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
         AEM_SHAPE(9, 128, 6, true)
         default:
             return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream,
-                                               counter_ext, active);
+                                               counter_ext, active, steps);
     }
 #undef AEM_SHAPE
 }
@@ -829,7 +923,8 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
 template <class Models>
 int launch_forward_f32(const aem_system *sys, const Models *models, float *gates, float *imh, const double *y_obs,
                        int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name,
-                       int *counter_ext = nullptr, const int *active = nullptr) {
+                       int *counter_ext = nullptr, const int *active = nullptr,
+                       unsigned long long *steps = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -842,7 +937,7 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
                            models->m, models->logtau, models->c};
     const int LS = models->lmax;
     return launch_shape_index(sys->f32_shape[LS], sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
-                              (cudaStream_t)stream, counter_ext, active);
+                              (cudaStream_t)stream, counter_ext, active, steps);
 }
 
 }  // namespace
@@ -870,6 +965,13 @@ using namespace aem;
 extern "C" int aem_forward_f32(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh,
                                void *stream) {
     return launch_forward_f32(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream, "aem_forward_f32");
+}
+
+extern "C" int aem_forward_f32_count(const aem_system *sys, const aem_models_f32 *models, float *gates, float *imh,
+                                     unsigned long long *layer_steps, void *stream) {
+    if (!layer_steps) return fail(AEM_ERR_INVALID_ARG, "aem_forward_f32_count: NULL layer_steps");
+    return launch_forward_f32(sys, models, gates, imh, nullptr, 0, nullptr, 0.0, nullptr, stream,
+                              "aem_forward_f32_count", nullptr, nullptr, layer_steps);
 }
 
 extern "C" int aem_forward_f64(const aem_system *sys, const aem_models_f64 *models, double *gates, double *imh,
@@ -903,6 +1005,14 @@ int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *mode
                               "aem_loglik_grad_f32", counter);
 }
 }  // namespace aem
+
+extern "C" int aem_system_set_depth_cutoff(aem_system *sys, double attenuation) {
+    if (!sys) return fail(AEM_ERR_INVALID_ARG, "aem_system_set_depth_cutoff: NULL system");
+    if (!(attenuation >= 0.0) || !(attenuation < 1e30))
+        return fail(AEM_ERR_INVALID_ARG, "aem_system_set_depth_cutoff: attenuation must be >= 0 and finite");
+    sys->depth_att = (float)attenuation;
+    return AEM_OK;
+}
 
 extern "C" int aem_autotune_forward(aem_system *sys, const aem_models_f32 *sample, int repeats, void *stream,
                                     int *shape_out, float *ms_out) {

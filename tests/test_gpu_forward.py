@@ -314,6 +314,41 @@ def test_results_independent_of_launch_shape_and_padding(lib, torch_mod, name):
     assert torch_mod.equal(y19, ref[0]) and torch_mod.equal(imh19, ref[1])
 
 
+@pytest.mark.parametrize("name", list(I.CONFIGS))
+def test_depth_cutoff_is_below_fp32_resolution(lib, torch_mod, name):
+    """The depth cutoff (default attenuation 20) against the whole stack
+    (attenuation 0) on the same GPU and models: every Hankel sum moves by less
+    than 2^-20 of its magnitude A_f (the FP32 spectrum bar against the oracle
+    is 2^-17), both settings meet that bar against the oracle, the counted
+    layer-steps equal the whole stack's with the cutoff off and fall with it
+    on, and invalid settings are refused."""
+    sysg = lib.System(**I.system_kwargs(name))
+    models = as_f32_inputs(I.random_models(1000, seed=29))
+    tm = I.to_torch(models, torch_mod.float32)
+    _, imh_ref, absh, _ = oracle_ref(models, name)
+    try:
+        sysg.set_depth_cutoff(0.0)
+        _, imh_full = lib.forward_f32(sysg, tm, want_imh=True)
+        n_full, frac_full = lib.forward_layer_steps(sysg, tm)
+        sysg.set_depth_cutoff(20.0)
+        _, imh_cut = lib.forward_f32(sysg, tm, want_imh=True)
+        n_cut, frac_cut = lib.forward_layer_steps(sysg, tm)
+    finally:
+        sysg.set_depth_cutoff(20.0)
+    a = imh_full.cpu().numpy().astype(np.float64)
+    b = imh_cut.cpu().numpy().astype(np.float64)
+    d = np.abs(a - b) / absh
+    print(f"\n{name}: cutoff kept {frac_cut:.3f} of the layer-steps; |full - cut| / A_f max {d.max():.2e}, "
+          f"spectrum error against the oracle: whole stack {spectrum_err(a, imh_ref, absh).max():.2e}, "
+          f"cut {spectrum_err(b, imh_ref, absh).max():.2e}")
+    assert frac_full == 1.0 and n_cut < n_full
+    assert d.max() < 2.0 ** -20
+    assert spectrum_err(a, imh_ref, absh).max() < DELTA_S32 and spectrum_err(b, imh_ref, absh).max() < DELTA_S32
+    for bad in (-1.0, float("inf"), float("nan")):
+        with pytest.raises(lib.AEMError):
+            sysg.set_depth_cutoff(bad)
+
+
 def test_autotune_records_the_fastest_shape(lib, torch_mod):
     sysg = lib.System(**I.system_kwargs("forward-g30-f60-k200"))
     models = I.to_torch(I.random_models(1 << 15, seed=3), torch_mod.float32)
