@@ -47,12 +47,12 @@ ADJ_FLOPS_PER_LAYER_STEP = 230
 ACCURACY_MODELS = 4096     # subset of the batch on which each variant's per-gate error is measured
 DEPTH_CUTOFF = 20.0        # the forward kernel's default (aem_system_set_depth_cutoff)
 K_PARAM_BYTES = 201        # per model in: 5 float parameters x 10 layers + the int8 layer count
-# DRAM bytes (read 219.66 MB + write 211.05 MB) of one spectrum-writing
+# DRAM bytes (read 218.59 MB + write 210.84 MB) of one spectrum-writing
 # forward launch of the 256 x 3 dynamic-scheduled shape on 1,048,576 models of
 # this workload, from an ncu capture (dram__bytes_read.sum and
 # dram__bytes_write.sum, one pass); spectra still dirty in L2 when the launch
 # ends are written back after it and are not counted
-SPECTRUM_LAUNCH_BYTES_1M = 219.66e6 + 211.05e6
+SPECTRUM_LAUNCH_BYTES_1M = 218.59e6 + 210.84e6
 METRIC = "forward+loglik evals/s"
 UNIT = "evals/s"
 
@@ -654,6 +654,29 @@ def main():
         transforms["fp32_fused_epilogue"] = {"evals_per_s": P / (fused_ms * 1e-3), "ms_per_step": fused_ms,
                                              "roofline_frac": steps_exec * FLOPS_PER_LAYER_STEP / (fused_ms * 1e-3)
                                              / (2.0 * peaks["fp32_fma_per_s"])}
+        # the benchmark's step with the depth cutoff off: the recursion runs
+        # every layer of every model (the paper's form of the recursion)
+        sysg.set_depth_cutoff(0.0)
+        try:
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            t0_ = torch.cuda.Event(enable_timing=True)
+            t1_ = torch.cuda.Event(enable_timing=True)
+            fwd_events.clear()
+            t0_.record(stream)
+            for _ in range(args.steps):
+                step(record=True)
+            t1_.record(stream)
+            torch.cuda.synchronize()
+            ws_ms = t0_.elapsed_time(t1_) / args.steps
+            ws_fwd = sum(a.elapsed_time(b) for a, b in fwd_events) / len(fwd_events)
+        finally:
+            sysg.set_depth_cutoff(DEPTH_CUTOFF)
+        transforms["tf32_split_whole_stack"] = {
+            "evals_per_s": P / (ws_ms * 1e-3), "ms_per_step": ws_ms, "forward_kernel_ms": ws_fwd,
+            "roofline_frac": steps_work * FLOPS_PER_LAYER_STEP / (ws_fwd * 1e-3) / (2.0 * peaks["fp32_fma_per_s"]),
+            "mufu_frac": steps_work * MUFU_PER_LAYER_STEP / (ws_fwd * 1e-3) / peaks["mufu_mix_per_s"]}
         imh = imh_buf
         for name, mode in (("fp32", L.GATES_FP32), ("tf32_split", L.GATES_TF32_SPLIT),
                            ("bf16_split", L.GATES_BF16_SPLIT)):

@@ -535,17 +535,17 @@ constexpr int kValsWords = 6144;
 static_assert(kValsWords % 512 == 0, "rounds must end on a multiple of every launch shape's thread count");
 
 // Words (floats) of the forward kernel's value region: the value buffer, or
-// the prologue's stmp[F*LS] (float2) and TH[F*LS] (float) that share it,
-// whichever is larger.
+// the prologue's stmp[F*LS] (float2) that shares it, whichever is larger.
 __host__ __device__ inline size_t value_words(int F, int LS) {
-    const size_t st = (size_t)3 * F * LS;
+    const size_t st = (size_t)2 * F * LS;
     return st > (size_t)kValsWords ? st : (size_t)kValsWords;
 }
 
 // Shared memory (dynamic), in order: REC[F*(LS+1)*kRecWords] (the record
 // blocks of im_r0_pair), KR[2*K2] (ulonglong2: per abscissa pair the
 // (lambda^2, sqrt(2) lambda) pairs, then the two Hankel weights), Y[F*LS]
-// (u64), the value region (value_words floats), imh[F], T[G*F] (float).  The
+// (u64), the value region (value_words floats), imh[F], T[G*F], TH[F*LS]
+// (float: the depth cutoff's thresholds).  The
 // items (frequency major, F*K2 of them) are taken in rounds of kValsWords:
 // every item stores
 // its weighted pair value at its own index in the buffer; after the round
@@ -580,12 +580,9 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     u64 *Y = reinterpret_cast<u64 *>(KR + 2 * K2);
     float *vals = reinterpret_cast<float *>(Y + (size_t)F * LS);
     float2 *stmp = reinterpret_cast<float2 *>(vals);  // prologue only: the item loop overwrites it
-    float *TH = vals + (size_t)2 * F * LS;            // prologue only, after stmp
     float *imh = vals + value_words(F, LS);
     float *Ts = imh + F;
-    const int ngroups = (F * K2 + 31) / 32;  // groups of 32 consecutive items
-    int *G0 = reinterpret_cast<int *>(Ts + (size_t)G * F);  // per group: (f << 16) | k of its first item
-    unsigned char *LPW = reinterpret_cast<unsigned char *>(G0 + ngroups);  // per group: its layer count
+    float *TH = Ts + (size_t)G * F;  // depth-cutoff thresholds, [F][LS]
     __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
     __shared__ float lh[AEM_MAX_LAYERS];
     __shared__ float lsig[AEM_MAX_LAYERS], lm[AEM_MAX_LAYERS], ltau[AEM_MAX_LAYERS], lc[AEM_MAX_LAYERS];
@@ -606,7 +603,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     const int FK2 = F * K2;
 
     __shared__ int next_model;
-    unsigned int nsteps = 0;  // layer-steps of the groups this thread bucketed (steps_out)
+    unsigned int nsteps = 0;  // layer-steps of the groups this lane bucketed (steps_out)
     for (int p = blockIdx.x; p < mv.n; p = DYN ? next_model : p + gridDim.x) {
         const int L = mv.nlayers[p];
         __syncthreads();
@@ -721,52 +718,50 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 }
             }
         __syncthreads();
-        // the layer count of each group of 32 consecutive items (the items
-        // one warp takes together in any launch shape): the largest count any
-        // of them needs, which within a frequency is that of its smallest
-        // lambda (the pair's first abscissa), so the group's first item and
-        // the first item of each later frequency it reaches
-        for (int g = tid; g < ngroups; g += blockDim.x) {
-            int lp = L;
-            if (cut) {
-                const int first = 32 * g, last = min(first + 31, FK2 - 1);
-                const int f0 = first / K2, f1 = last / K2;
-                lp = 1;
-                for (int ff = f0; ff <= f1; ++ff) {
-                    float l2, lb2;
-                    up2(KR[2 * (ff == f0 ? first - f0 * K2 : 0)].x, l2, lb2);
-                    int c = 1;
-                    for (int j = 0; j + 1 < L; ++j) c += l2 <= TH[(size_t)ff * LS + j] ? 1 : 0;
-                    lp = max(lp, c);
-                }
-            }
-            LPW[g] = (unsigned char)lp;
-            G0[g] = ((32 * g / K2) << 16) | (32 * g - (32 * g / K2) * K2);
-            if (steps_out) nsteps += (unsigned int)lp * (unsigned int)(min(32 * g + 32, FK2) - 32 * g);
-        }
-        __syncthreads();
 
         // The item loop in rounds of kValsWords items.  A warp takes whole
-        // groups (32 items, one per lane): its groups of the round are
-        // g = g0 + warp + j NW, read 32 at a time (one per lane), and each such
-        // chunk is taken bucket by bucket of layer count (a ballot per count),
-        // so every bucket runs the recursion specialised on its count.
+        // groups of 32 consecutive items (one per lane), the same groups in
+        // every launch shape: its groups of the round are g = g0 + warp + j NW,
+        // taken 32 at a time, one per lane.  Each lane finds its group's layer
+        // count: the largest any of its items needs, which within a frequency
+        // is that of its smallest lambda (the pair's first abscissa), so the
+        // group's first item and the first item of each later frequency it
+        // reaches.  The chunk is then taken bucket by bucket of layer count (a
+        // ballot per count), so every bucket runs the recursion specialised
+        // on its count.
         for (int r0 = 0; r0 < FK2; r0 += kValsWords) {
             const int r1 = r0 + kValsWords < FK2 ? r0 + kValsWords : FK2;
             const int g0 = r0 >> 5, g1 = (r1 + 31) >> 5;
             for (int gc = g0 + warp; gc < g1; gc += 32 * NW) {
                 const int gl = gc + lane * NW;
-                const int lpl = gl < g1 ? LPW[gl] : 0;
+                int lpl = 0, pkl = 0;
+                if (gl < g1) {
+                    const int first = 32 * gl, last = min(first + 31, FK2 - 1);
+                    const int f0 = first / K2, f1 = last / K2;
+                    pkl = (f0 << 16) | (first - f0 * K2);
+                    lpl = L;
+                    if (cut) {
+                        lpl = 1;
+                        for (int ff = f0; ff <= f1; ++ff) {
+                            float l2, lb2;
+                            up2(KR[2 * (ff == f0 ? first - f0 * K2 : 0)].x, l2, lb2);
+                            int c = 1;
+                            for (int j = 0; j + 1 < L; ++j) c += l2 <= TH[(size_t)ff * LS + j] ? 1 : 0;
+                            lpl = max(lpl, c);
+                        }
+                    }
+                    if (steps_out) nsteps += (unsigned int)lpl * (unsigned int)(last + 1 - first);
+                }
                 for (int v = __reduce_max_sync(kFull, lpl); v >= 1; --v) {
                     unsigned int mask = __ballot_sync(kFull, lpl == v);
                     auto run = [&](auto lt) {
                         constexpr int LT = decltype(lt)::value;
                         while (mask) {
-                            const int g = gc + (__ffs(mask) - 1) * NW;
+                            const int jl = __ffs(mask) - 1;
                             mask &= mask - 1;
-                            const int item = 32 * g + lane;
+                            const int pk = __shfl_sync(kFull, pkl, jl);
+                            const int item = 32 * (gc + jl * NW) + lane;
                             if (item >= r1) continue;
-                            const int pk = G0[g];
                             int f = pk >> 16, k = (pk & 0xffff) + lane;
                             while (k >= K2) {
                                 k -= K2;
@@ -849,8 +844,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
 size_t smem_bytes_f32(int F, int G, int K, int LS) {
     const int K2 = (K + 1) / 2;
     return sizeof(ulonglong2) * ((size_t)F * (LS + 1) * kRecWords + 2 * (size_t)K2) + sizeof(u64) * (size_t)F * LS +
-           sizeof(float) * (value_words(F, LS) + F + (size_t)G * F) + sizeof(int) * (((size_t)F * K2 + 31) / 32) +
-           (((size_t)F * K2 + 31) / 32 + 15) / 16 * 16;
+           sizeof(float) * (value_words(F, LS) + F + (size_t)G * F + (size_t)F * LS);
 }
 
 // Launch shapes of forward_f32_kernel: (threads per CTA, resident CTAs per SM
