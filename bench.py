@@ -506,11 +506,9 @@ def main():
     # launch shape of the forward kernel, picked by the project's autotuner
     # on a 65,536-model sample of the workload before any timing
     shape, shape_ms = sysg.autotune(I.to_torch(I.subset(models_np, np.arange(min(P, 1 << 16))), torch.float32))
-    # the layer-steps the recursion runs on this batch with the depth cutoff
-    # (counted by the kernel, one untimed launch): the roofline's algorithmic
-    # work; the whole stack's F K L count is reported beside it
-    steps_run, kept_frac = L.forward_layer_steps(sysg, models)
-    steps_exec = steps_work * kept_frac
+    # the share of the whole stack's layer-steps the recursion runs on this
+    # batch with the depth cutoff (counted by the kernel, one untimed launch)
+    _, kept_frac = L.forward_layer_steps(sysg, models)
 
     stream = torch.cuda.current_stream()
     # One step: the forward model (Cole-Cole, TE recursion, Hankel sums) writes
@@ -652,7 +650,7 @@ def main():
         torch.cuda.synchronize()
         fused_ms = t0_.elapsed_time(t1_) / args.steps
         transforms["fp32_fused_epilogue"] = {"evals_per_s": P / (fused_ms * 1e-3), "ms_per_step": fused_ms,
-                                             "roofline_frac": steps_exec * FLOPS_PER_LAYER_STEP / (fused_ms * 1e-3)
+                                             "roofline_frac": steps_work * FLOPS_PER_LAYER_STEP / (fused_ms * 1e-3)
                                              / (2.0 * peaks["fp32_fma_per_s"])}
         # the benchmark's step with the depth cutoff off: the recursion runs
         # every layer of every model (the paper's form of the recursion)
@@ -815,16 +813,15 @@ def main():
                 accuracy[name] = gate_errors(g_.cpu().numpy(), ref, floor)
 
     if rank == 0:
-        # the dominant kernel (the forward model, 98 % of the step): its
-        # algorithmic flops per launch over its own event-timed duration
-        # the layer-steps the kernel runs: the whole stack less the layers the
-        # depth cutoff drops (aem_system_set_depth_cutoff), counted on the batch
-        flops = steps_exec * FLOPS_PER_LAYER_STEP
+        # the dominant kernel (the forward model, 99 % of the step): its
+        # algorithmic flops per launch (F K L layer-steps per model, the whole
+        # stack) over its own event-timed duration
+        flops = steps_work * FLOPS_PER_LAYER_STEP
         achieved = flops / (fwd_ms * 1e-3) / 1e12
         peak = 2.0 * peaks["fp32_fma_per_s"] / 1e12
         # the special-function unit: layer-steps x 6 MUFU ops against the
         # measured rate of the same mix (rsqrt, rsqrt, rcp, ex2, sin, cos)
-        mufu_frac = steps_exec * MUFU_PER_LAYER_STEP / (fwd_ms * 1e-3) / peaks["mufu_mix_per_s"]
+        mufu_frac = steps_work * MUFU_PER_LAYER_STEP / (fwd_ms * 1e-3) / peaks["mufu_mix_per_s"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -852,12 +849,15 @@ def main():
                          # fraction of that bound the launch reaches, and its pipe
                          "roofline_time_frac": max(achieved / peak, mufu_frac),
                          "binding_pipe": "mufu" if mufu_frac > achieved / peak else "fp32",
-                         "layer_steps_per_s": steps_exec / (ms * 1e-3),
-                         # the depth cutoff: attenuation exponent, the share of
-                         # the whole stack's F K L layer-steps it kept on this
-                         # batch, and the FP32 fraction counted on the whole stack
+                         "layer_steps_per_s": steps_work / (ms * 1e-3),
+                         # the depth cutoff (aem_system_set_depth_cutoff): the
+                         # kernel runs only this share of the whole stack's
+                         # layer-steps (counted by the kernel on the batch), so
+                         # its pipes' efficiency on the steps it runs is
+                         # frac_executed and mufu_frac_executed
                          "depth_cutoff": DEPTH_CUTOFF, "layer_steps_kept_frac": kept_frac,
-                         "frac_whole_stack": steps_work * FLOPS_PER_LAYER_STEP / (fwd_ms * 1e-3) / 1e12 / peak},
+                         "frac_executed": achieved / peak * kept_frac,
+                         "mufu_frac_executed": mufu_frac * kept_frac},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "peaks_measured": peaks,

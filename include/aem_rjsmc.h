@@ -173,8 +173,9 @@ int aem_forward_shape(aem_system *sys, int lmax, int shape);
 
 /* Depth cutoff of the FP32 forward kernel (aem_forward_f32, aem_loglik_f32,
  * the tensor-core and gradient entries' forward pass and every sampler call
- * that evaluates the FP32 forward model; the FP64 form always takes the whole
- * stack).  The TE recursion of Section 2 (Ward & Hohmann's reflection form)
+ * that evaluates the FP32 forward model) and of the FP32 adjoint
+ * (aem_loglik_grad_f32, where each abscissa runs the layers it needs); the
+ * FP64 form always takes the whole stack.  The TE recursion of Section 2 (Ward & Hohmann's reflection form)
  * runs bottom-up through every layer, but a layer below a depth where the
  * round-trip attenuation exp(-2 sum Re(u_i) h_i) of the layers above is under
  * exp(-a) changes R_0 by less than exp(-a) times the largest reflection

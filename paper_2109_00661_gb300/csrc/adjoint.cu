@@ -28,6 +28,7 @@
 #include <cstdint>
 
 #include "aem_internal.h"
+#include "depth_cutoff.h"
 #include "f32x2.h"
 
 namespace aem {
@@ -132,11 +133,11 @@ struct GradModels {
 // (Im s, Im s)), lamp[K2] (ulonglong2: (lam_a^2, lam_b^2), (lam_a, lam_b)),
 // DS[F*LS*4] (float2 ds/dp for log10 sigma, m, log10 tau, c), RY2[F*LS] (u64:
 // (Im s)^2 twice), hwp[K2] (float2 weights of the pair), af[F], T[G*F],
-// part[kGW * LS * kNP] (float).
+// part[kGW * LS * kNP], TH[F*LS] (float: the depth cutoff's thresholds).
 size_t grad_smem_bytes(int F, int G, int K, int LS) {
     const size_t K2 = (size_t)(K + 1) / 2, FL = (size_t)F * LS;
     return sizeof(ulonglong2) * (FL + K2) + sizeof(float2) * (FL * 4) + sizeof(u64) * FL + sizeof(float2) * K2 +
-           sizeof(float) * ((size_t)F + (size_t)G * F + (size_t)kGW * LS * kNP);
+           sizeof(float) * ((size_t)F + (size_t)G * F + (size_t)kGW * LS * kNP + FL);
 }
 
 // MAXL: the largest layer count the per-thread arrays hold (10 or
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                                                           const double *__restrict__ y_obs, int obs_per,
                                                           const double *__restrict__ eps_an, double eps_mn,
                                                           const float *__restrict__ g_gates, float *__restrict__ grad,
-                                                          int *__restrict__ work_counter) {
+                                                          int *__restrict__ work_counter, float att0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
     const size_t FL = (size_t)F * LS;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
     float *af = reinterpret_cast<float *>(hwp + K2);
     float *Ts = af + F;
     float *part = Ts + (size_t)G * F;
+    float *TH = part + (size_t)kGW * LS * kNP;
     __shared__ ulonglong2 HE[AEM_MAX_LAYERS];
     __shared__ float thick[AEM_MAX_LAYERS];
     __shared__ float sig_s[AEM_MAX_LAYERS], m_s[AEM_MAX_LAYERS], tau_s[AEM_MAX_LAYERS], c_s[AEM_MAX_LAYERS];
@@ -251,6 +253,22 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
         }
         __syncthreads();
 
+        // ---- the depth cutoff's thresholds (depth_cutoff.h), one frequency per
+        // thread; each item then runs only the layers its abscissa needs (the
+        // forward kernel runs at least those: the largest count of the item's
+        // 32-item group), so a layer it drops contributes nothing to this
+        // item's gradient, a change under exp(-att0) of the item's share
+        const bool cut = att0 > 0.f && L > 1;
+        if (cut)
+            for (int f = tid; f < F; f += blockDim.x)
+                depth_thresholds(
+                    [&](int n) {
+                        float sx, sy, t;
+                        up2(RS[(size_t)f * LS + n].x, sx, t);
+                        up2(RS[(size_t)f * LS + n].y, sy, t);
+                        return make_float2(sx, sy);
+                    },
+                    thick, L, att0, TH + (size_t)f * LS);
         // ---- dl/dyhat from the forward kernel's gates of this model
         if (tid < G) {
             const double yh = (double)g_gates[(size_t)p * G + tid];
@@ -283,11 +301,17 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
             const u64 *Yf = RY2 + (size_t)f * LS;
             const float2 *Df = DS + (size_t)f * LS * 4;
             const C2x2 air = c2(lp.y, kZero2);  // u of the air: lambda
+            int Li = L;  // the layers this item runs
+            if (cut) {
+                float l2, lb2;
+                up2(lp.x, l2, lb2);
+                Li = depth_layers(l2, TH + (size_t)f * LS, L);
+            }
             u64 imod;
             // bottom-up: Gamma_j for every interface j
             {
-                C2x2 ub = c2root(lp.x, Sf[L - 1], Yf[L - 1], imod);
-                for (int j = L - 1; j >= 0; --j) {
+                C2x2 ub = c2root(lp.x, Sf[Li - 1], Yf[Li - 1], imod);
+                for (int j = Li - 1; j >= 0; --j) {
                     const ulonglong2 sb = Sf[j];
                     C2x2 ua, dsab;  // u above the interface; s above minus s below
                     if (j > 0) {
@@ -299,7 +323,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                         dsab = c2(sub2(kZero2, sb.x), sub2(kZero2, sb.y));
                     }
                     const C2x2 rho = c2div(dsab, c2sq(c2add(ua, ub)));
-                    if (j == L - 1) {
+                    if (j == Li - 1) {
                         Gam[j] = rho;
                     } else {
                         const C2x2 b = c2mul(Gam[j + 1], c2expm(HE[j], ub));
@@ -314,7 +338,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
             u64 imod_up = kZero2;
             ulonglong2 sp = make_ulonglong2(kZero2, kZero2);
             C2x2 uj = c2root(lp.x, Sf[0], Yf[0], imod);
-            for (int j = 0; j < L; ++j) {
+            for (int j = 0; j < Li; ++j) {
                 const ulonglong2 sj = Sf[j];
                 const C2x2 q = c2add(up, uj);
                 const u64 iqn = c2inorm(q);
@@ -322,7 +346,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                 const C2x2 iq2c = c2sq(iqc);       // conj(1 / q^2)
                 const C2x2 rho = c2mulc(c2(sub2(sp.x, sj.x), sub2(sp.y, sj.y)), iq2c);
                 C2x2 rbar, ubar_j = c2(kZero2, kZero2), gnext = ubar_j;
-                if (j < L - 1) {
+                if (j < Li - 1) {
                     const ulonglong2 he = HE[j];
                     const C2x2 E = c2expm(he, uj);
                     const C2x2 b = c2mul(Gam[j + 1], E);
@@ -366,7 +390,7 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                 imod_up = imod;
                 sp = sj;
                 gbar = gnext;
-                if (j + 1 < L) uj = c2root(lp.x, Sf[j + 1], Yf[j + 1], imod);
+                if (j + 1 < Li) uj = c2root(lp.x, Sf[j + 1], Yf[j + 1], imod);
             }
             {
                 sbar_p = c2add(sbar_p, c2scale(c2mulc(ubar_p, up), imod_up));
@@ -374,9 +398,9 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                 up2(mul2(wgt, sbar_p.re), x0, x1);
                 up2(mul2(wgt, sbar_p.im), y0, y1);
                 const float swx = x0 + x1, swy = y0 + y1;
-                const float4 *d = reinterpret_cast<const float4 *>(Df + (size_t)(L - 1) * 4);
+                const float4 *d = reinterpret_cast<const float4 *>(Df + (size_t)(Li - 1) * 4);
                 const float4 d01 = d[0], d23 = d[1];
-                float *ac = acc + (L - 1) * kNP;
+                float *ac = acc + (Li - 1) * kNP;
                 ac[0] += fmaf(swx, d01.y, swy * d01.x);
                 ac[2] += fmaf(swx, d01.w, swy * d01.z);
                 ac[3] += fmaf(swx, d23.y, swy * d23.x);
@@ -446,7 +470,7 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
         if (e == cudaSuccess) {
             kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, h.cc_form, sys->d_omega_f, sys->d_lam_f,
                                                         sys->d_hw_f, sys->d_T_f, y_obs, models_per_sounding, eps_an,
-                                                        eps_mn, gates, grad, counter);
+                                                        eps_mn, gates, grad, counter, sys->depth_att);
             e = cudaGetLastError();
         }
     }

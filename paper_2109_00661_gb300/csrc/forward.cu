@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "aem_internal.h"
+#include "depth_cutoff.h"
 #include "f32x2.h"
 
 namespace aem {
@@ -682,41 +683,11 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 r[2] = make_ulonglong2(pk2(-2.f * bx, -2.f * bx), pk2(2.f * by, 2.f * by));
             }
         }
-        // The depth cutoff.  Below a depth where the round-trip attenuation
-        // exp(-2 sum_i Re(u_i) h_i) of the layers above has fallen under
-        // exp(-att) for att = att0 + ln(max_n |s_n| / |s_0|), the layers change
-        // R_0 by less than that factor of the largest reflection below, so the
-        // recursion may treat that layer as the half-space.  A lower bound of
-        // the attenuation suffices: Re u_i >= Re sqrt(s_i) and, as Re u grows
-        // with lambda^2, Re u_i >= sqrt(lambda^2 - ms) with ms = max_n(-Re s_n).
-        // TH[f][j] is the lambda^2 above which the bound through layers 0..j
-        // exceeds att (-1: every lambda), non-increasing in j.
+        // the depth cutoff's thresholds (depth_cutoff.h), one frequency per thread
         const bool cut = att0 > 0.f && L > 1;
-        // (The hardware approximations suffice here: the thresholds only
-        // need to be right to well under the exp(-att0) margin.)
         if (cut)
-            for (int f = tid; f < F; f += blockDim.x) {
-                const float2 *st = stmp + (size_t)f * LS;
-                float s2max = 0.f, ms = 0.f;
-                for (int n = 0; n < L; ++n) {
-                    s2max = fmaxf(s2max, fmaf(st[n].x, st[n].x, st[n].y * st[n].y));
-                    ms = fmaxf(ms, -st[n].x);
-                }
-                const float s02 = fmaf(st[0].x, st[0].x, st[0].y * st[0].y);
-                const float att = att0 + 0.5f * __logf(s2max * rcp_approx(s02));
-                float C = 0.f, H = 0.f;
-                for (int j = 0; j + 1 < L; ++j) {
-                    const float2 a = st[j];
-                    const float m = sqrt_approx(fmaf(a.x, a.x, a.y * a.y));
-                    // Re sqrt(s_j) without cancellation
-                    const float rs = a.x >= 0.f ? sqrt_approx(0.5f * (m + a.x))
-                                                : 0.5f * fabsf(a.y) * rsqrt_approx(0.5f * (m - a.x));
-                    C = fmaf(2.f * lh[j], rs, C);
-                    H += lh[j];
-                    const float q = 0.5f * att * rcp_approx(H);
-                    TH[(size_t)f * LS + j] = C > att ? -1.f : fmaf(q, q, ms);
-                }
-            }
+            for (int f = tid; f < F; f += blockDim.x)
+                depth_thresholds([&](int n) { return stmp[(size_t)f * LS + n]; }, lh, L, att0, TH + (size_t)f * LS);
         __syncthreads();
 
         // The item loop in rounds of kValsWords items.  A warp takes whole
@@ -745,9 +716,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                         for (int ff = f0; ff <= f1; ++ff) {
                             float l2, lb2;
                             up2(KR[2 * (ff == f0 ? first - f0 * K2 : 0)].x, l2, lb2);
-                            int c = 1;
-                            for (int j = 0; j + 1 < L; ++j) c += l2 <= TH[(size_t)ff * LS + j] ? 1 : 0;
-                            lpl = max(lpl, c);
+                            lpl = max(lpl, depth_layers(l2, TH + (size_t)ff * LS, L));
                         }
                     }
                     if (steps_out) nsteps += (unsigned int)lpl * (unsigned int)(last + 1 - first);
