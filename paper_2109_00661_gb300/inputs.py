@@ -62,6 +62,29 @@ def random_models(P, seed=0, lmax=10, lmin=1, layers_max=10):
     )
 
 
+def contrast_models(P, seed=0, lmax=10):
+    """Stacks that stress a depth cutoff: ten layers whose conductivities
+    alternate between the prior's bounds (1e-4 and 1 S/m, the resistive one on
+    top in half of them), thicknesses all at 2 m, all at 200 m or
+    log-uniform, and chargeabilities 0 or up to 0.95 (float64)."""
+    rng = np.random.default_rng(seed)
+    n = np.arange(lmax)
+    top = rng.integers(0, 2, size=P)
+    logsig = np.where((n[None, :] + top[:, None]) % 2 == 0, -4.0, 0.0)
+    kind = rng.integers(0, 3, size=P)
+    logh = np.where(kind[:, None] == 0, np.log10(2.0),
+                    np.where(kind[:, None] == 1, np.log10(200.0), rng.uniform(np.log10(2.0), np.log10(200.0), (P, lmax))))
+    charge = rng.integers(0, 2, size=P)
+    return dict(
+        nlayers=np.full(P, lmax, dtype=np.int8),
+        logsig=logsig,
+        logh=logh,
+        m=np.where(charge[:, None] == 1, rng.uniform(0.5, 0.95, (P, lmax)), 0.0),
+        logtau=rng.uniform(-6.0, -1.0, (P, lmax)),
+        c=rng.uniform(0.1, 1.0, (P, lmax)),
+    )
+
+
 def truth_3layer():
     """Single-sounding truth: sigma (0.01, 0.1, 0.01) S/m, thicknesses (20, 30) m,
     Cole-Cole IP in layer 2 with m = 0.3, tau = 1e-3 s, c = 0.5."""

@@ -314,16 +314,19 @@ def test_results_independent_of_launch_shape_and_padding(lib, torch_mod, name):
     assert torch_mod.equal(y19, ref[0]) and torch_mod.equal(imh19, ref[1])
 
 
-@pytest.mark.parametrize("name", list(I.CONFIGS))
-def test_depth_cutoff_is_below_fp32_resolution(lib, torch_mod, name):
+@pytest.mark.parametrize("name,kind", [(n, k) for n in I.CONFIGS for k in ("random", "contrast")])
+def test_depth_cutoff_is_below_fp32_resolution(lib, torch_mod, name, kind):
     """The depth cutoff (default attenuation 20) against the whole stack
     (attenuation 0) on the same GPU and models: every Hankel sum moves by less
     than 2^-20 of its magnitude A_f (the FP32 spectrum bar against the oracle
     is 2^-17), both settings meet that bar against the oracle, the counted
     layer-steps equal the whole stack's with the cutoff off and fall with it
-    on, and invalid settings are refused."""
+    on, and invalid settings are refused.  Models: the throughput workload's
+    draws, and ten-layer stacks alternating between the prior's conductivity
+    bounds with thin, thick or mixed layers (the contrast term's case)."""
     sysg = lib.System(**I.system_kwargs(name))
-    models = as_f32_inputs(I.random_models(1000, seed=29))
+    draw = I.random_models if kind == "random" else I.contrast_models
+    models = as_f32_inputs(draw(1000, seed=29))
     tm = I.to_torch(models, torch_mod.float32)
     _, imh_ref, absh, _ = oracle_ref(models, name)
     try:
@@ -338,7 +341,7 @@ def test_depth_cutoff_is_below_fp32_resolution(lib, torch_mod, name):
     a = imh_full.cpu().numpy().astype(np.float64)
     b = imh_cut.cpu().numpy().astype(np.float64)
     d = np.abs(a - b) / absh
-    print(f"\n{name}: cutoff kept {frac_cut:.3f} of the layer-steps; |full - cut| / A_f max {d.max():.2e}, "
+    print(f"\n{name} ({kind}): cutoff kept {frac_cut:.3f} of the layer-steps; |full - cut| / A_f max {d.max():.2e}, "
           f"spectrum error against the oracle: whole stack {spectrum_err(a, imh_ref, absh).max():.2e}, "
           f"cut {spectrum_err(b, imh_ref, absh).max():.2e}")
     assert frac_full == 1.0 and n_cut < n_full
