@@ -67,15 +67,19 @@ int build_tables(const aem_system_desc *desc, SystemTables *out);
 // counter: optional device int the dynamic-scheduled shapes use for model
 // claiming instead of a per-launch stream-ordered allocation.  active:
 // optional device int; when it holds 0 the launch does nothing (a sweep of a
-// captured stage loop that the device-side sweep count switched off).
+// captured stage loop that the device-side sweep count switched off).  valid:
+// optional per-model device flags; a model whose flag is 0 is skipped and its
+// ll left as it was (a proposal that was no move, which the accept step
+// ignores).
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, int *counter = nullptr, const int *active = nullptr);
+                         cudaStream_t stream, int *counter = nullptr, const int *active = nullptr,
+                         const int8_t *valid = nullptr);
 // The plain FP64 forward model + log-likelihood with the same per-sounding
-// rows of y_obs (forward.cu); active as above.
+// rows of y_obs (forward.cu); active and valid as above.
 int loglik_f64_soundings(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, const int *active = nullptr);
+                         cudaStream_t stream, const int *active = nullptr, const int8_t *valid = nullptr);
 // Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
 // with per-sounding rows of y_obs (forward.cu); counter as above.
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,

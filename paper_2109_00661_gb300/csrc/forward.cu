@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
                                                            const double *__restrict__ y_obs, int obs_per,
                                                            const double *__restrict__ eps_an, double eps_mn,
                                                            double *__restrict__ ll_out,
-                                                           const int *__restrict__ active) {
+                                                           const int *__restrict__ active,
+                                                           const int8_t *__restrict__ valid) {
     using R = typename Ops::R;
     if (active && *active == 0) return;  // a gated launch the caller switched off on the device
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(ModelsView<Ops> mv, i
     const int FK = F * K;
 
     for (int p = blockIdx.x; p < mv.n; p += gridDim.x) {
+        if (valid && !valid[p]) continue;  // a proposal the caller will not use (CTA-uniform)
         const int L = mv.nlayers[p];
         __syncthreads();  // previous model's epilogue is done with imh / s_tab
         if (tid < L) {
@@ -320,7 +322,8 @@ template <class Ops, class Models>
 int launch_forward(const aem_system *sys, const Models *models, typename Ops::R *gates, typename Ops::R *imh,
                    const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream,
                    const typename Ops::R *omega, const typename Ops::R *lam, const typename Ops::R *hw,
-                   const typename Ops::R *T, const char *name, const int *active = nullptr) {
+                   const typename Ops::R *T, const char *name, const int *active = nullptr,
+                   const int8_t *valid = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -343,7 +346,7 @@ int launch_forward(const aem_system *sys, const Models *models, typename Ops::R 
     if (grid > models->n_models) grid = models->n_models;
     kern<<<(unsigned)grid, kThreads, smem, (cudaStream_t)stream>>>(mv, h.F, h.G, h.K, h.cc_form, omega, lam, hw, T,
                                                                    gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
-                                                                   active);
+                                                                   active, valid);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
 }
@@ -570,7 +573,8 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                                                                double *__restrict__ ll_out,
                                                                int *__restrict__ work_counter,
                                                                const int *__restrict__ active, float att0,
-                                                               unsigned long long *__restrict__ steps_out) {
+                                                               unsigned long long *__restrict__ steps_out,
+                                                               const int8_t *__restrict__ valid) {
     if (active && *active == 0) return;  // a gated launch the caller switched off on the device
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -610,6 +614,10 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         __syncthreads();
         // claimed now, read after this model's later barriers
         if (DYN && tid == 0) next_model = (int)gridDim.x + atomicAdd(work_counter, 1);
+        if (valid && !valid[p]) {  // a proposal the caller will not use (CTA-uniform)
+            if (DYN) __syncthreads();  // next_model visible to every thread
+            continue;
+        }
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             lsig[tid] = exp10f(mv.logsig[o]);
@@ -829,7 +837,8 @@ constexpr int kNumF32Shapes = 2 * kNumBase;
 template <int NT, int MINB, bool DYN>
 int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates, float *imh,
                  const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
-                 cudaStream_t stream, int *counter_ext, const int *active, unsigned long long *steps) {
+                 cudaStream_t stream, int *counter_ext, const int *active, unsigned long long *steps,
+                 const int8_t *valid) {
     const SystemTables &h = sys->host;
     auto kern = forward_f32_kernel<NT, MINB, DYN>;
     const size_t smem = smem_bytes_f32(h.F, h.G, h.K, LS);
@@ -851,7 +860,7 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
     if (DYN) AEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     kern<<<(unsigned)grid, NT, smem, stream>>>(mv, h.F, h.G, h.K, h.cc_form, LS, sys->d_omega_f, sys->d_lam_f,
                                                sys->d_hw_f, sys->d_T_f, gates, imh, y_obs, obs_per, eps_an, eps_mn,
-                                               ll, counter, active, sys->depth_att, steps);
+                                               ll, counter, active, sys->depth_att, steps, valid);
     const cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(counter, stream);
     AEM_CUDA_TRY(e);
@@ -861,11 +870,11 @@ int launch_shape(const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, f
 int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops> &mv, int LS, float *gates,
                        float *imh, const double *y_obs, int obs_per, const double *eps_an, double eps_mn, double *ll,
                        cudaStream_t stream, int *counter_ext = nullptr, const int *active = nullptr,
-                       unsigned long long *steps = nullptr) {
+                       unsigned long long *steps = nullptr, const int8_t *valid = nullptr) {
 #define AEM_SHAPE(I, NT, MINB, DYN) \
     case I:                         \
         return launch_shape<NT, MINB, DYN>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream, \
-                                           counter_ext, active, steps);
+                                           counter_ext, active, steps, valid);
     switch (idx) {
         AEM_SHAPE(1, 128, 8, false)
         AEM_SHAPE(2, 512, 2, false)
@@ -878,7 +887,7 @@ int launch_shape_index(int idx, const aem_system *sys, const ModelsView<FP32Ops>
         AEM_SHAPE(9, 128, 6, true)
         default:
             return launch_shape<256, 4, false>(sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll, stream,
-                                               counter_ext, active, steps);
+                                               counter_ext, active, steps, valid);
     }
 #undef AEM_SHAPE
 }
@@ -887,7 +896,7 @@ template <class Models>
 int launch_forward_f32(const aem_system *sys, const Models *models, float *gates, float *imh, const double *y_obs,
                        int obs_per, const double *eps_an, double eps_mn, double *ll, void *stream, const char *name,
                        int *counter_ext = nullptr, const int *active = nullptr,
-                       unsigned long long *steps = nullptr) {
+                       unsigned long long *steps = nullptr, const int8_t *valid = nullptr) {
     if (!sys || !models) return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": NULL system or models");
     if (models->n_models < 0 || models->lmax < 1 || models->lmax > AEM_MAX_LAYERS)
         return fail(AEM_ERR_INVALID_ARG, std::string(name) + ": n_models < 0 or lmax outside 1..AEM_MAX_LAYERS");
@@ -900,7 +909,7 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
                            models->m, models->logtau, models->c};
     const int LS = models->lmax;
     return launch_shape_index(sys->f32_shape[LS], sys, mv, LS, gates, imh, y_obs, obs_per, eps_an, eps_mn, ll,
-                              (cudaStream_t)stream, counter_ext, active, steps);
+                              (cudaStream_t)stream, counter_ext, active, steps, valid);
 }
 
 }  // namespace
@@ -909,17 +918,17 @@ int launch_forward_f32(const aem_system *sys, const Models *models, float *gates
 namespace aem {
 int loglik_f64_soundings(const aem_system *sys, const aem_models_f64 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, const int *active) {
+                         cudaStream_t stream, const int *active, const int8_t *valid) {
     return launch_forward<FP64Ops>(sys, models, (double *)nullptr, (double *)nullptr, y_obs, models_per_sounding,
                                    eps_an, eps_mn, ll, (void *)stream, sys ? sys->d_omega_d : nullptr,
                                    sys ? sys->d_lam_d : nullptr, sys ? sys->d_hw_d : nullptr,
-                                   sys ? sys->d_T_d : nullptr, "loglik (SMC, FP64)", active);
+                                   sys ? sys->d_T_d : nullptr, "loglik (SMC, FP64)", active, valid);
 }
 int loglik_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
-                         cudaStream_t stream, int *counter, const int *active) {
+                         cudaStream_t stream, int *counter, const int *active, const int8_t *valid) {
     return launch_forward_f32(sys, models, (float *)nullptr, (float *)nullptr, y_obs, models_per_sounding, eps_an,
-                              eps_mn, ll, (void *)stream, "loglik (SMC)", counter, active);
+                              eps_mn, ll, (void *)stream, "loglik (SMC)", counter, active, nullptr, valid);
 }
 }  // namespace aem
 

@@ -1830,22 +1830,25 @@ int sanitize(smc_state *st, double *ll, const int *active = nullptr) {
 
 // Merge and forward model + log-likelihood of a particle set, in FP32 or, with
 // desc.precision = AEM_SMC_FP64, in the plain FP64 form; non-finite results
-// become -inf.
-int run_loglik(smc_state *st, PState ps, const int *active = nullptr) {
+// become -inf.  valid (proposals): particles flagged 0 made no move (their
+// proposal is a copy of the current particle, which the accept step leaves
+// as it is), so the forward model skips them.
+int run_loglik(smc_state *st, PState ps, const int *active = nullptr, const int8_t *valid = nullptr) {
     int rc;
     if (st->d.precision == AEM_SMC_FP64) {
         merge_kernel<double><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(
             ps, st->P, st->LMS, st->m_nl, st->m64_logsig, st->m64_logh, st->m64_m, st->m64_logtau, st->m64_c);
         AEM_CUDA_TRY(cudaGetLastError());
         aem_models_f64 mm{st->P, st->LMS, st->m_nl, st->m64_logsig, st->m64_logh, st->m64_m, st->m64_logtau, st->m64_c};
-        rc = loglik_f64_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream, active);
+        rc = loglik_f64_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream, active,
+                                  valid);
     } else {
         merge_kernel<float><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(
             ps, st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c);
         AEM_CUDA_TRY(cudaGetLastError());
         aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
         rc = loglik_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->stream,
-                                  st->fwd_counter, active);
+                                  st->fwd_counter, active, valid);
     }
     if (rc) return rc;
     return sanitize(st, ps.ll, active);
@@ -2237,7 +2240,7 @@ static int adapt_stage(smc_state *st, const int *stage_dev = nullptr) {
                                                                           pca_view(st), st->pca_lo, st->pca_hi,
                                                                           st->stage, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
-        if ((rc = run_loglik(st, st->prop))) return rc;
+        if ((rc = run_loglik(st, st->prop, nullptr, st->valid))) return rc;
         pca_stat_kernel<<<nb, 128, 0, st->stream>>>(st->cur.ll, st->prop.ll, st->valid, st->perm, st->off,
                                                     st->counts, st->pca_ok, st->gamma, st->pr, st->d.pca_target,
                                                     st->pca_lo, st->pca_hi);
@@ -2308,7 +2311,7 @@ extern "C" int smc_mutate(smc_state *st, int n_sweeps) {
     if (st->d.adaptive && (rc = adapt_stage(st))) return rc;
     for (int sw = 0; sw < R; ++sw) {
         if ((rc = smc_propose(st, st->stage, sw))) return rc;
-        if ((rc = run_loglik(st, st->prop))) return rc;
+        if ((rc = run_loglik(st, st->prop, nullptr, st->valid))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, st->stream>>>(st->cur, st->prop, st->move, st->valid,
                                                                       st->gamma, st->pr, st->stage, sw, st->acc,
                                                                       st->nprop, nullptr, st->lf);
@@ -2393,7 +2396,7 @@ static int enqueue_graph_stage(smc_state *st, int R, int stop_stage, cudaGraphCo
         propose_kernel<<<blocks_for(st->P, 128), 128, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->pr, 0, sw,
                                                                pca_view(st), st->d_stage, st->lf, gate);
         AEM_CUDA_TRY(cudaGetLastError());
-        if ((rc = run_loglik(st, st->prop, gate))) return rc;
+        if ((rc = run_loglik(st, st->prop, gate, st->valid))) return rc;
         accept_kernel<<<blocks_for(st->P, 256), 256, 0, s>>>(st->cur, st->prop, st->move, st->valid, st->gamma,
                                                              st->pr, 0, sw, st->acc, st->nprop, st->d_stage, st->lf,
                                                              gate);
