@@ -293,6 +293,9 @@ def rjsmc_measure(torch, L, I, n_soundings, n_particles, kappa_max, lambda_max, 
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) * 1e-3
     post, lb, _ = sm.model_odds()
+    # every particle at the prior draw and every proposal of every sweep,
+    # including the proposals that made no move (an impossible move, about
+    # 16 % of them), whose evaluation the forward kernel skips
     evals = n_soundings * n_particles * (1 + stages * sweeps)
     lang = None
     if n_langevin:
