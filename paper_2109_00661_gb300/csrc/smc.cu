@@ -302,10 +302,24 @@ __device__ inline double warp_max(double v) {
 // One CTA per sounding.  With W uniform within each model after the last
 // resample, a_i = dgamma * ll_i, S1_k = sum e^{a_i - a_max}, S2_k = sum e^{2(a_i - a_max)},
 // ESS_k = S1^2 / S2 and TESS = sum_k ESS_k.  gamma_t by bisection on TESS = alpha N.
+// dense (dynamic shared memory of reweight_dense_bytes(N)): the sounding's
+// log-likelihoods are staged once in model-grouped order, and each evaluation
+// forms every particle's e^{a_i - a_max} once, one particle per thread, before
+// the per-model sums read them (the FP64 exponentials are the step's cost on
+// this part, and per-model lanes would leave most of them idle on small
+// models); the sums, and so every result, are the same as without it.
+constexpr int kDenseMaxParticles = 12000;
+size_t reweight_dense_bytes(int N) {
+    return N <= kDenseMaxParticles ? (size_t)N * (2 * sizeof(double) + 1) : 0;
+}
 __global__ void __launch_bounds__(kGroupThreads)
     reweight_kernel(const double *ll, const int *perm, const int *off, const int *counts, int N, int M, double alpha,
                     int iters, double *gamma, double *logz, double *Wg, double *dgamma_out, int *done_out,
-                    int *status = nullptr) {
+                    int *status = nullptr, int dense = 0) {
+    extern __shared__ __align__(16) unsigned char rw_smem[];
+    double *sv = reinterpret_cast<double *>(rw_smem);               // [N] ll at each grouped position
+    double *se = sv + N;                                             // [N] e^{a - a_max} of the evaluation
+    unsigned char *spm = reinterpret_cast<unsigned char *>(se + N);  // [N] model at each grouped position
     __shared__ double s_max[AEM_SMC_MAX_MODELS], s_s1[AEM_SMC_MAX_MODELS], s_ess[AEM_SMC_MAX_MODELS];
     __shared__ double s_tess;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -345,13 +359,33 @@ __global__ void __launch_bounds__(kGroupThreads)
         }
         return;
     }
+    if (dense) {
+        for (int k = warp; k < M; k += nw)
+            for (int r = lane; r < cnt[k]; r += 32) {
+                sv[o[k] + r] = ll[perm[s * N + o[k] + r]];
+                spm[o[k] + r] = (unsigned char)k;
+            }
+        __syncthreads();
+    }
     auto evaluate = [&](double dg) {
+        if (dense) {
+            for (int q = tid; q < o[M]; q += blockDim.x) {
+                const double v = sv[q];
+                se[q] = (v == -INFINITY) ? 0.0 : exp(dg * (v - s_max[spm[q]]));
+            }
+            __syncthreads();
+        }
         for (int k = warp; k < M; k += nw) {
             double s1 = 0.0, s2 = 0.0;
             const double mk = s_max[k];
             for (int r = lane; r < cnt[k]; r += 32) {
-                double v = ll[perm[s * N + o[k] + r]];
-                double e = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk));
+                double e;
+                if (dense) {
+                    e = se[o[k] + r];
+                } else {
+                    const double v = ll[perm[s * N + o[k] + r]];
+                    e = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk));
+                }
                 s1 += e;
                 s2 += e * e;
             }
@@ -400,8 +434,15 @@ __global__ void __launch_bounds__(kGroupThreads)
         if (n == 0) continue;
         const double mk = s_max[k], s1 = s_s1[k];
         for (int r = lane; r < n; r += 32) {
-            double v = ll[perm[s * N + o[k] + r]];
-            Wg[s * N + o[k] + r] = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk)) / s1;
+            // the last evaluation was at dg: its e^{a - a_max} are in se
+            double e;
+            if (dense) {
+                e = se[o[k] + r];
+            } else {
+                const double v = ll[perm[s * N + o[k] + r]];
+                e = (v == -INFINITY) ? 0.0 : exp(dg * (v - mk));
+            }
+            Wg[s * N + o[k] + r] = e / s1;
         }
         if (lane == 0) logz[s * M + k] += dg * mk + log(s1) - log((double)n);
     }
@@ -2048,6 +2089,16 @@ extern "C" int smc_create(const aem_system *sys, const smc_desc *desc, const dou
         smc_destroy(st);
         return cuda_fail(e, "smc_create: upload data");
     }
+    // the reweight step's staging of the sounding's log-likelihoods: set now,
+    // not during a stream capture of the stage loop
+    const size_t rw_smem = reweight_dense_bytes(st->N);
+    if (rw_smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(reweight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rw_smem);
+        if (e != cudaSuccess) {
+            smc_destroy(st);
+            return cuda_fail(e, "smc_create: reweight shared memory");
+        }
+    }
     *out = st;
     return AEM_OK;
 }
@@ -2112,9 +2163,11 @@ static int launch_reweight(smc_state *st, cudaStream_t stream) {
     if (st->N >= 1024)
         while (C < 8 && (long long)st->S * C * 2 <= st->sys->num_sms) C *= 2;
     if (C == 1) {
-        reweight_kernel<<<st->S, kGroupThreads, 0, stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N, st->M,
-                                                             st->d.alpha, st->d.bisect_iters, st->gamma, st->logz,
-                                                             st->Wg, st->dgamma, st->done, st->d_status);
+        const size_t smem = reweight_dense_bytes(st->N);
+        reweight_kernel<<<st->S, kGroupThreads, smem, stream>>>(st->cur.ll, st->perm, st->off, st->counts, st->N,
+                                                                st->M, st->d.alpha, st->d.bisect_iters, st->gamma,
+                                                                st->logz, st->Wg, st->dgamma, st->done, st->d_status,
+                                                                smem > 0);
         AEM_CUDA_TRY(cudaGetLastError());
         return AEM_OK;
     }
@@ -2925,8 +2978,11 @@ extern "C" int aem_reweight(const double *ll, const int *model, int n, int n_mod
     group_kernel<<<1, kGroupThreads, n, s>>>(w.kappa, w.lam, n, 1, n_models, w.perm, w.off, w.counts);
     AEM_CUDA_TRY(cudaMemcpyAsync(w.gamma, &gamma_prev, sizeof(double), cudaMemcpyHostToDevice, s));
     AEM_CUDA_TRY(cudaMemsetAsync(logz_inc, 0, sizeof(double) * n_models, s));
-    reweight_kernel<<<1, kGroupThreads, 0, s>>>(ll, w.perm, w.off, w.counts, n, n_models, alpha, bisect_iters,
-                                                w.gamma, logz_inc, w.Wg, dgamma, reached_one);
+    const size_t smem = reweight_dense_bytes(n);
+    if (smem > 48 * 1024)
+        AEM_CUDA_TRY(cudaFuncSetAttribute(reweight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    reweight_kernel<<<1, kGroupThreads, smem, s>>>(ll, w.perm, w.off, w.counts, n, n_models, alpha, bisect_iters,
+                                                   w.gamma, logz_inc, w.Wg, dgamma, reached_one, nullptr, smem > 0);
     scatter_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.Wg, w.perm, w.off, n_models, W);
     AEM_CUDA_TRY(cudaGetLastError());
     return AEM_OK;
