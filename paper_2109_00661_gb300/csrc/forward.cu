@@ -800,15 +800,24 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
         if (imh_out)
             for (int j = tid; j < F; j += blockDim.x) imh_out[(size_t)p * F + j] = imh[j];
         if (ll_out) {
-            if (warp * 32 < G) {
-                const double t = warp_sum<double>(term);
-                if (lane == 0) ll_part[warp] = t;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double acc = 0.0;
-                for (int w = 0; w * 32 < G; ++w) acc += ll_part[w];
-                ll_out[p] = -0.5 * acc;
+            if (G <= 32) {
+                // every term is in warp 0: its tree is the whole sum (0 + t = t
+                // exactly, as the general form below would add it), no barrier
+                if (warp == 0) {
+                    const double t = warp_sum<double>(term);
+                    if (lane == 0) ll_out[p] = -0.5 * t;
+                }
+            } else {
+                if (warp * 32 < G) {
+                    const double t = warp_sum<double>(term);
+                    if (lane == 0) ll_part[warp] = t;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double acc = 0.0;
+                    for (int w = 0; w * 32 < G; ++w) acc += ll_part[w];
+                    ll_out[p] = -0.5 * acc;
+                }
             }
         }
     }
