@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
                                                           const double *__restrict__ y_obs, int obs_per,
                                                           const double *__restrict__ eps_an, double eps_mn,
                                                           const float *__restrict__ g_gates, float *__restrict__ grad,
-                                                          int *__restrict__ work_counter, float att0) {
+                                                          int *__restrict__ work_counter, float att0,
+                                                          const int8_t *__restrict__ valid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K2 = (K + 1) / 2;
     const size_t FL = (size_t)F * LS;
@@ -190,6 +191,10 @@ __global__ void __launch_bounds__(kGT, 3) loglik_grad_kernel(GradModels mv, int 
         const int L = mv.nlayers[p];
         __syncthreads();
         if (tid == 0) next_model = (int)gridDim.x + atomicAdd(work_counter, 1);
+        if (valid && !valid[p]) {  // a proposal the caller will not use (CTA-uniform)
+            __syncthreads();       // next_model visible to every thread
+            continue;
+        }
         if (tid < L) {
             const size_t o = (size_t)p * mv.lmax + tid;
             sig_s[tid] = exp10f(mv.logsig[o]);
@@ -443,7 +448,7 @@ size_t grad_work_bytes(int n_models, int G) { return kGateOff + sizeof(float) * 
 
 int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
-                              cudaStream_t stream, void *work_ext) {
+                              cudaStream_t stream, void *work_ext, const int8_t *valid) {
     const SystemTables &h = sys->host;
     const int LS = models->lmax;
     const size_t smem = grad_smem_bytes(h.F, h.G, h.K, LS);
@@ -463,14 +468,14 @@ int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *model
     int *fwd_counter = reinterpret_cast<int *>(static_cast<char *>(work) + 64);
     float *gates = reinterpret_cast<float *>(static_cast<char *>(work) + kGateOff);
     int rc = loglik_gates_f32_soundings(sys, models, y_obs, models_per_sounding, eps_an, eps_mn, ll, gates, stream,
-                                        fwd_counter);
+                                        fwd_counter, valid);
     cudaError_t e = cudaSuccess;
     if (rc == AEM_OK) {
         e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
         if (e == cudaSuccess) {
             kern<<<(unsigned)grid, kGT, smem, stream>>>(gm, h.F, h.G, h.K, LS, h.cc_form, sys->d_omega_f, sys->d_lam_f,
                                                         sys->d_hw_f, sys->d_T_f, y_obs, models_per_sounding, eps_an,
-                                                        eps_mn, gates, grad, counter, sys->depth_att);
+                                                        eps_mn, gates, grad, counter, sys->depth_att, valid);
             e = cudaGetLastError();
         }
     }

@@ -81,20 +81,21 @@ int loglik_f64_soundings(const aem_system *sys, const aem_models_f64 *models, co
                          int models_per_sounding, const double *eps_an, double eps_mn, double *ll,
                          cudaStream_t stream, const int *active = nullptr, const int8_t *valid = nullptr);
 // Gates [P][G] and log-likelihood (may be NULL) of the FP32 forward kernel
-// with per-sounding rows of y_obs (forward.cu); counter as above.
+// with per-sounding rows of y_obs (forward.cu); counter and valid as above.
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                                int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *gates,
-                               cudaStream_t stream, int *counter = nullptr);
+                               cudaStream_t stream, int *counter = nullptr, const int8_t *valid = nullptr);
 // Log-likelihood and its merged-layer gradient [P][lmax][5] with the same
 // per-sounding rows of y_obs (adjoint.cu).  work: optional device scratch of
 // grad_work_bytes(P, G) bytes (the claim counters and the gates); without it
 // the call takes stream-ordered scratch of that size for its duration.  With
 // it the call makes no allocation, so it can be captured inside a
-// conditional graph body.
+// conditional graph body.  valid: optional per-model device flags; a model
+// whose flag is 0 is skipped (its ll and gradient left as they were).
 size_t grad_work_bytes(int n_models, int G);
 int loglik_grad_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                               int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *grad,
-                              cudaStream_t stream, void *work = nullptr);
+                              cudaStream_t stream, void *work = nullptr, const int8_t *valid = nullptr);
 // Gates (and log-likelihood) from spectra [P][F] by the transform of the
 // given aem_gates_mode; y_obs rows advance every obs_per models (gates_tc.cu).
 int gates_from_spectrum(const aem_system *sys, const float *imh, int P, int mode, const double *y_obs,

@@ -981,9 +981,9 @@ namespace aem {
 // per-sounding rows of y_obs (ll may be NULL).
 int loglik_gates_f32_soundings(const aem_system *sys, const aem_models_f32 *models, const double *y_obs,
                                int models_per_sounding, const double *eps_an, double eps_mn, double *ll, float *gates,
-                               cudaStream_t stream, int *counter) {
+                               cudaStream_t stream, int *counter, const int8_t *valid) {
     return launch_forward_f32(sys, models, gates, nullptr, y_obs, models_per_sounding, eps_an, eps_mn, ll, stream,
-                              "aem_loglik_grad_f32", counter);
+                              "aem_loglik_grad_f32", counter, nullptr, nullptr, valid);
 }
 }  // namespace aem
 

@@ -1898,13 +1898,14 @@ int run_loglik(smc_state *st, PState ps, const int *active = nullptr, const int8
 // Log-likelihood and particle-space gradient of a particle set: merge, the
 // adjoint kernel on the merged models, then the chain rule back to the
 // particle's parameters.
-int run_grad(smc_state *st, PState ps, float *pg) {
+// valid (proposals): particles flagged 0 are skipped, as in run_loglik.
+int run_grad(smc_state *st, PState ps, float *pg, const int8_t *valid = nullptr) {
     merge_kernel<float><<<blocks_for(st->P, 256), 256, 0, st->stream>>>(ps, st->P, st->LMS, st->m_nl, st->m_logsig,
                                                                 st->m_logh, st->m_m, st->m_logtau, st->m_c);
     AEM_CUDA_TRY(cudaGetLastError());
     aem_models_f32 mm{st->P, st->LMS, st->m_nl, st->m_logsig, st->m_logh, st->m_m, st->m_logtau, st->m_c};
     int rc = loglik_grad_f32_soundings(st->sys, &mm, st->y, st->N, st->eps_an, st->eps_mn, ps.ll, st->mgrad,
-                                       st->stream, st->grad_work);
+                                       st->stream, st->grad_work, valid);
     if (rc) return rc;
     if ((rc = sanitize(st, ps.ll))) return rc;
     pgrad_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(ps, st->mgrad, st->P, st->LMS,
@@ -2318,7 +2319,7 @@ static int langevin_sweeps(smc_state *st, int n, const int *stage_dev = nullptr)
         langevin_propose_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
             st->cur, st->prop, st->gcur, st->gamma, st->lang_h, st->pr, st->stage, l, st->valid, st->lq, stage_dev);
         AEM_CUDA_TRY(cudaGetLastError());
-        if ((rc = run_grad(st, st->prop, st->gprop))) return rc;
+        if ((rc = run_grad(st, st->prop, st->gprop, st->valid))) return rc;
         langevin_accept_kernel<<<blocks_for(st->P, 128), 128, 0, st->stream>>>(
             st->cur, st->prop, st->gcur, st->gprop, st->valid, st->lq, st->gamma, st->lang_h, st->pr, st->stage, l,
             st->lacc, st->lprop, stage_dev);
