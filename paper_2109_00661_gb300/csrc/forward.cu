@@ -5,9 +5,11 @@
 // frequency node and merged layer (Cole-Cole, Section 2), then its threads
 // sweep the flattened (frequency, Hankel abscissa) index space.  Each item runs
 // the bottom-up TE reflection recursion over the layers (the hot loop: F*K*L
-// layer-steps per model), weights Im R_0 by the folded Hankel weight and
-// reduces over the abscissae of a frequency with a segmented warp sum into
-// shared memory.  The epilogue applies the G x F step-off transform and, for
+// layer-steps per model) and weights Im R_0 by the folded Hankel weight; the
+// sums over the abscissae of a frequency are taken in a fixed order (per-warp
+// rows in the FP64 kernel, a per-item value buffer in the FP32 kernel, which
+// also drops the layers under its depth cutoff, depth_cutoff.h).  The
+// epilogue applies the G x F step-off transform and, for
 // the likelihood entry points, the Gaussian log-likelihood of Section 2.3.2
 // (FP32 terms with an FP64 sum in the FP32 kernel, FP64 throughout in the
 // FP64 one).
