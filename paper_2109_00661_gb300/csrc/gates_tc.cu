@@ -246,58 +246,84 @@ __device__ __forceinline__ void stage_chunk(const float *__restrict__ src, int F
 // loads; a tile needs JC KC / 4 <= kPF of them per thread (F <= 64 for both
 // splits) and F a multiple of 4 (16-byte rows).  The next tile's loads are
 // issued before the current tile's MMA wait and epilogue, so their latency
-// overlaps both.
+// overlaps both.  Chunk j's core-matrix index is (tid >> 3) + 32 j: its
+// quotient and remainder by NKC (row group, core-matrix column) advance by
+// those of 32 with one carry per chunk, from one division per thread.
 constexpr int kPF = 8;
 
 template <int KIND>
 struct TilePrefetch {
     static constexpr int KC = 16 / Split<KIND>::ES;  // elements per core-matrix row
     static constexpr int Q = KC / 4;                 // float4 loads per chunk
+    static constexpr int JMAX = kPF / Q;             // chunks per thread
     float4 v[kPF];
+    int nkc;   // NKC
+    int pack;  // divmod(tid >> 3, NKC) and divmod(32, NKC), a byte each (all below 64 when the prefetch applies)
 
-    __device__ __forceinline__ void load(const float *__restrict__ imh, int P, int F, int NKC, size_t row0, int tid) {
+    __device__ __forceinline__ void init(int NKC, int tid) {
+        nkc = NKC;
+        const int q0 = (tid >> 3) / NKC, dq = 32 / NKC;
+        pack = q0 | (((tid >> 3) - q0 * NKC) << 8) | (dq << 16) | ((32 - dq * NKC) << 24);
+    }
+
+    __device__ __forceinline__ void load(const float *__restrict__ imh, int P, int F, size_t row0) {
+        const int jc = nkc * kTM / kThreads, r7 = threadIdx.x & 7;
+        const int dq = (pack >> 16) & 0xff, dc = pack >> 24;
+        int q = pack & 0xff, kc = (pack >> 8) & 0xff;
 #pragma unroll
-        for (int q = 0; q < kPF; ++q) {
-            const int j = q / Q, part = q - (q / Q) * Q;
-            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < NKC * kTM / kThreads) {
-                const int c = tid + j * kThreads;
-                const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
-                const size_t m = row0 + r;
+        for (int j = 0; j < JMAX; ++j) {
+            const size_t m = row0 + (size_t)(r7 + 8 * q);
+#pragma unroll
+            for (int part = 0; part < Q; ++part) {
                 const int k0 = kc * KC + part * 4;
-                if (m < (size_t)P && k0 < F) v[q] = __ldg(reinterpret_cast<const float4 *>(imh + m * F + k0));
+                v[j * Q + part] = (j < jc && m < (size_t)P && k0 < F)
+                                      ? __ldg(reinterpret_cast<const float4 *>(imh + m * F + k0))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            q += dq;
+            kc += dc;
+            if (kc >= nkc) {
+                kc -= nkc;
+                ++q;
             }
         }
     }
 
-    __device__ __forceinline__ void store(int NKC, uint32_t sbo, int tid, unsigned char *hi, unsigned char *lo) const {
+    __device__ __forceinline__ void store(uint32_t sbo, unsigned char *hi, unsigned char *lo) const {
         using S = Split<KIND>;
+        const int jc = nkc * kTM / kThreads, r7 = threadIdx.x & 7;
+        const int dq = (pack >> 16) & 0xff, dc = pack >> 24;
+        int q = pack & 0xff, kc = (pack >> 8) & 0xff;
 #pragma unroll
-        for (int j = 0; j < kPF / Q; ++j) {
-            if (j < NKC * kTM / kThreads) {
-                const int c = tid + j * kThreads;
-                const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
-                const uint32_t o = (uint32_t)(r >> 3) * sbo + (uint32_t)kc * 128u + (uint32_t)(r & 7) * 16u;
+        for (int j = 0; j < JMAX; ++j) {
+            if (j < jc) {
+                const uint32_t o = (uint32_t)q * sbo + (uint32_t)kc * 128u + (uint32_t)r7 * 16u;
                 float x[KC];
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    x[4 * q] = v[j * Q + q].x;
-                    x[4 * q + 1] = v[j * Q + q].y;
-                    x[4 * q + 2] = v[j * Q + q].z;
-                    x[4 * q + 3] = v[j * Q + q].w;
+                for (int p = 0; p < Q; ++p) {
+                    x[4 * p] = v[j * Q + p].x;
+                    x[4 * p + 1] = v[j * Q + p].y;
+                    x[4 * p + 2] = v[j * Q + p].z;
+                    x[4 * p + 3] = v[j * Q + p].w;
                 }
                 typename S::T h[KC], l[KC];
 #pragma unroll
-                for (int q = 0; q < KC; ++q) S::run(x[q], h[q], l[q]);
+                for (int p = 0; p < KC; ++p) S::run(x[p], h[p], l[p]);
                 *reinterpret_cast<uint4 *>(hi + o) = *reinterpret_cast<const uint4 *>(h);
                 *reinterpret_cast<uint4 *>(lo + o) = *reinterpret_cast<const uint4 *>(l);
+            }
+            q += dq;
+            kc += dc;
+            if (kc >= nkc) {
+                kc -= nkc;
+                ++q;
             }
         }
     }
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, KIND == 0 ? 2 : 3) gates_tc_kernel(TcArgs a) {
     using S = Split<KIND>;
     constexpr int ES = S::ES;
     constexpr int KI = 32 / ES;  // K of one MMA: two core matrices
@@ -347,26 +373,30 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
     bool first = true;
     const bool pf_ok = vec4 && NKC * kTM / kThreads * TilePrefetch<KIND>::Q <= kPF;
     TilePrefetch<KIND> pf;
-    if (pf_ok && (int)blockIdx.x < ntiles) pf.load(a.imh, a.P, a.F, NKC, (size_t)blockIdx.x * kTM, tid);
+    if (pf_ok) pf.init(NKC, tid);
+    if (pf_ok && (int)blockIdx.x < ntiles) pf.load(a.imh, a.P, a.F, (size_t)blockIdx.x * kTM);
+    // P < 2^31 and obs_per >= 1: the datum row of model m is m / obs_per in 32-bit arithmetic
+    const unsigned int obs_per = (unsigned int)a.obs_per;
+    const unsigned int last_row = (unsigned int)(a.P - 1) / obs_per;
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const size_t row0 = (size_t)tile * kTM;
         // the datum rows this tile's models use, as float pairs (at most two
         // when models_per_row >= the tile; otherwise the epilogue splits per model)
-        const size_t s0 = row0 / (size_t)a.obs_per;
-        const bool split_rows = a.y_obs && (size_t)a.obs_per >= (size_t)kTM;
+        const unsigned int s0 = (unsigned int)row0 / obs_per;
+        const bool split_rows = a.y_obs && obs_per >= (unsigned int)kTM;
         if (split_rows)
             for (int i = tid; i < 2 * a.G; i += kThreads) {
-                const size_t srow = s0 + (size_t)(i / a.G);
-                const size_t last = ((size_t)a.P - 1) / (size_t)a.obs_per;
-                const double y = a.y_obs[(srow <= last ? srow : last) * a.G + (i % a.G)];
+                const int two = i >= a.G ? 1 : 0;
+                const unsigned int srow = s0 + (unsigned int)two;
+                const double y = a.y_obs[(size_t)(srow <= last_row ? srow : last_row) * a.G + (i - two * a.G)];
                 const float hi = (float)y;
                 ysplit[i] = make_float2(hi, (float)(y - (double)hi));
             }
         // stage the tile's spectra (rows past P and columns past F are zero);
         // consecutive lanes fill consecutive 16-byte rows of one core matrix
         if (pf_ok) {
-            pf.store(NKC, sbo, tid, Ahi, Alo);
+            pf.store(sbo, Ahi, Alo);
         } else {
             for (int c = tid; c < kTM * NKC; c += kThreads) {
                 const int r = (c & 7) + 8 * ((c >> 3) / NKC), kc = (c >> 3) % NKC;
@@ -395,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
         pending = issue;
         // the next tile's loads go out while the MMA runs and the epilogue reads it
         if (pf_ok && tile + (int)gridDim.x < ntiles)
-            pf.load(a.imh, a.P, a.F, NKC, (size_t)(tile + gridDim.x) * kTM, tid);
+            pf.load(a.imh, a.P, a.F, (size_t)(tile + gridDim.x) * kTM);
         const bool done = mbar_wait_bounded(mbar, phase, a.spins);
         if (!done) atomicExch(abort_p, 1);
         __syncthreads();
@@ -409,9 +439,12 @@ __global__ void __launch_bounds__(kThreads) gates_tc_kernel(TcArgs a) {
         const int row = quarter * 32 + lane;
         const size_t m = row0 + (size_t)row;
         const bool valid = m < (size_t)a.P;
-        const size_t srow = valid ? m / (size_t)a.obs_per : 0;
+        // with split rows the tile spans datum rows s0 and s0 + 1 at most
+        const unsigned int srow =
+            !valid ? 0u
+                   : split_rows ? s0 + ((unsigned int)m >= (s0 + 1u) * obs_per ? 1u : 0u) : (unsigned int)m / obs_per;
         const float2 *yrow = split_rows ? ysplit + (srow - s0) * a.G : nullptr;
-        const double *yd = (a.y_obs && !split_rows) ? a.y_obs + srow * a.G : nullptr;
+        const double *yd = (a.y_obs && !split_rows) ? a.y_obs + (size_t)srow * a.G : nullptr;
         LlAcc acc;
         const int c_lo = half * (a.N / 2), c_hi = c_lo + a.N / 2;
         for (int c = c_lo; c < c_hi; c += 8) {
