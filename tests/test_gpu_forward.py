@@ -352,6 +352,60 @@ def test_depth_cutoff_is_below_fp32_resolution(lib, torch_mod, name, kind):
             sysg.set_depth_cutoff(bad)
 
 
+def expected_layer_steps(models, name, att0=20.0):
+    """The layer-steps the depth cutoff runs, from its rule evaluated in FP64
+    on the host: per model and frequency, att = att0 + ln(max|s_n| / |s_0|),
+    ms = max(0, max_n -Re s_n), and for j < L - 1 the threshold on lambda^2
+    (-1 once sum_{i<=j} 2 h_i Re sqrt(s_i) exceeds att, else
+    ms + (att / (2 sum_{i<=j} h_i))^2); the abscissa pair (k, k + K/2) needs
+    1 + the number of thresholds its first lambda^2 does not exceed; items in
+    frequency-major order form groups of 32, and a group runs its largest
+    count on every item.  One-layer models run one layer-step per item."""
+    so = I.oracle_system(name)
+    K = so["K"]
+    K2 = (K + 1) // 2
+    l2 = np.asarray(O.hankel_rule(K, so["a"], so["h"])[0])[:K2] ** 2
+    mu0 = 4e-7 * np.pi
+    total = 0
+    for p in range(len(models["nlayers"])):
+        L = int(models["nlayers"][p])
+        if L == 1:
+            total += len(so["freqs"]) * K2
+            continue
+        h = 10.0 ** models["logh"][p, :L]
+        cnt = np.empty((len(so["freqs"]), K2), dtype=np.int64)
+        for fi, fr in enumerate(so["freqs"]):
+            w = 2 * np.pi * fr
+            s = np.array([1j * w * mu0 * O.colecole(so["cc_form"], 10.0 ** models["logsig"][p, n], models["m"][p, n],
+                                                     10.0 ** models["logtau"][p, n], models["c"][p, n], w)
+                          for n in range(L)])
+            att = att0 + np.log(np.abs(s).max() / abs(s[0]))
+            ms = max(0.0, float((-s.real).max()))
+            C = np.cumsum(2 * h[:L - 1] * np.sqrt(s[:L - 1]).real)
+            H = np.cumsum(h[:L - 1])
+            th = np.where(C > att, -1.0, ms + (att / (2 * H)) ** 2)
+            cnt[fi] = 1 + (l2[:, None] <= th[None, :]).sum(axis=1)
+        flat = cnt.ravel()
+        for g in range(0, flat.size, 32):
+            total += int(flat[g:g + 32].max()) * min(32, flat.size - g)
+    return total
+
+
+@pytest.mark.parametrize("kind", ["random", "contrast"])
+def test_layer_step_count_follows_the_cutoff_rule(lib, torch_mod, kind):
+    """aem_forward_f32_count (the kept fraction the roofline line reports)
+    equals the cutoff rule evaluated on the host in FP64, up to the items whose
+    lambda^2 lies within the FP32 thresholds' rounding of a threshold."""
+    name = "forward-g30-f60-k200"
+    sysg = lib.System(**I.system_kwargs(name))
+    draw = I.random_models if kind == "random" else I.contrast_models
+    models = as_f32_inputs(draw(120, seed=31))
+    n_gpu, frac = lib.forward_layer_steps(sysg, I.to_torch(models, torch_mod.float32))
+    n_host = expected_layer_steps(models, name)
+    print(f"\n{kind}: kept {frac:.4f}; GPU count {n_gpu}, host rule {n_host}")
+    assert abs(n_gpu - n_host) <= 1e-3 * n_host
+
+
 def test_autotune_records_the_fastest_shape(lib, torch_mod):
     sysg = lib.System(**I.system_kwargs("forward-g30-f60-k200"))
     models = I.to_torch(I.random_models(1 << 15, seed=3), torch_mod.float32)
