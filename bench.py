@@ -83,7 +83,39 @@ def parse():
                          "for the four basement conductivities, all soundings in one sampler")
     ap.add_argument("--flight-line", type=int, default=0, metavar="S",
                     help="run only the flight-line sampler: S soundings x 2048 particles in one sampler")
+    ap.add_argument("--layer-sweep", default="", metavar="L1,L2,...",
+                    help="run only the forward kernel's cost per layer count: 65,536 models of exactly L layers "
+                         "each on the throughput system, in the autotuned launch shape, one log-likelihood "
+                         "launch per count after warm-up (the intercept is the per-item and per-model work)")
     return ap.parse_args()
+
+
+def layer_sweep(torch, L, I, counts, steps):
+    """ms per launch of loglik_f32 on 65,536 models of exactly n layers, for
+    each n in counts, and the least-squares line through them."""
+    import numpy as np
+    sysg = L.System(**I.system_kwargs(WORKLOAD))
+    y_obs = np.full(sysg.G, 1e-11)
+    P = 1 << 16
+    sysg.autotune(I.to_torch(I.random_models(P, seed=0), torch.float32), repeats=2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for n in counts:
+        m = I.to_torch(I.random_models(P, seed=5, lmin=n, layers_max=n), torch.float32)
+        for _ in range(3):
+            L.loglik_f32(sysg, m, y_obs, I.EPS_AN, I.EPS_MN)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            L.loglik_f32(sysg, m, y_obs, I.EPS_AN, I.EPS_MN)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append({"layers": n, "ms_per_launch": e0.elapsed_time(e1) / steps})
+    res = {"workload": WORKLOAD, "models": P, "per_layer_count": out}
+    if len(out) > 1:
+        slope, icpt = np.polyfit([o["layers"] for o in out], [o["ms_per_launch"] for o in out], 1)
+        res["fit_ms"] = {"intercept": float(icpt), "per_layer": float(slope)}
+    return res
 
 
 class ClockSampler:
@@ -480,6 +512,10 @@ def main():
         return
     if args.convergence_study:
         print(json.dumps({"convergence_study": convergence_study(torch, L, I)}), flush=True)
+        return
+    if args.layer_sweep:
+        counts = [int(x) for x in args.layer_sweep.split(",") if x]
+        print(json.dumps({"layer_sweep": layer_sweep(torch, L, I, counts, max(1, args.steps))}), flush=True)
         return
     if args.rjsmc_only:
         if args.rjsmc_only == "large":
