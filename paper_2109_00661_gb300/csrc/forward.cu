@@ -608,6 +608,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
     }
     const float mu0 = (float)kMu0;
     const int FK2 = F * K2;
+    const bool wide = K2 >= 32;  // 32 consecutive items span two frequencies at most
 
     __shared__ int next_model;
     unsigned int nsteps = 0;  // layer-steps of the groups this lane bucketed (steps_out)
@@ -742,9 +743,14 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                             const int item = 32 * (gc + jl * NW) + lane;
                             if (item >= r1) continue;
                             int f = pk >> 16, k = (pk & 0xffff) + lane;
-                            while (k >= K2) {
+                            if (k >= K2) {  // K2 >= 32: a group reaches one more frequency at most
                                 k -= K2;
                                 ++f;
+                                if (!wide)
+                                    while (k >= K2) {
+                                        k -= K2;
+                                        ++f;
+                                    }
                             }
                             const ulonglong2 lw = KR[2 * k];
                             float v0, v1;
@@ -771,12 +777,21 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                 }
             }
             __syncthreads();
-            // the round's share of each frequency's Hankel sum, in a fixed order
-            const int fa = r0 / K2, fb = (r1 - 1) / K2;
+            // the round's share of each frequency's Hankel sum, in a fixed
+            // order: lane l adds the values at a + l, a + l + 32, ... in turn,
+            // four per pass with no loop control inside a pass, then the warp
+            // tree (one round, the throughput systems' case: frequencies 0..F-1)
+            const int fa = r0 == 0 ? 0 : r0 / K2, fb = r1 == FK2 ? F - 1 : (r1 - 1) / K2;
             for (int j = fa + warp; j <= fb; j += NW) {
                 const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
+                const float *vj = vals + (a - r0) + lane;
+                const int nb = b - a - lane;  // this lane's values: vj[32 u] for 32 u < nb
                 float acc = 0.f;
-                for (int q = a + lane; q < b; q += 32) acc += vals[q - r0];
+                for (int u0 = 0; u0 < nb; u0 += 128) {
+#pragma unroll
+                    for (int u = 0; u < 128; u += 32)
+                        if (u0 + u < nb) acc += vj[u0 + u];
+                }
                 acc = warp_sum<float>(acc);
                 if (lane == 0) imh[j] += acc;
             }
