@@ -515,6 +515,8 @@ def main():
         return
     if args.layer_sweep:
         counts = [int(x) for x in args.layer_sweep.split(",") if x]
+        if not counts or any(not 1 <= n <= 10 for n in counts):
+            raise SystemExit("--layer-sweep: layer counts must lie in 1..10 (the workload's row stride)")
         print(json.dumps({"layer_sweep": layer_sweep(torch, L, I, counts, max(1, args.steps))}), flush=True)
         return
     if args.rjsmc_only:
