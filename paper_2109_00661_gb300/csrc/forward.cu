@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
                             const int item = 32 * (gc + jl * NW) + lane;
                             if (item >= r1) continue;
                             int f = pk >> 16, k = (pk & 0xffff) + lane;
-                            if (k >= K2) {  // K2 >= 32: a group reaches one more frequency at most
+                            if (k >= K2) {  // into the next frequency; further ones only when K2 < 32
                                 k -= K2;
                                 ++f;
                                 if (!wide)
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             for (int j = fa + warp; j <= fb; j += NW) {
                 const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
                 const float *vj = vals + (a - r0) + lane;
-                const int nb = b - a - lane;  // this lane's values: vj[32 u] for 32 u < nb
+                const int nb = b - a - lane;  // this lane's values: vj[v], v = 0, 32, 64, ... below nb
                 float acc = 0.f;
                 for (int u0 = 0; u0 < nb; u0 += 128) {
 #pragma unroll
