@@ -778,22 +778,27 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             }
             __syncthreads();
             // the round's share of each frequency's Hankel sum, in a fixed
-            // order: lane l adds the values at a + l, a + l + 32, ... in turn,
-            // four per pass with no loop control inside a pass, then the warp
-            // tree (one round, the throughput systems' case: frequencies 0..F-1)
+            // order: four consecutive lanes per frequency, lane s adding the
+            // s-th quarter of the frequency's values of the round in turn,
+            // then (q0 + q1) + (q2 + q3) by two shuffles (one round, the
+            // throughput systems' case: frequencies 0..F-1)
             const int fa = r0 == 0 ? 0 : r0 / K2, fb = r1 == FK2 ? F - 1 : (r1 - 1) / K2;
-            for (int j = fa + warp; j <= fb; j += NW) {
-                const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
-                const float *vj = vals + (a - r0) + lane;
-                const int nb = b - a - lane;  // this lane's values: vj[v], v = 0, 32, 64, ... below nb
+            for (int t0 = 0; t0 < 4 * (fb - fa + 1); t0 += blockDim.x) {  // CTA-uniform trip count
+                const int t = t0 + tid, j = fa + (t >> 2), s = t & 3;
                 float acc = 0.f;
-                for (int u0 = 0; u0 < nb; u0 += 128) {
+                if (j <= fb) {
+                    const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
+                    const int c = (b - a + 3) >> 2, lo = a + s * c, hi = lo + c < b ? lo + c : b;
+                    const float *vq = vals - r0;
+                    for (int q0 = lo; q0 < hi; q0 += 4) {
 #pragma unroll
-                    for (int u = 0; u < 128; u += 32)
-                        if (u0 + u < nb) acc += vj[u0 + u];
+                        for (int u = 0; u < 4; ++u)
+                            if (q0 + u < hi) acc += vq[q0 + u];
+                    }
                 }
-                acc = warp_sum<float>(acc);
-                if (lane == 0) imh[j] += acc;
+                acc += __shfl_xor_sync(kFull, acc, 1);
+                acc += __shfl_xor_sync(kFull, acc, 2);
+                if (s == 0 && j <= fb) imh[j] += acc;
             }
             __syncthreads();
         }
