@@ -555,9 +555,10 @@ __host__ __device__ inline size_t value_words(int F, int LS) {
 // items (frequency major, F*K2 of them) are taken in rounds of kValsWords:
 // every item stores
 // its weighted pair value at its own index in the buffer; after the round
-// each frequency the round touched is summed by one warp (lane l takes the
-// round's values k = l, l + 32, ... of that frequency, then a warp tree) and
-// added to imh[f], rounds in order.  The order of every sum is fixed by the
+// each frequency the round touched is summed by four consecutive lanes (lane
+// s adds the s-th contiguous quarter of the round's values of that frequency
+// in turn, then (q0 + q1) + (q2 + q3) by two shuffles) and added to imh[f],
+// rounds in order.  The order of every sum is fixed by the
 // item indices alone.  (The throughput system's 60 x 100 items take one
 // round.)  Before the item loop the value region holds the prologue's
 // stmp[F*LS] (float2).
