@@ -556,9 +556,9 @@ __host__ __device__ inline size_t value_words(int F, int LS) {
 // every item stores
 // its weighted pair value at its own index in the buffer; after the round
 // each frequency the round touched is summed by four consecutive lanes (lane
-// s adds the s-th contiguous quarter of the round's values of that frequency
-// in turn, then (q0 + q1) + (q2 + q3) by two shuffles) and added to imh[f],
-// rounds in order.  The order of every sum is fixed by the
+// s adds the values at s + 4 i into four accumulators by i mod 4, then a
+// tree over the sixteen partial sums, two levels by shuffles) and added to
+// imh[f], rounds in order.  The order of every sum is fixed by the
 // item indices alone.  (The throughput system's 60 x 100 items take one
 // round.)  Before the item loop the value region holds the prologue's
 // stmp[F*LS] (float2).
@@ -779,23 +779,28 @@ __global__ void __launch_bounds__(NT, MINB) forward_f32_kernel(ModelsView<FP32Op
             }
             __syncthreads();
             // the round's share of each frequency's Hankel sum, in a fixed
-            // order: four consecutive lanes per frequency, lane s adding the
-            // s-th quarter of the frequency's values of the round in turn,
-            // then (q0 + q1) + (q2 + q3) by two shuffles (one round, the
-            // throughput systems' case: frequencies 0..F-1)
+            // order: four consecutive lanes per frequency; lane s adds the
+            // values at a + s + 4 i into four accumulators by i mod 4 (the
+            // sixteen interleaved subsets of the frequency's values, each of
+            // them spread over its whole abscissa range, so partial sums
+            // cancel as the whole does), then (c0 + c1) + (c2 + c3) and two
+            // shuffles (one round, the throughput systems' case: frequencies
+            // 0..F-1)
             const int fa = r0 == 0 ? 0 : r0 / K2, fb = r1 == FK2 ? F - 1 : (r1 - 1) / K2;
             for (int t0 = 0; t0 < 4 * (fb - fa + 1); t0 += blockDim.x) {  // CTA-uniform trip count
                 const int t = t0 + tid, j = fa + (t >> 2), s = t & 3;
                 float acc = 0.f;
                 if (j <= fb) {
                     const int a = j * K2 > r0 ? j * K2 : r0, b = (j + 1) * K2 < r1 ? (j + 1) * K2 : r1;
-                    const int c = (b - a + 3) >> 2, lo = a + s * c, hi = lo + c < b ? lo + c : b;
                     const float *vq = vals - r0;
-                    for (int q0 = lo; q0 < hi; q0 += 4) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (q0 + u < hi) acc += vq[q0 + u];
+                    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+                    for (int q = a + s; q < b; q += 16) {
+                        c0 += vq[q];
+                        if (q + 4 < b) c1 += vq[q + 4];
+                        if (q + 8 < b) c2 += vq[q + 8];
+                        if (q + 12 < b) c3 += vq[q + 12];
                     }
+                    acc = (c0 + c1) + (c2 + c3);
                 }
                 acc += __shfl_xor_sync(kFull, acc, 1);
                 acc += __shfl_xor_sync(kFull, acc, 2);
