@@ -52,7 +52,7 @@ K_PARAM_BYTES = 201        # per model in: 5 float parameters x 10 layers + the 
 # this workload, from an ncu capture (dram__bytes_read.sum and
 # dram__bytes_write.sum, one pass); spectra still dirty in L2 when the launch
 # ends are written back after it and are not counted
-SPECTRUM_LAUNCH_BYTES_1M = 219.56e6 + 210.95e6
+SPECTRUM_LAUNCH_BYTES_1M = 219.61e6 + 210.86e6
 METRIC = "forward+loglik evals/s"
 UNIT = "evals/s"
 
