@@ -87,7 +87,15 @@ def parse():
                     help="run only the forward kernel's cost per layer count: 65,536 models of exactly L layers "
                          "each on the throughput system, in the autotuned launch shape, one log-likelihood "
                          "launch per count after warm-up (the intercept is the per-item and per-model work)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.layer_sweep:
+        try:
+            counts = [int(x) for x in args.layer_sweep.split(",") if x]
+        except ValueError:
+            counts = []
+        if not counts or any(not 1 <= n <= 10 for n in counts):
+            ap.error("--layer-sweep: comma-separated layer counts in 1..10 (the workload's row stride)")
+    return args
 
 
 def layer_sweep(torch, L, I, counts, steps):
@@ -515,8 +523,6 @@ def main():
         return
     if args.layer_sweep:
         counts = [int(x) for x in args.layer_sweep.split(",") if x]
-        if not counts or any(not 1 <= n <= 10 for n in counts):
-            raise SystemExit("--layer-sweep: layer counts must lie in 1..10 (the workload's row stride)")
         print(json.dumps({"layer_sweep": layer_sweep(torch, L, I, counts, max(1, args.steps))}), flush=True)
         return
     if args.rjsmc_only:

@@ -21,3 +21,13 @@ def test_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["metric"] == "forward+loglik evals/s" and line["config"]["workload"].startswith("forward-g30-f60-k200")
+
+
+def test_layer_sweep_refuses_counts_outside_the_row_stride():
+    """--layer-sweep is checked on the host before any device work: counts
+    outside 1..10 (the workload's row stride) or non-integers end with a
+    usage error."""
+    for bad in ("0,4", "11", "x", ","):
+        res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--layer-sweep", bad],
+                             capture_output=True, text=True, timeout=120, cwd=ROOT)
+        assert res.returncode == 2 and "--layer-sweep" in res.stderr, (bad, res.stderr[-500:])
